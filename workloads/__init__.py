@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs for the FMM vortex-particle workloads.
+
+Input generation only: this module holds none of the method's arithmetic and
+is shared by the tests, the benchmark and the oracle checks.  Every generator
+is seeded (numpy Philox, seed = 20111106 + workload id unless given) and
+returns float32 positions/strengths as the GPU receives them.
+
+Workloads (all sizes as used by the benchmark and the parity tests):
+  jittered_lattice  N = n^3 blobs on a jittered lattice in the unit cube
+                    (spacing h = 1/n, points (i+1/2)h, jitter U(+-0.25h)),
+                    gamma ~ N(0,1)^3 drawn in FP64 then rounded, sigma = 1.5h,
+                    free space.  n = 16 is the 4096-blob accuracy case.
+  taylor_green      N = n^3 blobs on the lattice (i+1/2)h of the periodic cube
+                    [0, 2 pi)^3, h = 2 pi/n, gamma = omega_TG(x) h^3 with
+                    u_TG = (sin x cos y cos z, -cos x sin y cos z, 0),
+                    sigma = 1.2h.  n = 128 is the 2,097,152-blob benchmark.
+  random_spectrum   Lattice in [0, 2 pi)^3 with vorticity of a random-phase
+                    solenoidal field, E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4,
+                    u_rms = 1, gamma = omega h^3, sigma = 1.2h.  Also returns
+                    the Fourier modes so the velocity can be evaluated exactly.
+  uniform_ball / plummer   clustered free-space inputs with Gaussian strengths.
+"""
+import math
+
+import numpy as np
+
+BASE_SEED = 20111106
+
+
+def rng(seed):
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def jittered_lattice(n=16, seed=BASE_SEED + 1):
+    g = rng(seed)
+    h = 1.0 / n
+    i = (np.arange(n) + 0.5) * h
+    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    pos = pos + g.uniform(-0.25 * h, 0.25 * h, size=pos.shape)
+    gamma = g.standard_normal(size=pos.shape)
+    return dict(pos=pos.astype(np.float32), gamma=gamma.astype(np.float32),
+                sigma=np.float32(1.5 * h), periodic=False, p=6, theta=0.5, ncrit=32,
+                name="jittered-lattice-%d^3" % n)
+
+
+def _tg_vorticity(x):
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    return np.stack([-np.cos(X) * np.sin(Y) * np.sin(Z),
+                     -np.sin(X) * np.cos(Y) * np.sin(Z),
+                     2.0 * np.sin(X) * np.sin(Y) * np.cos(Z)], 1)
+
+
+def taylor_green(n=128):
+    L = 2.0 * math.pi
+    h = L / n
+    i = (np.arange(n) + 0.5) * h
+    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    pos32 = pos.astype(np.float32)
+    gamma = _tg_vorticity(pos32.astype(np.float64)) * h ** 3
+    return dict(pos=pos32, gamma=gamma.astype(np.float32), sigma=np.float32(1.2 * h),
+                periodic=True, box_min=np.zeros(3), box_len=L, p=10, theta=0.4, ncrit=64,
+                images=3, name="taylor-green-%d^3" % n)
+
+
+def random_spectrum(n=64, k0=4.0, seed=BASE_SEED + 3, kmax=None):
+    """Random-phase solenoidal field on an n^3 lattice; returns modes too."""
+    g = rng(seed)
+    L = 2.0 * math.pi
+    h = L / n
+    if kmax is None:
+        kmax = min(n // 2 - 1, int(5 * k0))
+    r = np.arange(-kmax, kmax + 1)
+    KX, KY, KZ = np.meshgrid(r, r, r, indexing="ij")
+    k = np.stack([KX.ravel(), KY.ravel(), KZ.ravel()], 1).astype(np.float64)
+    kk = np.sqrt((k * k).sum(1))
+    keep = (kk > 0) & (kk <= kmax)
+    # one representative per +-k pair (Hermitian symmetry)
+    first = (k[:, 0] > 0) | ((k[:, 0] == 0) & (k[:, 1] > 0)) | ((k[:, 0] == 0) & (k[:, 1] == 0) & (k[:, 2] > 0))
+    keep &= first
+    k = k[keep]
+    kk = kk[keep]
+    E = kk ** 4 * np.exp(-2.0 * (kk / k0) ** 2)
+    xi = g.standard_normal((k.shape[0], 3)) + 1j * g.standard_normal((k.shape[0], 3))
+    khat = k / kk[:, None]
+    xi = xi - (xi * khat).sum(1)[:, None] * khat  # solenoidal projection
+    amp = np.sqrt(E / (4.0 * math.pi * kk ** 2))
+    uhat = xi * amp[:, None]
+    i = (np.arange(n) + 0.5) * h
+    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    pos32 = pos.astype(np.float32)
+    x = pos32.astype(np.float64)
+    u = np.zeros_like(x)
+    w = np.zeros_like(x)
+    for c0 in range(0, k.shape[0], 256):
+        kc = k[c0:c0 + 256]
+        ph = np.exp(1j * (x @ kc.T))
+        uc = uhat[c0:c0 + 256]
+        u += 2.0 * np.real(ph @ uc)
+        w += 2.0 * np.real(ph @ (1j * np.cross(kc, uc)))
+    scale = 1.0 / math.sqrt((u * u).sum(1).mean())
+    uhat *= scale
+    w *= scale
+    gamma = w * h ** 3
+    return dict(pos=pos32, gamma=gamma.astype(np.float32), sigma=np.float32(1.2 * h),
+                periodic=True, box_min=np.zeros(3), box_len=L, p=10, theta=0.4, ncrit=64,
+                images=3, modes=k, uhat=uhat, name="random-spectrum-%d^3" % n)
+
+
+def uniform_ball(n, seed=BASE_SEED + 4):
+    g = rng(seed)
+    v = g.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    r = g.random(n) ** (1.0 / 3.0)
+    pos = v * r[:, None]
+    gamma = g.standard_normal((n, 3))
+    sigma = 1.5 * (4.0 / 3.0 * math.pi / n) ** (1.0 / 3.0)
+    return dict(pos=pos.astype(np.float32), gamma=gamma.astype(np.float32),
+                sigma=np.float32(sigma), periodic=False, name="ball-%d" % n)
+
+
+def plummer(n, a=0.1, seed=BASE_SEED + 5):
+    g = rng(seed)
+    X = g.random(2 * n + 16)
+    X = X[X < 0.999][:n]
+    while X.shape[0] < n:
+        extra = g.random(n)
+        X = np.concatenate([X, extra[extra < 0.999]])[:n]
+    r = a / np.sqrt(X ** (-2.0 / 3.0) - 1.0)
+    v = g.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    pos = v * r[:, None]
+    gamma = g.standard_normal((n, 3))
+    sigma = 1.5 * (4.0 / 3.0 * math.pi / n) ** (1.0 / 3.0)
+    return dict(pos=pos.astype(np.float32), gamma=gamma.astype(np.float32),
+                sigma=np.float32(sigma), periodic=False, name="plummer-%d" % n)
+
+
+def random_cloud(n, seed=BASE_SEED + 6, box=1.0, zero_net=False):
+    g = rng(seed)
+    pos = g.random((n, 3)) * box
+    gamma = g.standard_normal((n, 3))
+    if zero_net and n > 0:
+        gamma -= gamma.mean(0)
+    return dict(pos=pos.astype(np.float32), gamma=gamma.astype(np.float32))
