@@ -1,0 +1,297 @@
+"""Benchmark: FMM velocity + stretching throughput on GB300.
+
+Default workload: N = 128^3 = 2,097,152 Gaussian vortex blobs on the lattice
+of the periodic cube [0, 2pi)^3 with Taylor-Green strengths, sigma = 1.2h,
+p = 10, theta = 0.4, ncrit = 64, 27 explicit images + 2 lattice rings.
+A step = one full fmm_eval_velocity_stretching call (tree build, upward
+pass, traversal, M2L, downward pass, P2P) on inputs resident in HBM; L2 is
+flushed (512 MB write) before every timed step.  `e2e` is the same metric
+through fmm_eval_velocity_stretching_host with pinned host buffers (copies
+in the timed region).  Multi-GPU: independent replicas (one problem per GPU,
+no collective); value = total particles / max-over-ranks time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fmm|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM Biot-Savart+stretching particles/s at rel-L2<=1e-4"
+UNIT = "particles/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# FP32 flops per P2P pair counted from the CUDA source of pair_acc (FMA = 2):
+# difference 3, r^2 5, cutoff/S/T 26, gamma_j x d 9, u 6, sum S gamma_j 6,
+# T (gamma_i . d) 6, s 6.  Plus 2 MUFU ops (rsqrt, ex2).
+P2P_FLOPS_PER_PAIR = 67
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fmm", choices=["fmm", "reference"])
+    ap.add_argument("--n-side", type=int, default=128)
+    ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-targets", type=int, default=48)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n_side):
+    import workloads
+    return workloads.taylor_green(n_side)
+
+
+def cpu_baseline(w, vel_gpu, n_targets):
+    """Oracle leg: FP64 direct sum (C, OpenMP) on sampled targets + accuracy of the GPU result."""
+    import numpy as np
+    from oracle import direct as od
+    from oracle import periodic as op
+    od.build()
+    n = w["pos"].shape[0]
+    rng = np.random.default_rng(7)
+    tgt = rng.choice(n, size=n_targets, replace=False)
+    imgs = op.image_shifts(w["box_len"], 1)
+    t0 = time.perf_counter()
+    od.direct(w["pos"][tgt], w["gamma"][tgt], w["pos"], w["gamma"], float(w["sigma"]), images=imgs)
+    dt = time.perf_counter() - t0
+    out = {"value": n_targets / dt, "unit": UNIT, "cores": od.num_threads(), "kind": "oracle",
+           "sample": "FP64 direct sum of Eqs. 1-3 (plain C, OpenMP) for %d sampled targets against all %d "
+                     "sources in the 27 explicit periodic images (no lattice far field); value = targets/s"
+                     % (n_targets, n)}
+    acc = None
+    if vel_gpu is not None:
+        u_ref, _ = op.taylor_green(w["pos"].astype(np.float64), w["gamma"].astype(np.float64), float(w["sigma"]))
+        d = vel_gpu.astype(np.float64) - u_ref
+        acc = float(np.linalg.norm(d) / np.linalg.norm(u_ref))
+    return out, acc
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle as it stands, on the host cores, same workload/metric."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import direct as od
+    from oracle import periodic as op
+    w = workload(args.n_side)
+    od.build()
+    n = w["pos"].shape[0]
+    imgs = op.image_shifts(w["box_len"], 1)
+    rng = np.random.default_rng(11)
+    per_step = max(1, args.cpu_targets // 4)
+    times = []
+    for it in range(args.warmup + args.steps):
+        tgt = rng.choice(n, size=per_step, replace=False)
+        t0 = time.perf_counter()
+        od.direct(w["pos"][tgt], w["gamma"][tgt], w["pos"], w["gamma"], float(w["sigma"]), images=imgs)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "n": n, "p": 10, "theta": 0.4, "ncrit": 64, "periodic": True},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": od.num_threads(),
+                             "sample": "FP64 direct sum over the 27 explicit images for %d sampled targets per "
+                                       "step; value = targets/s" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1106_5273_gb300 import Params, Plan
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args.n_side)
+    n = w["pos"].shape[0]
+    mode = {"auto": 0, "simt": 1, "tensor": 2}[args.m2l]
+    prm = Params.default(p=w["p"], theta=w["theta"], ncrit=w["ncrit"], periodic=1, box_min=w["box_min"],
+                         box_len=w["box_len"], images=w["images"], m2l_mode=mode)
+    plan = Plan(n, prm)
+    pos = torch.from_numpy(w["pos"]).cuda()
+    gam = torch.from_numpy(w["gamma"]).cuda()
+    vel = torch.empty((n, 3), device="cuda")
+    dg = torch.empty((n, 3), device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sig = float(w["sigma"])
+    for _ in range(args.warmup):
+        plan.eval(pos, gam, sigma_uniform=sig, vel=vel, dgamma=dg)
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, p2p_ms = [], []
+    launches = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval(pos, gam, sigma_uniform=sig, vel=vel, dgamma=dg)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st = plan.stats()
+        p2p_ms.append(st.ms_p2p)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    st = plan.stats()
+    t_step = sum(ms) / len(ms)
+    if dist:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * n / (t_step * 1e-3)
+    # end to end through the host-buffer entry point (pinned memory)
+    hp = torch.from_numpy(w["pos"]).pin_memory().numpy()
+    hg = torch.from_numpy(w["gamma"]).pin_memory().numpy()
+    hv = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    hd = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
+    plan.set_timing(False)
+    plan.eval_host(hp, hg, sigma_uniform=sig, vel=hv, dgamma=hd)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.eval_host(hp, hg, sigma_uniform=sig, vel=hv, dgamma=hd)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_t = sum(e2e_ms) / len(e2e_ms)
+    # roofline of the dominant kernel (P2P), from its CUDA-event time inside the step
+    pairs = st.p2p_pairs
+    p2p_t = sum(p2p_ms) / len(p2p_ms) * 1e-3
+    achieved = P2P_FLOPS_PER_PAIR * pairs / p2p_t / 1e12
+    clk_mhz = 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "p2p_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch_full_workload")
+        except Exception:
+            traffic = None
+    if rank == 0:
+        cpu, acc = (None, None)
+        if not args.no_cpu_baseline and world == 1:
+            cpu, acc = cpu_baseline(w, vel.cpu().numpy(), args.cpu_targets)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "n": n, "p": w["p"], "theta": w["theta"], "ncrit": w["ncrit"],
+                       "periodic": True, "images": w["images"], "sigma_over_h": 1.2,
+                       "l2": "flushed (512 MB write) before every timed step", "m2l": args.m2l,
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy": {"rel_l2_u_vs_closed_form": acc},
+            "e2e": {"value": world * n / (e2e_t * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * n * 12), "d2h_bytes_per_step": int(2 * n * 12)},
+            "gpu_launches": None,
+            "roofline": {"bound": "alu", "kernel": "k_p2p", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "flops_per_pair": P2P_FLOPS_PER_PAIR, "pairs_per_launch": pairs,
+                         "ms_per_launch": p2p_t * 1e3,
+                         "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
+            "paper_convention_tflops": 174 * pairs / p2p_t / 1e12,
+            "phases_ms": {k: getattr(st, k) for k in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
+                                                       "ms_downward", "ms_p2p", "ms_total")},
+            "work": {k: getattr(st, k) for k in ("ncells", "nleaves", "nlevels", "p2p_cell_pairs", "p2p_pairs",
+                                                  "m2l_pairs", "m2l_steps", "m2l_keys", "m2l_tensor")},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

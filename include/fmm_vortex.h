@@ -1,0 +1,189 @@
+/*
+ * fmm_vortex.h -- C ABI of the GB300 (sm_103a) FMM for vortex particles.
+ *
+ * One call evaluates, for N Gaussian vortex blobs, the regularized
+ * Biot-Savart velocity (Eq. 1 with the cutoff of Eq. 2) and the
+ * vortex-stretching term (Eq. 3), with the fast multipole method of
+ * Sec. 3 (Morton octree, P2M/M2M, dual-tree traversal with the FMM MAC of
+ * Algorithms 1-2, M2L, L2L/L2P, P2P) in free space or in a periodic cube
+ * (Sec. 3.5).  All compute runs in CUDA kernels on the caller's stream.
+ *
+ * Conventions shared by every entry point
+ *   - d = x_i - x_j, r = |d|, rho = r / sigma_j (the SOURCE core width),
+ *     g(rho) = erf(rho/sqrt2) - sqrt(2/pi) rho exp(-rho^2/2)           (Eq. 2)
+ *     u_i    = (1/4pi) sum_j g/r^3 (gamma_j x d)                         (Eq. 1)
+ *     s_i    = (gamma_i . grad) u (x_i)                                  (Eq. 3)
+ *   - Arrays are float32, row-major, contiguous: pos[n][3], gamma[n][3],
+ *     vel[n][3], dgamma[n][3], sigma[n].  Device pointers unless the entry
+ *     point name ends in _host.  The caller owns every array it passes.
+ *   - Calls are asynchronous with respect to the host unless stated; they
+ *     may block briefly to read small counts (tree and list sizes).
+ *   - Return value: FMM_OK (0) or a negative FMM_E_* code; no call exits,
+ *     traps or prints.  After an error the outputs are undefined.
+ *   - A plan may be used by one host thread at a time.
+ */
+#ifndef FMM_VORTEX_H
+#define FMM_VORTEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FMM_OK = 0,
+  FMM_E_INVAL = -1,    /* bad argument (null pointer, n > n_max, p out of range ...) */
+  FMM_E_NOMEM = -2,    /* device or host allocation failed */
+  FMM_E_CAPACITY = -3, /* an internal list overflowed a configured bound */
+  FMM_E_TIMEOUT = -4,  /* a bounded device wait gave up */
+  FMM_E_DEPTH = -5,    /* translation vector outside the encodable range */
+  FMM_E_CUDA = -6      /* a CUDA runtime call failed (sticky device error etc.) */
+};
+
+enum { FMM_OUT_VELOCITY = 1, FMM_OUT_STRETCHING = 2 };
+
+/* How M2L products are computed. */
+enum {
+  FMM_M2L_AUTO = 0,   /* tensor cores when p^2 <= 128, else SIMT FP32 */
+  FMM_M2L_SIMT = 1,   /* FP32 CUDA-core GEMM per (target tile, translation) */
+  FMM_M2L_TENSOR = 2  /* tcgen05 BF16x3 split products, FP32 accumulation */
+};
+
+typedef struct fmm_plan_s* fmm_plan;
+
+/*
+ * Parameters (Sec. 3 and 4.2).  fmm_params_default() fills the defaults.
+ *   p          expansion order: degrees n = 0..p-1, p^2 real coefficients per
+ *              potential; 1 <= p <= 16.  (The paper uses p = 14.)
+ *   theta      MAC opening parameter: M2L iff R_A + R_B < theta |X_A - X_B|
+ *              (Sec. 3.3, Fig. mac); 0 < theta < 1.
+ *   ncrit      leaf capacity: a cell splits while it holds more than ncrit
+ *              particles and its level is below 21 (Sec. 3.2); 1..4096.
+ *   periodic   0 free space, 1 periodic cube [box_min, box_min + box_len)^3.
+ *   images     periodic lattice levels: 27 explicit images through the
+ *              traversal, then images-1 rings of super-cells (3^images cells
+ *              per axis in total, Sec. 4.2); 1..8; ignored if !periodic.
+ *   box_min, box_len   the periodic cube; ignored if !periodic.
+ *   sigma_sep  k_sigma: M2L also needs |X_A-X_B| - R_A - R_B >= k_sigma *
+ *              max sigma, because the far field uses the singular kernel.
+ *   outputs    FMM_OUT_VELOCITY | FMM_OUT_STRETCHING (informational; a
+ *              NULL output pointer skips that output).
+ *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR.
+ */
+typedef struct {
+  int32_t p;
+  float theta;
+  int32_t ncrit;
+  int32_t periodic;
+  int32_t images;
+  double box_min[3];
+  double box_len;
+  float sigma_sep;
+  int32_t outputs;
+  int32_t m2l_mode;
+} fmm_params;
+
+/* Work counts of the last evaluation (for throughput and roofline reports). */
+typedef struct {
+  int64_t n;              /* particles */
+  int64_t ncells;         /* octree cells */
+  int64_t nleaves;
+  int32_t nlevels;        /* deepest level + 1 */
+  int32_t m2l_tensor;     /* 1 if the last M2L ran on tensor cores */
+  int64_t p2p_cell_pairs; /* (target leaf, source leaf, image) entries */
+  int64_t p2p_pairs;      /* particle-particle interactions (incl. self pair) */
+  int64_t m2l_pairs;      /* (target cell, source cell, image) M2L entries */
+  int64_t m2l_steps;      /* (64-cell target tile, translation) GEMM steps */
+  int64_t m2l_keys;       /* distinct translation operators */
+  double ms_tree;         /* phase times in ms (CUDA events), if timing enabled */
+  double ms_upward;
+  double ms_traverse;
+  double ms_m2l;
+  double ms_downward;
+  double ms_p2p;
+  double ms_total;
+} fmm_stats;
+
+/* Fill *prm with defaults: p=10, theta=0.4, ncrit=64, free space, images=3,
+ * box [0,1)^3, sigma_sep=5, both outputs, FMM_M2L_AUTO. */
+void fmm_params_default(fmm_params* prm);
+
+/*
+ * Create a plan for up to n_max particles on the current CUDA device.
+ * Builds the M2M/L2L operators and, if periodic, the FP64 lattice operator
+ * (Sec. 3.5).  Device workspace is allocated here and grown on demand by
+ * evaluations.  Returns FMM_E_INVAL for bad parameters, FMM_E_NOMEM, or
+ * FMM_E_CUDA; *out is set only on success.
+ */
+int fmm_plan_create(const fmm_params* prm, int64_t n_max, fmm_plan* out);
+
+/*
+ * Evaluate velocity (vel) and stretching (dgamma) for n <= n_max particles.
+ *   pos[n][3], gamma[n][3]   device float32 inputs (positions in the periodic
+ *                             cube when periodic; free space: any finite values)
+ *   sigma[n] or NULL          per-particle core widths (device); when NULL every
+ *                             particle has sigma_uniform (> 0)
+ *   vel[n][3], dgamma[n][3]   device float32 outputs, either may be NULL
+ *   cuda_stream               cudaStream_t (NULL = legacy default stream)
+ * Sec. 2.1 Eqs. (1)-(3), Sec. 3.1 (the six kernels), Algorithms 1-2.
+ * Blocks the host for the small counts that size the tree and the lists.
+ */
+int fmm_eval_velocity_stretching(fmm_plan plan, int64_t n, const float* pos,
+                                 const float* gamma, const float* sigma,
+                                 float sigma_uniform, float* vel, float* dgamma,
+                                 void* cuda_stream);
+
+/*
+ * Same as fmm_eval_velocity_stretching with HOST arrays: the inputs are
+ * copied to plan-owned device buffers, the outputs copied back, and the call
+ * returns after the stream has finished (synchronous).  Page-locked host
+ * memory gives the fastest copies; pageable memory works.
+ */
+int fmm_eval_velocity_stretching_host(fmm_plan plan, int64_t n, const float* pos,
+                                      const float* gamma, const float* sigma,
+                                      float sigma_uniform, float* vel, float* dgamma,
+                                      void* cuda_stream);
+
+/* Release every resource of the plan (synchronizes the device). NULL is ok. */
+void fmm_plan_destroy(fmm_plan plan);
+
+/* Static string for an FMM_* code. */
+const char* fmm_strerror(int code);
+
+/*
+ * All-pairs direct sum of Eqs. (1)-(3) on the device, free space, without
+ * a tree: the same P2P pair kernel over every (target, source) pair of one
+ * array (the self pair excluded).  Device arrays as above.  O(n^2).
+ */
+int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gamma,
+                                   const float* sigma, float sigma_uniform, float* vel,
+                                   float* dgamma, void* cuda_stream);
+
+/* Enable (1) or disable (0) CUDA-event phase timing in fmm_stats. */
+int fmm_plan_set_timing(fmm_plan plan, int enable);
+
+/* Work counts and phase times of the last evaluation (synchronizes). */
+int fmm_plan_get_stats(fmm_plan plan, fmm_stats* out);
+
+/*
+ * Inspection of the last evaluation's tree and lists (synchronizes, copies
+ * to HOST arrays the caller sized from fmm_plan_get_stats).  Any pointer may
+ * be NULL to skip it.
+ *   order[n]  sorted position -> input index;  keys[n]  sorted Morton keys
+ *   per cell: begin, end (sorted particle range), level, parent, child_begin,
+ *   nchild, center[3] (FP64 cube centre), radius (FP64)
+ *   p2p[m][3] / m2l[m][3]: (target cell, source cell, image 0..26; 13 = none)
+ *   in traversal order (P2P grouped by target leaf).
+ */
+int fmm_plan_get_order(fmm_plan plan, uint32_t* order, uint64_t* keys);
+int fmm_plan_get_cells(fmm_plan plan, int32_t* begin, int32_t* end, int32_t* level,
+                       int32_t* parent, int32_t* child_begin, int32_t* nchild,
+                       double* center, double* radius);
+int fmm_plan_get_lists(fmm_plan plan, int32_t* p2p, int32_t* m2l);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_VORTEX_H */

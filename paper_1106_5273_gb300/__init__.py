@@ -1,0 +1,22 @@
+"""GB300 (sm_103a) FMM for the regularized Biot-Savart velocity and the
+vortex-stretching term of N Gaussian vortex blobs (Yokota, Barba, Narumi,
+Yasuoka, arXiv:1106.5273, Secs. 2-3).
+
+The compute path is the CUDA library built from csrc/ (C ABI in
+include/fmm_vortex.h); `binding` is its thin Python binding:
+
+    from paper_1106_5273_gb300 import Params, Plan, direct
+
+The binding is loaded on first use, so `python -m paper_1106_5273_gb300.build`
+works before the library exists; using the binding without the library
+raises ImportError (there is no fallback).
+"""
+__all__ = ["Params", "Plan", "Stats", "FmmError", "direct", "lib", "library_path",
+           "FMM_M2L_AUTO", "FMM_M2L_SIMT", "FMM_M2L_TENSOR"]
+
+
+def __getattr__(name):
+    if name in __all__:
+        from . import binding
+        return getattr(binding, name)
+    raise AttributeError(name)

@@ -1,0 +1,210 @@
+"""ctypes binding of include/fmm_vortex.h (argument marshalling only).
+
+Every computation runs in the CUDA library; there is no CPU fallback.  The
+library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1106_5273_gb300.build``); importing this module raises if
+it is missing.  Device arrays are torch CUDA tensors (float32, contiguous),
+passed by ``data_ptr()``; host arrays for the ``_host`` entry point are numpy.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "_lib", "libfmm_vortex.so")
+
+FMM_OK = 0
+FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
+FMM_OUT_VELOCITY, FMM_OUT_STRETCHING = 1, 2
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s failed: %s (%d)" % (what, _strerror(code), code))
+        self.code = code
+
+
+if not os.path.exists(library_path):
+    raise ImportError("CUDA library %s is missing: run __graft_entry__.build() "
+                      "(python -m paper_1106_5273_gb300.build)" % library_path)
+lib = ctypes.CDLL(library_path)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("theta", ctypes.c_float), ("ncrit", ctypes.c_int32),
+                ("periodic", ctypes.c_int32), ("images", ctypes.c_int32),
+                ("box_min", ctypes.c_double * 3), ("box_len", ctypes.c_double),
+                ("sigma_sep", ctypes.c_float), ("outputs", ctypes.c_int32),
+                ("m2l_mode", ctypes.c_int32)]
+
+    @classmethod
+    def default(cls, **kw):
+        q = cls()
+        lib.fmm_params_default(ctypes.byref(q))
+        for k, v in kw.items():
+            if k == "box_min":
+                for i in range(3):
+                    q.box_min[i] = float(v[i])
+            else:
+                setattr(q, k, v)
+        return q
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
+                ("nlevels", ctypes.c_int32), ("m2l_tensor", ctypes.c_int32),
+                ("p2p_cell_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("m2l_pairs", ctypes.c_int64), ("m2l_steps", ctypes.c_int64),
+                ("m2l_keys", ctypes.c_int64), ("ms_tree", ctypes.c_double),
+                ("ms_upward", ctypes.c_double), ("ms_traverse", ctypes.c_double),
+                ("ms_m2l", ctypes.c_double), ("ms_downward", ctypes.c_double),
+                ("ms_p2p", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+lib.fmm_params_default.argtypes = [ctypes.POINTER(Params)]
+lib.fmm_params_default.restype = None
+lib.fmm_strerror.argtypes = [ctypes.c_int]
+lib.fmm_strerror.restype = ctypes.c_char_p
+lib.fmm_plan_create.argtypes = [ctypes.POINTER(Params), _i64, ctypes.POINTER(_vp)]
+lib.fmm_plan_destroy.argtypes = [_vp]
+lib.fmm_plan_destroy.restype = None
+for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host"):
+    getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
+lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
+lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+lib.fmm_plan_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
+lib.fmm_plan_get_order.argtypes = [_vp, _vp, _vp]
+lib.fmm_plan_get_cells.argtypes = [_vp] + [_vp] * 8
+lib.fmm_plan_get_lists.argtypes = [_vp, _vp, _vp]
+
+
+def _strerror(code):
+    return lib.fmm_strerror(code).decode()
+
+
+def _check(code, what):
+    if code != FMM_OK:
+        raise FmmError(code, what)
+
+
+def _dptr(t, n=None, name="array"):
+    """Device pointer of a float32 contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float32":
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """An FMM plan (tree, lists and expansions resident on the device)."""
+
+    def __init__(self, n_max, params=None, **kw):
+        self.params = params if params is not None else Params.default(**kw)
+        h = _vp()
+        _check(lib.fmm_plan_create(ctypes.byref(self.params), int(n_max), ctypes.byref(h)),
+               "fmm_plan_create")
+        self._h = h
+        self.n_max = int(n_max)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fmm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None):
+        """fmm_eval_velocity_stretching on torch CUDA tensors; returns (vel, dgamma)."""
+        import torch
+        n = pos.shape[0]
+        if vel is None:
+            vel = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        if dgamma is None:
+            dgamma = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        _check(lib.fmm_eval_velocity_stretching(
+            self._h, n, _dptr(pos, name="pos"), _dptr(gamma, name="gamma"), _dptr(sigma, name="sigma"),
+            float(sigma_uniform), _dptr(vel, name="vel"), _dptr(dgamma, name="dgamma"),
+            _stream_ptr(stream)), "fmm_eval_velocity_stretching")
+        return vel, dgamma
+
+    def eval_host(self, pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None):
+        """fmm_eval_velocity_stretching_host on numpy float32 arrays (synchronous)."""
+        import numpy as np
+        n = pos.shape[0]
+        for a in (pos, gamma) + ((sigma,) if sigma is not None else ()):
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+        if vel is None:
+            vel = np.empty((n, 3), np.float32)
+        if dgamma is None:
+            dgamma = np.empty((n, 3), np.float32)
+        _check(lib.fmm_eval_velocity_stretching_host(
+            self._h, n, pos.ctypes.data, gamma.ctypes.data,
+            sigma.ctypes.data if sigma is not None else None, float(sigma_uniform),
+            vel.ctypes.data, dgamma.ctypes.data, _stream_ptr(stream)), "fmm_eval_velocity_stretching_host")
+        return vel, dgamma
+
+    def set_timing(self, on=True):
+        _check(lib.fmm_plan_set_timing(self._h, 1 if on else 0), "fmm_plan_set_timing")
+
+    def stats(self):
+        s = Stats()
+        _check(lib.fmm_plan_get_stats(self._h, ctypes.byref(s)), "fmm_plan_get_stats")
+        return s
+
+    def order(self):
+        import numpy as np
+        n = self.stats().n
+        o = np.zeros(n, np.uint32)
+        k = np.zeros(n, np.uint64)
+        _check(lib.fmm_plan_get_order(self._h, o.ctypes.data, k.ctypes.data), "fmm_plan_get_order")
+        return o, k
+
+    def cells(self):
+        import numpy as np
+        nc = self.stats().ncells
+        a = {k: np.zeros(nc, np.int32) for k in ("begin", "end", "level", "parent", "child_begin", "nchild")}
+        a["center"] = np.zeros((nc, 3), np.float64)
+        a["radius"] = np.zeros(nc, np.float64)
+        _check(lib.fmm_plan_get_cells(self._h, *[a[k].ctypes.data for k in
+                                                 ("begin", "end", "level", "parent", "child_begin", "nchild",
+                                                  "center", "radius")]), "fmm_plan_get_cells")
+        return a
+
+    def lists(self):
+        import numpy as np
+        s = self.stats()
+        p2p = np.zeros((s.p2p_cell_pairs, 3), np.int32)
+        m2l = np.zeros((s.m2l_pairs, 3), np.int32)
+        _check(lib.fmm_plan_get_lists(self._h, p2p.ctypes.data, m2l.ctypes.data), "fmm_plan_get_lists")
+        return p2p, m2l
+
+
+def direct(pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None):
+    """fmm_direct_velocity_stretching: all pairs on the device (O(n^2))."""
+    import torch
+    n = pos.shape[0]
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+    if dgamma is None:
+        dgamma = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+    _check(lib.fmm_direct_velocity_stretching(n, _dptr(pos, name="pos"), _dptr(gamma, name="gamma"),
+                                              _dptr(sigma, name="sigma"), float(sigma_uniform),
+                                              _dptr(vel, name="vel"), _dptr(dgamma, name="dgamma"),
+                                              _stream_ptr(stream)), "fmm_direct_velocity_stretching")
+    return vel, dgamma

@@ -1,0 +1,136 @@
+// Plan structure and the host-side entry points of each translation unit.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "harmonics.cuh"
+#include "primitives.cuh"
+
+// Layout of the small device scalar block (doubles).
+namespace fmm {
+constexpr int kScalBox = 0;     // box_min[3], box_len
+constexpr int kScalDipole = 4;  // dipole velocity correction [3] (double)
+constexpr int kScalSigma = 8;   // float bits of max sigma (per-particle sigma)
+constexpr int kScalCount = 16;  // u32 counters area
+}  // namespace fmm
+
+// Plan: parameters, constant operator tables, and the grow-only workspace.
+struct fmm_plan_s {
+  fmm_params prm;
+  int64_t n_max = 0;
+  int P = 0;      // p^2 real coefficients per potential
+  int Kpad = 0;   // P rounded up to a multiple of 16 (tensor-core K)
+  int device = 0;
+  int timing = 0;
+  int tc_ok = 0;  // tensor-core M2L usable for this p
+  // constant operator tables (device)
+  fmm::DBuf m2m_T;    // [8][P(k)][P(r)] FP32 transposed M2M matrices by child octant
+  fmm::DBuf l2l_T;    // [8][P(k)][P(r)] FP32 transposed L2L matrices by child octant
+  fmm::DBuf l2p_w;    // [5][P] FP32 L2P weights
+  fmm::DBuf lattice;  // [P][P] FP64 periodic lattice operator (row = output)
+  // particles
+  fmm::DBuf keys0, keys1, vals0, vals1;  // radix sort ping-pong
+  uint64_t* skeys = nullptr;             // sorted keys (points into keys0/keys1)
+  uint32_t* sidx = nullptr;              // sorted position -> input index
+  fmm::DBuf sortA, sortB;                // float4 (x,y,z,sigma), (gx,gy,gz,0) in sorted order
+  fmm::DBuf far_u, far_s;                // [n][3] far field, sorted order
+  fmm::DBuf leaf_of;                     // [n]
+  fmm::DBuf in_pos, in_gam, in_sig, out_vel, out_dg;  // staging of the _host entry point
+  // cells
+  fmm::DBuf c_begin, c_end, c_level, c_parent, c_child, c_nchild;  // int32
+  fmm::DBuf c_key;                                                  // u64 level-local Morton index
+  fmm::DBuf c_center, c_radius2, c_radius;                          // double[3], u64 bits, double
+  fmm::DBuf c_tile;                                                 // int32 tile*64+slot
+  fmm::DBuf leaves;                                                 // leaf cell ids
+  fmm::DBuf M, L;                                                   // [cells][3][P] FP32
+  fmm::DBuf Mbf;                                                    // [cells][2][3][Kpad] BF16 hi/lo
+  // traversal
+  fmm::DBuf fr0, fr1;                                 // frontier int4 (a,b,o,0)
+  fmm::DBuf tcount, tmask, tscan0, tscan1, tscan2;    // per-item scratch
+  fmm::DBuf p2p_raw, m2l_raw;                         // int4 (a,b,o,0)
+  fmm::DBuf lk0, lk1, lv0, lv1;                       // list sort ping-pong
+  fmm::DBuf p2p_sorted, p2p_off;                      // int2 (b,o) by leaf, CSR offsets per leaf
+  fmm::DBuf m2l_key, m2l_slot, ukeys;                 // per pair key, slot; unique keys
+  fmm::DBuf T32, Tbf;                                 // M2L operators
+  fmm::DBuf st_tile, st_slot, st_src, tile_range;     // M2L steps
+  // scratch
+  fmm::DBuf scan_tmp, sort_hist;
+  fmm::DBuf scal;   // small scalars (see kScal*)
+  fmm::DBuf flags;  // int error flags
+  void* pinned = nullptr;  // host pinned scratch (counts)
+  // host mirror of the last tree / lists
+  std::vector<int> level_begin;  // cells of level l: [level_begin[l], level_begin[l+1])
+  std::vector<int> tile_begin;   // tiles of level l: [tile_begin[l], tile_begin[l+1])
+  int64_t ncells = 0, nleaves = 0, ntiles = 0;
+  int nlevels = 0;
+  int64_t n_p2p = 0, n_m2l = 0, n_keys = 0, n_steps = 0, p2p_pairs = 0;
+  int64_t last_n = 0;
+  int last_tc = 0;
+  fmm_stats stats;
+  cudaEvent_t ev[8];
+  int have_events = 0;
+};
+
+namespace fmm {
+// tree.cu
+int grow_cells(fmm_plan p, int64_t need, cudaStream_t s);
+int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u,
+               cudaStream_t s);
+// operators.cu
+int build_constant_operators(fmm_plan p);
+int build_m2l_operators(fmm_plan p, cudaStream_t s);
+int apply_lattice(fmm_plan p, cudaStream_t s);
+// upward.cu
+int upward_pass(fmm_plan p, cudaStream_t s);
+// traverse.cu
+int traverse(fmm_plan p, double sigma_max_host, cudaStream_t s);
+// m2l.cu
+int m2l_simt(fmm_plan p, cudaStream_t s);
+int m2l_tensor(fmm_plan p, cudaStream_t s);
+// downward.cu
+int downward_pass(fmm_plan p, int64_t n, cudaStream_t s);
+// p2p.cu
+int p2p_near(fmm_plan p, int64_t n, float sig_u, int per_particle_sigma, float* vel, float* dg, cudaStream_t s);
+int p2p_direct_all(int64_t n, const float* pos, const float* gam, const float* sig, float sig_u, float* vel,
+                   float* dg, cudaStream_t s);
+}  // namespace fmm
+
+namespace fmm {
+// M2L translation key (level-independent thanks to the cell-size scaling):
+// delta = level(target) - level(source); t = 2 (c_t - c_s - o L) / a_f with
+// a_f the side of the finer of the two cells (an integer vector).
+// Bits: [57,63) delta+32, [38,57) tx, [19,38) ty, [0,19) tz (two's complement).
+constexpr int kKeyBits = 19;
+constexpr long long kKeyLim = (1ll << (kKeyBits - 1)) - 1;
+
+__host__ __device__ inline uint64_t m2l_key_encode(int delta, long long tx, long long ty, long long tz) {
+  const uint64_t mask = (1ull << kKeyBits) - 1ull;
+  return ((uint64_t)(delta + 32) << 57) | (((uint64_t)tx & mask) << 38) | (((uint64_t)ty & mask) << 19) |
+         ((uint64_t)tz & mask);
+}
+
+__host__ __device__ inline long long key_field(uint64_t key, int shift) {
+  long long v = (long long)((key >> shift) & ((1ull << kKeyBits) - 1ull));
+  if (v >= (1ll << (kKeyBits - 1))) v -= (1ll << kKeyBits);
+  return v;
+}
+
+// delta and tau = (c_t - c_s)/a_t (target-cell units); a_s/a_t = 2^delta.
+__host__ __device__ inline void m2l_key_decode(uint64_t key, int* delta, double tau[3]) {
+  int d = (int)(key >> 57) - 32;
+  *delta = d;
+  double f = 0.5 * (d < 0 ? ldexp(1.0, d) : 1.0);
+  tau[0] = (double)key_field(key, 38) * f;
+  tau[1] = (double)key_field(key, 19) * f;
+  tau[2] = (double)key_field(key, 0) * f;
+}
+
+// Level / tile layout of the current tree, passed to kernels by value.
+struct LevelInfo {
+  int nlevels;
+  int level_begin[kMaxLevel + 2];
+  int tile_begin[kMaxLevel + 2];
+};
+}  // namespace fmm

@@ -1,0 +1,272 @@
+// Translation operators as real matrices on the real-packed coefficients.
+//
+// Sec. 3.1: M2M, M2L, L2L of the spherical-harmonic Laplace expansions
+// (formulas in harmonics.cuh).  Octree children sit at beta = (+-1/2)^3 in
+// child units with scale ratio 1/2, so M2M and L2L reduce to 8 fixed matrices
+// per p, built here once in FP64 on the host.  Each distinct M2L translation
+// (level difference, offset; see m2l_key_* in traverse.cu) becomes one P x P
+// matrix built in FP64 on the device per evaluation.  The periodic far field
+// (Sec. 3.5) is one FP64 P x P operator on the root multipole: images-1
+// rings of 702 super-cells, each ring the M2L sum from offsets
+// {-4..4}^3 \ {-1..1}^3, the next super-cell the M2M sum of 27 copies.
+#include <complex>
+
+#include "fmm_internal.cuh"
+#include <cuda_bf16.h>
+
+namespace fmm {
+
+namespace {
+
+using Mat = std::vector<double>;
+
+// Y_n^m (m >= 0) += c * X_j^k  (conj_in: c * conj(X_j^k)), X_j^{-k} = (-1)^k conj(X_j^k).
+void add_term(Mat& A, int P, int n, int m, int j, int k, cd c, bool conj_in) {
+  int ak = k < 0 ? -k : k;
+  double sgn = (k < 0 && (ak & 1)) ? -1.0 : 1.0;
+  bool conj_total = (k < 0) != conj_in;
+  double br = conj_total ? -1.0 : 1.0;
+  cd ca = {c.re * sgn, c.im * sgn};
+  cd cb = {-c.im * sgn * br, c.re * sgn * br};
+  int row_re = ridx(n, m, 0);
+  int col_a = ridx(j, ak, 0);
+  A[(size_t)row_re * P + col_a] += ca.re;
+  if (m > 0) A[(size_t)ridx(n, m, 1) * P + col_a] += ca.im;
+  if (ak > 0) {
+    int col_b = ridx(j, ak, 1);
+    A[(size_t)row_re * P + col_b] += cb.re;
+    if (m > 0) A[(size_t)ridx(n, m, 1) * P + col_b] += cb.im;
+  }
+}
+
+Mat m2m_matrix(int p, const double beta[3], double ratio) {
+  const int P = p * p;
+  Mat A((size_t)P * P, 0.0);
+  std::vector<cd> R(kPMax * (kPMax + 1) / 2);
+  regular_table_d(beta[0], beta[1], beta[2], p, R.data());
+  for (int n = 0; n < p; ++n)
+    for (int m = 0; m <= n; ++m)
+      for (int k = 0; k <= n; ++k)
+        for (int l = -k; l <= k; ++l) {
+          if (std::abs(m - l) > n - k) continue;
+          double w = pow(ratio, n) * nu_d(n, m) / (nu_d(k, l) * nu_d(n - k, m - l));
+          cd c = cscale(cconj(harm_get(R.data(), k, l)), w);
+          add_term(A, P, n, m, n - k, m - l, c, false);
+        }
+  return A;
+}
+
+Mat l2l_matrix(int p, const double beta[3], double ratio) {
+  const int P = p * p;
+  Mat A((size_t)P * P, 0.0);
+  std::vector<cd> R(kPMax * (kPMax + 1) / 2);
+  regular_table_d(beta[0], beta[1], beta[2], p, R.data());
+  for (int n = 0; n < p; ++n)
+    for (int m = 0; m <= n; ++m)
+      for (int k = 0; k < p - n; ++k)
+        for (int l = -k; l <= k; ++l) {
+          if (std::abs(m + l) > n + k) continue;
+          double w = pow(ratio, n + k + 1) * nu_d(n + k, m + l) / (nu_d(n, m) * nu_d(k, l));
+          cd c = cscale(harm_get(R.data(), k, l), w);
+          add_term(A, P, n, m, n + k, m + l, c, false);
+        }
+  return A;
+}
+
+Mat m2l_matrix(int p, const double tau[3], double ratio) {
+  const int P = p * p;
+  Mat A((size_t)P * P, 0.0);
+  const int D = 2 * p - 1;
+  std::vector<cd> I(D * (D + 1) / 2);
+  irregular_table_d(tau[0], tau[1], tau[2], D, I.data());
+  for (int n = 0; n < p; ++n)
+    for (int m = 0; m <= n; ++m)
+      for (int j = 0; j < p; ++j)
+        for (int k = -j; k <= j; ++k) {
+          double w = ((n & 1) ? -1.0 : 1.0) * pow(ratio, j) / (nu_d(n, m) * nu_d(j, k));
+          cd c = cscale(cconj(harm_get(I.data(), j + n, k + m)), w);
+          add_term(A, P, n, m, j, k, c, true);
+        }
+  return A;
+}
+
+Mat matmul(const Mat& A, const Mat& B, int P) {
+  Mat C((size_t)P * P, 0.0);
+  for (int i = 0; i < P; ++i)
+    for (int k = 0; k < P; ++k) {
+      double a = A[(size_t)i * P + k];
+      if (a == 0.0) continue;
+      for (int j = 0; j < P; ++j) C[(size_t)i * P + j] += a * B[(size_t)k * P + j];
+    }
+  return C;
+}
+
+// Lattice operator: L~_root += A_lat M~_root (root side = box length).
+Mat lattice_matrix(int p, int images) {
+  const int P = p * p;
+  Mat A((size_t)P * P, 0.0);
+  Mat S((size_t)P * P, 0.0);  // M2M of level-(lev-1) super-cell from the root
+  for (int i = 0; i < P; ++i) S[(size_t)i * P + i] = 1.0;
+  // one-level super-cell M2M: 27 copies at offsets o (child units), ratio 1/3
+  Mat S3((size_t)P * P, 0.0);
+  for (int ox = -1; ox <= 1; ++ox)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int oz = -1; oz <= 1; ++oz) {
+        double b[3] = {(double)ox, (double)oy, (double)oz};
+        Mat T = m2m_matrix(p, b, 1.0 / 3.0);
+        for (size_t q = 0; q < T.size(); ++q) S3[q] += T[q];
+      }
+  double scale = 1.0;  // super-cell side / root side
+  for (int lev = 1; lev < images; ++lev) {
+    Mat ring((size_t)P * P, 0.0);
+    for (int ox = -4; ox <= 4; ++ox)
+      for (int oy = -4; oy <= 4; ++oy)
+        for (int oz = -4; oz <= 4; ++oz) {
+          if (std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz))) <= 1) continue;
+          double tau[3] = {-ox * scale, -oy * scale, -oz * scale};
+          Mat T = m2l_matrix(p, tau, scale);
+          for (size_t q = 0; q < T.size(); ++q) ring[q] += T[q];
+        }
+    Mat contrib = matmul(ring, S, P);
+    for (size_t q = 0; q < A.size(); ++q) A[q] += contrib[q];
+    S = matmul(S3, S, P);
+    scale *= 3.0;
+  }
+  return A;
+}
+
+// ---- device: M2L operator per translation key
+
+__global__ void k_build_m2l(const uint64_t* __restrict__ keys, int nkeys, int p, float* __restrict__ T32,
+                            __nv_bfloat16* __restrict__ Tbf, int tc) {
+  __shared__ cd I[(2 * kPMax - 1) * (2 * kPMax) / 2];
+  __shared__ double nu[kNCoefMax];
+  __shared__ double rp[kPMax];
+  __shared__ int nmp[kNCoefMax];  // real index -> (n, m, part) packed
+  const int key_id = blockIdx.x;
+  if (key_id >= nkeys) return;
+  const int P = p * p;
+  uint64_t key = keys[key_id];
+  int delta;
+  double tau[3];
+  m2l_key_decode(key, &delta, tau);
+  if (threadIdx.x == 0) irregular_table_d(tau[0], tau[1], tau[2], 2 * p - 1, I);
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    int n = (int)sqrtf((float)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    int o = r - n * n;
+    int m = (o + 1) / 2, part = (o == 0) ? 0 : ((o - 1) & 1);
+    nmp[r] = (n << 16) | (m << 8) | part;
+    nu[r] = nu_d(n, m);
+  }
+  if (threadIdx.x < (unsigned)p) rp[threadIdx.x] = ldexp(1.0, delta * (int)threadIdx.x);
+  __syncthreads();
+  for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+    int r = e / P, c = e % P;
+    int a = nmp[r], b = nmp[c];
+    int n = a >> 16, m = (a >> 8) & 0xff, po = a & 1;
+    int j = b >> 16, k = (b >> 8) & 0xff, pi = b & 1;
+    double s = ((n & 1) ? -1.0 : 1.0) * rp[j] / (nu[r] * nu[c]);
+    cd A = cconj(harm_get(I, j + n, k + m));
+    cd B = {0.0, 0.0};
+    if (k > 0) {
+      B = cconj(harm_get(I, j + n, m - k));
+      if (k & 1) B = {-B.re, -B.im};
+    }
+    double v;
+    if (pi == 0) v = po == 0 ? s * (A.re + B.re) : s * (A.im + B.im);
+    else v = po == 0 ? -s * (B.im - A.im) : s * (B.re - A.re);
+    T32[(size_t)key_id * P * P + e] = (float)v;
+    if (tc) {
+      __nv_bfloat16 hi = __double2bfloat16(v);
+      __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+      size_t base = (size_t)key_id * 2 * 128 * 128;
+      Tbf[base + (size_t)r * 128 + c] = hi;
+      Tbf[base + 128 * 128 + (size_t)r * 128 + c] = lo;
+    }
+  }
+}
+
+// zero padding of the BF16 operator tiles (rows >= P or cols >= P)
+__global__ void k_zero_bf(__nv_bfloat16* Tbf, int nkeys, int P) {
+  size_t total = (size_t)nkeys * 2 * 128 * 128;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int c = (int)(i % 128), r = (int)((i / 128) % 128);
+    if (r >= P || c >= P) Tbf[i] = __float2bfloat16(0.f);
+  }
+}
+
+__global__ void k_apply_lattice(const double* __restrict__ A, int P, float* __restrict__ L, const float* __restrict__ M) {
+  // root cell 0: L[0][c][r] += sum_k A[r][k] M[0][c][k]
+  for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) {
+    int c = e / P, r = e % P;
+    double acc = 0.0;
+    for (int k = 0; k < P; ++k) acc += A[(size_t)r * P + k] * (double)M[c * P + k];
+    L[c * P + r] += (float)acc;
+  }
+}
+
+}  // namespace
+
+int build_constant_operators(fmm_plan p) {
+  const int pp = p->prm.p, P = pp * pp;
+  std::vector<float> m2mT((size_t)8 * P * P), l2lT((size_t)8 * P * P);
+  for (int oct = 0; oct < 8; ++oct) {
+    double beta[3] = {(oct & 4) ? 0.5 : -0.5, (oct & 2) ? 0.5 : -0.5, (oct & 1) ? 0.5 : -0.5};
+    Mat A = m2m_matrix(pp, beta, 0.5);
+    Mat B = l2l_matrix(pp, beta, 0.5);
+    for (int r = 0; r < P; ++r)
+      for (int k = 0; k < P; ++k) {
+        m2mT[(size_t)oct * P * P + (size_t)k * P + r] = (float)A[(size_t)r * P + k];
+        l2lT[(size_t)oct * P * P + (size_t)k * P + r] = (float)B[(size_t)r * P + k];
+      }
+  }
+  FMM_TRY(p->m2m_T.ensure(m2mT.size() * sizeof(float)));
+  FMM_TRY(p->l2l_T.ensure(l2lT.size() * sizeof(float)));
+  FMM_CUDA_TRY(cudaMemcpy(p->m2m_T.ptr, m2mT.data(), m2mT.size() * sizeof(float), cudaMemcpyHostToDevice));
+  FMM_CUDA_TRY(cudaMemcpy(p->l2l_T.ptr, l2lT.data(), l2lT.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // L2P weights for the 5 outputs (n',m') in {(1,0),(1,1),(2,0),(2,1),(2,2)}
+  // over inputs (k,l), |l| <= k, index k^2 + k + l:  nu_{n'+k}^{m'+l} / nu_k^l
+  const int outs[5][2] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  std::vector<float> w((size_t)5 * P, 0.f);
+  for (int o = 0; o < 5; ++o)
+    for (int k = 0; k < pp; ++k)
+      for (int l = -k; l <= k; ++l) {
+        int n2 = outs[o][0], m2 = outs[o][1];
+        if (n2 + k > pp - 1 || std::abs(m2 + l) > n2 + k) continue;
+        w[(size_t)o * P + k * k + k + l] = (float)(nu_d(n2 + k, m2 + l) / nu_d(k, l));
+      }
+  FMM_TRY(p->l2p_w.ensure(w.size() * sizeof(float)));
+  FMM_CUDA_TRY(cudaMemcpy(p->l2p_w.ptr, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (p->prm.periodic) {
+    Mat A = lattice_matrix(pp, p->prm.images);
+    FMM_TRY(p->lattice.ensure(A.size() * sizeof(double)));
+    FMM_CUDA_TRY(cudaMemcpy(p->lattice.ptr, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return FMM_OK;
+}
+
+int build_m2l_operators(fmm_plan p, cudaStream_t s) {
+  const int P = p->P;
+  if (p->n_keys == 0) return FMM_OK;
+  FMM_TRY(p->T32.ensure((size_t)p->n_keys * P * P * sizeof(float)));
+  int tc = p->last_tc;
+  if (tc) {
+    FMM_TRY(p->Tbf.ensure((size_t)p->n_keys * 2 * 128 * 128 * sizeof(__nv_bfloat16)));
+    k_zero_bf<<<1024, 256, 0, s>>>(p->Tbf.as<__nv_bfloat16>(), (int)p->n_keys, P);
+  }
+  k_build_m2l<<<(unsigned)p->n_keys, 256, 0, s>>>(p->ukeys.as<uint64_t>(), (int)p->n_keys, p->prm.p,
+                                                   p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(), tc);
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+int apply_lattice(fmm_plan p, cudaStream_t s) {
+  if (!p->prm.periodic || p->prm.images <= 1) return FMM_OK;
+  k_apply_lattice<<<1, 512, 0, s>>>(p->lattice.as<double>(), p->P, p->L.as<float>(), p->M.as<float>());
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+}  // namespace fmm

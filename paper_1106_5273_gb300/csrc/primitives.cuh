@@ -1,0 +1,11 @@
+// Device-wide primitives: exclusive scan (u32) and stable LSD radix sort.
+#pragma once
+#include "common.cuh"
+
+namespace fmm {
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, DBuf& tmp,
+                       cudaStream_t s);
+int iota_u32(uint32_t* v, int64_t n, cudaStream_t s);
+int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bit_begin,
+                   int bit_end, int* in_second, DBuf& hist, DBuf& scan_tmp, cudaStream_t s);
+}  // namespace fmm

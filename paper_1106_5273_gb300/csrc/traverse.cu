@@ -1,0 +1,430 @@
+// Dual-tree traversal (Sec. 3.3, Algorithms 1-2) and list grouping.
+//
+// Algorithm 1 pops a pair (A, B), splits the cell with the larger radius
+// (B on a tie; the other one when that cell is a leaf) and calls Algorithm 2
+// on every child pair: M2L if the FMM MAC holds (R_A + R_B < theta |X_A-X_B|)
+// and the pair is at least k_sigma sigma_max apart (the far field uses the
+// singular kernel), else P2P if both are leaves, else push.  Here the stack
+// is a breadth-first frontier processed in two passes (classify, scan, emit),
+// so the emitted lists have a fixed order.  Periodic: the traversal starts
+// from (root, root + o L) for the 27 o in {-1,0,1}^3.  The MAC is evaluated
+// in FP64 with explicitly rounded operations in a fixed order.
+//
+// Outputs: P2P entries grouped by target leaf (CSR), and M2L entries grouped
+// into steps = (tile of 64 consecutive target cells of one level, translation
+// key), each step carrying the source cell of every tile slot (or -1).
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+struct TravArgs {
+  const double* center;
+  const double* radius;
+  const int* nchild;
+  const int* child;
+  double theta, ksig, smax, blen;
+};
+
+__device__ inline int interact(const TravArgs& t, int a, int b, int o) {
+  double sh[3] = {(double)(o / 9 - 1) * t.blen, (double)((o / 3) % 3 - 1) * t.blen, (double)(o % 3 - 1) * t.blen};
+  double d2 = 0.0;
+  double dx = __dsub_rn(t.center[3 * a], __dadd_rn(t.center[3 * b], sh[0]));
+  double dy = __dsub_rn(t.center[3 * a + 1], __dadd_rn(t.center[3 * b + 1], sh[1]));
+  double dz = __dsub_rn(t.center[3 * a + 2], __dadd_rn(t.center[3 * b + 2], sh[2]));
+  d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  double dist = __dsqrt_rn(d2);
+  double sr = __dadd_rn(t.radius[a], t.radius[b]);
+  if (sr < __dmul_rn(t.theta, dist) && __dsub_rn(dist, sr) >= __dmul_rn(t.ksig, t.smax)) return 0;  // M2L
+  if (t.nchild[a] == 0 && t.nchild[b] == 0) return 1;                                                // P2P
+  return 2;                                                                                          // push
+}
+
+// Initial pairs (root, root + o L), one thread, in image order.
+__global__ void k_trav_init(TravArgs t, int nimg, int img0, int4* fr, int4* m2l, int4* p2p, uint32_t* cnt) {
+  if (threadIdx.x || blockIdx.x) return;
+  uint32_t nm = 0, np = 0, nf = 0;
+  for (int q = 0; q < nimg; ++q) {
+    int o = img0 + q;
+    int ty = interact(t, 0, 0, o);
+    int4 v = make_int4(0, 0, o, 0);
+    if (ty == 0) m2l[nm++] = v;
+    else if (ty == 1) p2p[np++] = v;
+    else fr[nf++] = v;
+  }
+  cnt[0] = nm;
+  cnt[1] = np;
+  cnt[2] = nf;
+}
+
+__device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, int& c0, int& nc) {
+  split_a = t.radius[a] > t.radius[b];
+  if (split_a && t.nchild[a] == 0) split_a = false;
+  else if (!split_a && t.nchild[b] == 0) split_a = true;
+  int s = split_a ? a : b;
+  c0 = t.child[s];
+  nc = t.nchild[s];
+}
+
+__global__ void k_trav_classify(TravArgs t, const int4* __restrict__ fr, int nfr, uint32_t* __restrict__ mask,
+                                uint32_t* __restrict__ cm, uint32_t* __restrict__ cp, uint32_t* __restrict__ cf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfr) return;
+  int4 pr = fr[i];
+  bool sa;
+  int c0, nc;
+  split_of(t, pr.x, pr.y, sa, c0, nc);
+  uint32_t msk = 0, nm = 0, np = 0, nf = 0;
+  for (int q = 0; q < nc; ++q) {
+    int c = c0 + q;
+    int ty = sa ? interact(t, c, pr.y, pr.z) : interact(t, pr.x, c, pr.z);
+    msk |= (uint32_t)ty << (2 * q);
+    nm += ty == 0;
+    np += ty == 1;
+    nf += ty == 2;
+  }
+  mask[i] = msk;
+  cm[i] = nm;
+  cp[i] = np;
+  cf[i] = nf;
+}
+
+__global__ void k_trav_emit(TravArgs t, const int4* __restrict__ fr, int nfr, const uint32_t* __restrict__ mask,
+                            const uint32_t* __restrict__ om, const uint32_t* __restrict__ op,
+                            const uint32_t* __restrict__ of, uint32_t bm, uint32_t bp, int4* __restrict__ m2l,
+                            int4* __restrict__ p2p, int4* __restrict__ nfrontier) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nfr) return;
+  int4 pr = fr[i];
+  bool sa;
+  int c0, nc;
+  split_of(t, pr.x, pr.y, sa, c0, nc);
+  uint32_t msk = mask[i];
+  uint32_t im = bm + om[i], ip = bp + op[i], iff = of[i];
+  for (int q = 0; q < nc; ++q) {
+    int c = c0 + q;
+    int4 v = sa ? make_int4(c, pr.y, pr.z, 0) : make_int4(pr.x, c, pr.z, 0);
+    int ty = (msk >> (2 * q)) & 3;
+    if (ty == 0) m2l[im++] = v;
+    else if (ty == 1) p2p[ip++] = v;
+    else nfrontier[iff++] = v;
+  }
+}
+
+// ---- P2P CSR
+
+__global__ void k_p2p_keys(const int4* __restrict__ raw, int n, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = (uint64_t)raw[i].x;
+  vals[i] = (uint32_t)i;
+}
+
+__global__ void k_p2p_gather(const int4* __restrict__ raw, const uint32_t* __restrict__ order, int n,
+                             int2* __restrict__ out, const int* __restrict__ begin, const int* __restrict__ end,
+                             unsigned long long* __restrict__ pairs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cnt = 0;
+  if (i < n) {
+    int4 v = raw[order[i]];
+    out[i] = make_int2(v.y, v.z);
+    cnt = (unsigned long long)(end[v.x] - begin[v.x]) * (unsigned long long)(end[v.y] - begin[v.y]);
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(pairs, cnt);
+}
+
+__device__ inline int lower_bound_key(const uint64_t* a, int n, uint64_t v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_p2p_offsets(const int* __restrict__ leaves, int nl, const uint64_t* __restrict__ skeys, int n,
+                              int2* __restrict__ off) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nl) return;
+  uint64_t a = (uint64_t)leaves[i];
+  off[i] = make_int2(lower_bound_key(skeys, n, a), lower_bound_key(skeys, n, a + 1));
+}
+
+// ---- M2L steps
+
+__device__ inline void cell_ijk(uint64_t key, long long ijk[3]) {
+  uint64_t k = key;
+  long long r[3] = {0, 0, 0};
+  for (int b = 0; b < kMaxLevel; ++b) {
+    r[0] |= (long long)((k >> (3 * b + 2)) & 1ull) << b;
+    r[1] |= (long long)((k >> (3 * b + 1)) & 1ull) << b;
+    r[2] |= (long long)((k >> (3 * b)) & 1ull) << b;
+  }
+  ijk[0] = r[0];
+  ijk[1] = r[1];
+  ijk[2] = r[2];
+}
+
+__global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __restrict__ level,
+                           const uint64_t* __restrict__ ckey, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int4 v = raw[i];
+  int la = level[v.x], lb = level[v.y];
+  int lf = la > lb ? la : lb;
+  long long ia[3], ib[3];
+  cell_ijk(ckey[v.x], ia);
+  cell_ijk(ckey[v.y], ib);
+  int o[3] = {v.z / 9 - 1, (v.z / 3) % 3 - 1, v.z % 3 - 1};
+  long long t[3];
+  bool ok = true;
+  for (int q = 0; q < 3; ++q) {
+    t[q] = (2 * ia[q] + 1) * (1ll << (lf - la)) - (2 * ib[q] + 1) * (1ll << (lf - lb)) - (long long)o[q] * (1ll << (lf + 1));
+    if (t[q] > kKeyLim || t[q] < -kKeyLim) ok = false;
+  }
+  if (!ok) atomicExch(flag, FMM_E_DEPTH);
+  keys[i] = m2l_key_encode(la - lb, t[0], t[1], t[2]);
+  vals[i] = (uint32_t)i;
+}
+
+__global__ void k_unique_flags(const uint64_t* __restrict__ k, int n, uint32_t* __restrict__ f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_unique_write(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
+                               const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
+                               uint64_t* __restrict__ ukeys, uint32_t* __restrict__ slot_of_pair) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t s = e[i] + f[i] - 1u;
+  if (f[i]) ukeys[s] = k[i];
+  slot_of_pair[idx[i]] = s;
+}
+
+__global__ void k_cell_tiles(LevelInfo li, int nc, int* __restrict__ ctile) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  int l = 0;
+  while (l + 1 < li.nlevels && li.level_begin[l + 1] <= c) ++l;
+  int r = c - li.level_begin[l];
+  ctile[c] = (li.tile_begin[l] + r / kTile) * kTile + r % kTile;
+}
+
+__global__ void k_step_keys(const int4* __restrict__ raw, int n, const int* __restrict__ ctile,
+                            const uint32_t* __restrict__ slot, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int ts = ctile[raw[i].x];
+  uint64_t tile = (uint64_t)(ts / kTile), s_in = (uint64_t)(ts % kTile);
+  keys[i] = (tile << 26) | ((uint64_t)slot[i] << 6) | s_in;
+  vals[i] = (uint32_t)i;
+}
+
+__global__ void k_step_flags(const uint64_t* __restrict__ k, int n, uint32_t* __restrict__ f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = (i == 0 || (k[i] >> 6) != (k[i - 1] >> 6)) ? 1u : 0u;
+}
+
+__global__ void k_step_write(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
+                             const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
+                             const int4* __restrict__ raw, int* __restrict__ st_tile, int* __restrict__ st_slot,
+                             int* __restrict__ st_src) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t s = e[i] + f[i] - 1u;
+  uint64_t key = k[i];
+  if (f[i]) {
+    st_tile[s] = (int)(key >> 26);
+    st_slot[s] = (int)((key >> 6) & 0xfffffull);
+  }
+  st_src[(size_t)s * kTile + (key & 63ull)] = raw[idx[i]].y;
+}
+
+__global__ void k_tile_ranges(const int* __restrict__ st_tile, int ns, int2* __restrict__ tr) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  int t = st_tile[s];
+  if (s == 0 || st_tile[s - 1] != t) tr[t].x = s;
+  if (s == ns - 1 || st_tile[s + 1] != t) tr[t].y = s + 1;
+}
+
+int bits_for(int64_t v) {
+  int b = 1;
+  while (b < 63 && (1ll << b) <= v) ++b;
+  return (b + 7) / 8 * 8;
+}
+
+}  // namespace
+
+int traverse(fmm_plan p, double smax, cudaStream_t s) {
+  const int T = 256;
+  const int nc = (int)p->ncells;
+  TravArgs ta;
+  ta.center = p->c_center.as<double>();
+  ta.radius = p->c_radius.as<double>();
+  ta.nchild = p->c_nchild.as<int>();
+  ta.child = p->c_child.as<int>();
+  ta.theta = (double)p->prm.theta;
+  ta.ksig = (double)p->prm.sigma_sep;
+  ta.smax = smax;
+  ta.blen = p->prm.periodic ? p->prm.box_len : 0.0;
+  const int nimg = p->prm.periodic ? 27 : 1;
+  const int img0 = p->prm.periodic ? 0 : kImageZero;
+  uint32_t* hc = reinterpret_cast<uint32_t*>(p->pinned);
+  uint32_t* dcnt = reinterpret_cast<uint32_t*>(p->scal.as<double>() + kScalCount);
+
+  int64_t cap_fr = std::max<int64_t>(1024, 16 * (int64_t)nc);
+  int64_t cap_m = std::max<int64_t>(1024, 64 * (int64_t)nc);
+  int64_t cap_p = std::max<int64_t>(1024, 32 * (int64_t)nc);
+  FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
+  FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
+  FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int4), s));
+  FMM_TRY(p->p2p_raw.grow_copy(cap_p * sizeof(int4), s));
+  k_trav_init<<<1, 1, 0, s>>>(ta, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(), p->p2p_raw.as<int4>(), dcnt);
+  FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t nm = hc[0], np = hc[1], nf = hc[2];
+  fmm::DBuf* cur = &p->fr0;
+  fmm::DBuf* nxt = &p->fr1;
+  while (nf > 0) {
+    FMM_TRY(p->tmask.ensure((nf + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->tcount.ensure((nf + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->tscan0.ensure((nf + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->tscan1.ensure((nf + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->tscan2.ensure((nf + 1) * sizeof(uint32_t)));
+    unsigned g = (unsigned)((nf + T - 1) / T);
+    uint32_t* cm = p->tscan0.as<uint32_t>();
+    uint32_t* cp = p->tscan1.as<uint32_t>();
+    uint32_t* cf = p->tscan2.as<uint32_t>();
+    k_trav_classify<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf);
+    FMM_TRY(exclusive_scan_u32(cm, cm, nf, dcnt + 0, p->scan_tmp, s));
+    FMM_TRY(exclusive_scan_u32(cp, cp, nf, dcnt + 1, p->scan_tmp, s));
+    FMM_TRY(exclusive_scan_u32(cf, cf, nf, dcnt + 2, p->scan_tmp, s));
+    FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t am = hc[0], ap = hc[1], af = hc[2];
+    FMM_TRY(p->m2l_raw.grow_copy((nm + am) * sizeof(int4), s));
+    FMM_TRY(p->p2p_raw.grow_copy((np + ap) * sizeof(int4), s));
+    FMM_TRY(nxt->ensure((af + 1) * sizeof(int4)));
+    k_trav_emit<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf, (uint32_t)nm,
+                                (uint32_t)np, p->m2l_raw.as<int4>(), p->p2p_raw.as<int4>(), nxt->as<int4>());
+    FMM_CUDA_TRY(cudaGetLastError());
+    nm += am;
+    np += ap;
+    nf = af;
+    std::swap(cur, nxt);
+    if (nm > 0x7fffffff || np > 0x7fffffff) return FMM_E_CAPACITY;
+  }
+  p->n_m2l = nm;
+  p->n_p2p = np;
+
+  // ---- P2P: group by target leaf
+  {
+    const int n = (int)np;
+    FMM_TRY(p->lk0.ensure((n + 1) * sizeof(uint64_t)));
+    FMM_TRY(p->lk1.ensure((n + 1) * sizeof(uint64_t)));
+    FMM_TRY(p->lv0.ensure((n + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->lv1.ensure((n + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->p2p_sorted.ensure((n + 1) * sizeof(int2)));
+    FMM_TRY(p->p2p_off.ensure((p->nleaves + 1) * sizeof(int2)));
+    unsigned g = (unsigned)((n + T - 1) / T);
+    k_p2p_keys<<<g, T, 0, s>>>(p->p2p_raw.as<int4>(), n, p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
+    int second = 0;
+    FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                           p->lv1.as<uint32_t>(), n, 0, bits_for(nc), &second, p->sort_hist, p->scan_tmp, s));
+    uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
+    uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+    unsigned long long* dpairs = reinterpret_cast<unsigned long long*>(p->scal.as<double>() + kScalCount + 2);
+    FMM_CUDA_TRY(cudaMemsetAsync(dpairs, 0, sizeof(unsigned long long), s));
+    k_p2p_gather<<<g, T, 0, s>>>(p->p2p_raw.as<int4>(), sv, n, p->p2p_sorted.as<int2>(), p->c_begin.as<int>(),
+                                 p->c_end.as<int>(), dpairs);
+    k_p2p_offsets<<<(unsigned)((p->nleaves + T - 1) / T), T, 0, s>>>(p->leaves.as<int>(), (int)p->nleaves, sk, n,
+                                                                     p->p2p_off.as<int2>());
+    FMM_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(p->pinned) + 64, dpairs, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+  }
+
+  // ---- M2L: keys, unique operators, steps per (tile, key)
+  {
+    const int n = (int)nm;
+    // tiles of 64 consecutive cells per level
+    LevelInfo li;
+    li.nlevels = p->nlevels;
+    p->tile_begin.assign(p->nlevels + 1, 0);
+    for (int l = 0; l < p->nlevels; ++l) {
+      li.level_begin[l] = p->level_begin[l];
+      li.tile_begin[l] = p->tile_begin[l];
+      int cnt = p->level_begin[l + 1] - p->level_begin[l];
+      p->tile_begin[l + 1] = p->tile_begin[l] + (cnt + kTile - 1) / kTile;
+    }
+    li.level_begin[p->nlevels] = p->level_begin[p->nlevels];
+    li.tile_begin[p->nlevels] = p->tile_begin[p->nlevels];
+    p->ntiles = p->tile_begin[p->nlevels];
+    FMM_TRY(p->c_tile.ensure((nc + 1) * sizeof(int)));
+    k_cell_tiles<<<(unsigned)((nc + T - 1) / T), T, 0, s>>>(li, nc, p->c_tile.as<int>());
+    FMM_TRY(p->tile_range.ensure((p->ntiles + 1) * sizeof(int2)));
+    FMM_CUDA_TRY(cudaMemsetAsync(p->tile_range.ptr, 0, (p->ntiles + 1) * sizeof(int2), s));
+    p->n_keys = 0;
+    p->n_steps = 0;
+    if (n > 0) {
+      FMM_TRY(p->lk0.ensure((n + 1) * sizeof(uint64_t)));
+      FMM_TRY(p->lk1.ensure((n + 1) * sizeof(uint64_t)));
+      FMM_TRY(p->lv0.ensure((n + 1) * sizeof(uint32_t)));
+      FMM_TRY(p->lv1.ensure((n + 1) * sizeof(uint32_t)));
+      FMM_TRY(p->m2l_slot.ensure((n + 1) * sizeof(uint32_t)));
+      FMM_TRY(p->tcount.ensure((n + 1) * sizeof(uint32_t)));
+      FMM_TRY(p->tscan0.ensure((n + 1) * sizeof(uint32_t)));
+      FMM_TRY(p->ukeys.ensure((n + 1) * sizeof(uint64_t)));
+      unsigned g = (unsigned)((n + T - 1) / T);
+      int* flag = p->flags.as<int>();
+      k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_key.as<uint64_t>(),
+                                 p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), flag);
+      int second = 0;
+      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                             p->lv1.as<uint32_t>(), n, 0, 64, &second, p->sort_hist, p->scan_tmp, s));
+      uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
+      uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      k_unique_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
+      FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
+      k_unique_write<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
+                                     p->ukeys.as<uint64_t>(), p->m2l_slot.as<uint32_t>());
+      FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA_TRY(cudaStreamSynchronize(s));
+      p->n_keys = hc[0];
+      if (p->n_keys >= (1 << 20)) return FMM_E_CAPACITY;
+      // steps
+      k_step_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_tile.as<int>(), p->m2l_slot.as<uint32_t>(),
+                                  p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
+      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                             p->lv1.as<uint32_t>(), n, 0, 26 + bits_for(p->ntiles), &second, p->sort_hist,
+                             p->scan_tmp, s));
+      sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
+      sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      k_step_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
+      FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
+      FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA_TRY(cudaStreamSynchronize(s));
+      p->n_steps = hc[0];
+      FMM_TRY(p->st_tile.ensure((p->n_steps + 1) * sizeof(int)));
+      FMM_TRY(p->st_slot.ensure((p->n_steps + 1) * sizeof(int)));
+      FMM_TRY(p->st_src.ensure((p->n_steps + 1) * kTile * sizeof(int)));
+      FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (p->n_steps + 1) * kTile * sizeof(int), s));
+      k_step_write<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
+                                   p->m2l_raw.as<int4>(), p->st_tile.as<int>(), p->st_slot.as<int>(),
+                                   p->st_src.as<int>());
+      k_tile_ranges<<<(unsigned)((p->n_steps + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)p->n_steps,
+                                                                       p->tile_range.as<int2>());
+      FMM_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  p->p2p_pairs = (int64_t) * reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(p->pinned) + 64);
+  return FMM_OK;
+}
+
+}  // namespace fmm

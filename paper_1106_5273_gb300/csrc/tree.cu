@@ -1,0 +1,386 @@
+// Morton keys, sort, octree build, cell centres and radii (Sec. 3.2).
+//
+// Keys: positions normalised into the cube in FP64, 21 bits per axis
+// interleaved (bit b of x, y, z at 3b+2, 3b+1, 3b), stable LSD radix sort of
+// (key, index).  Cells: level by level, a cell splits while it holds more than
+// ncrit particles and its level is below 21; children are the non-empty
+// octants in digit order, so every level is stored in Morton order.
+// Expansion centre = geometric cube centre, radius = largest FP64 distance
+// from the centre to a particle of the cell.  Every FP64 expression uses
+// explicitly rounded operations (no contraction) in a fixed order, so the MAC
+// decisions built on them are reproducible.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+__global__ void k_bbox_partial(const float* __restrict__ pos, int64_t n, double* __restrict__ part) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = (double)pos[3 * i + a];
+      lo[a] = fmin(lo[a], v);
+      hi[a] = fmax(hi[a], v);
+    }
+  }
+  __shared__ double s[6][256];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s[a][threadIdx.x] = lo[a];
+    s[3 + a][threadIdx.x] = hi[a];
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        s[a][threadIdx.x] = fmin(s[a][threadIdx.x], s[a][threadIdx.x + o]);
+        s[3 + a][threadIdx.x] = fmax(s[3 + a][threadIdx.x], s[3 + a][threadIdx.x + o]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Free-space cube: centre of the bounding box, half side = longest extent/2
+// times (1 + 2^-10) (0.5 if all points coincide).
+__global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ box) {
+  if (threadIdx.x != 0) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int b = 0; b < nb; ++b)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], part[b * 6 + a]);
+      hi[a] = fmax(hi[a], part[b * 6 + 3 + a]);
+    }
+  double ext = 0.0;
+  for (int a = 0; a < 3; ++a) ext = fmax(ext, __dsub_rn(hi[a], lo[a]));
+  double half = __dmul_rn(__dmul_rn(ext, 0.5), 1.0 + 0.0009765625);
+  if (half == 0.0) half = 0.5;
+  for (int a = 0; a < 3; ++a) box[a] = __dsub_rn(__dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5), half);
+  box[3] = __dmul_rn(half, 2.0);
+}
+
+__global__ void k_set_box(double x, double y, double z, double len, double* box) {
+  box[0] = x;
+  box[1] = y;
+  box[2] = z;
+  box[3] = len;
+}
+
+__device__ inline uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffull;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ inline uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
+__device__ inline uint64_t quantize_axis(float x, double bmin, double blen) {
+  double u = __ddiv_rn(__dsub_rn((double)x, bmin), blen);
+  double k = floor(__dmul_rn(u, 2097152.0));
+  if (!(k >= 0.0)) k = 0.0;
+  if (k > 2097151.0) k = 2097151.0;
+  return (uint64_t)k;
+}
+
+__global__ void k_keys(const float* __restrict__ pos, int64_t n, const double* __restrict__ box,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double blen = box[3];
+  uint64_t kx = quantize_axis(pos[3 * i + 0], box[0], blen);
+  uint64_t ky = quantize_axis(pos[3 * i + 1], box[1], blen);
+  uint64_t kz = quantize_axis(pos[3 * i + 2], box[2], blen);
+  keys[i] = (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
+  idx[i] = (uint32_t)i;
+}
+
+__global__ void k_permute(const float* __restrict__ pos, const float* __restrict__ gam,
+                          const float* __restrict__ sig, float sig_u, const uint32_t* __restrict__ idx,
+                          int64_t n, float4* __restrict__ A, float4* __restrict__ B) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t j = idx[i];
+  float s = sig ? sig[j] : sig_u;
+  A[i] = make_float4(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], s);
+  B[i] = make_float4(gam[3 * j], gam[3 * j + 1], gam[3 * j + 2], 0.f);
+}
+
+__global__ void k_sigma_max(const float* __restrict__ sig, int64_t n, unsigned int* __restrict__ out) {
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, sig[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // sigma > 0: order of bits = order of values
+}
+
+__global__ void k_root(int n, int* begin, int* end, int* level, int* parent, uint64_t* key) {
+  begin[0] = 0;
+  end[0] = n;
+  level[0] = 0;
+  parent[0] = -1;
+  key[0] = 0;
+}
+
+__device__ inline int lower_bound_u64(const uint64_t* a, int lo, int hi, uint64_t v) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Child boundaries of cell c at level l (8 digits -> 9 bounds).
+__device__ inline void child_bounds(const uint64_t* skeys, int b, int e, uint64_t prefix, int l, int* bd) {
+  const int shift = 3 * (kMaxLevel - 1 - l);
+  bd[0] = b;
+  bd[8] = e;
+  for (int d = 1; d < 8; ++d) bd[d] = lower_bound_u64(skeys, b, e, ((prefix << 3) | (uint64_t)d) << shift);
+}
+
+__global__ void k_split_count(const uint64_t* __restrict__ skeys, const int* __restrict__ begin,
+                              const int* __restrict__ end, const uint64_t* __restrict__ key, int lb, int le,
+                              int l, int ncrit, uint32_t* __restrict__ cnt) {
+  int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= le) return;
+  int b = begin[c], e = end[c];
+  uint32_t k = 0;
+  if (e - b > ncrit && l < kMaxLevel) {
+    int bd[9];
+    child_bounds(skeys, b, e, key[c], l, bd);
+    for (int d = 0; d < 8; ++d) k += bd[d + 1] > bd[d] ? 1u : 0u;
+  }
+  cnt[c - lb] = k;
+}
+
+__global__ void k_split_write(const uint64_t* __restrict__ skeys, int* __restrict__ begin, int* __restrict__ end,
+                              int* __restrict__ level, int* __restrict__ parent, int* __restrict__ child,
+                              int* __restrict__ nchild, uint64_t* __restrict__ key, int lb, int le, int l,
+                              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off) {
+  int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= le) return;
+  uint32_t k = cnt[c - lb];
+  nchild[c] = (int)k;
+  if (k == 0) {
+    child[c] = -1;
+    return;
+  }
+  int first = le + (int)off[c - lb];
+  child[c] = first;
+  int bd[9];
+  child_bounds(skeys, begin[c], end[c], key[c], l, bd);
+  int o = first;
+  for (int d = 0; d < 8; ++d) {
+    if (bd[d + 1] > bd[d]) {
+      begin[o] = bd[d];
+      end[o] = bd[d + 1];
+      level[o] = l + 1;
+      parent[o] = c;
+      key[o] = (key[c] << 3) | (uint64_t)d;
+      ++o;
+    }
+  }
+}
+
+
+__global__ void k_centers(const int* __restrict__ level, const uint64_t* __restrict__ key, int nc,
+                          const double* __restrict__ box, double* __restrict__ center,
+                          unsigned long long* __restrict__ r2bits) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  int l = level[c];
+  uint64_t k = key[c];
+  double a = __dmul_rn(box[3], ldexp(1.0, -l));
+  uint32_t ijk[3] = {compact3(k >> 2), compact3(k >> 1), compact3(k)};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) center[3 * c + q] = __dadd_rn(box[q], __dmul_rn((double)ijk[q] + 0.5, a));
+  r2bits[c] = 0ull;
+}
+
+__global__ void k_leaf_flags(const int* __restrict__ nchild, int nc, uint32_t* __restrict__ f) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) f[c] = nchild[c] == 0 ? 1u : 0u;
+}
+
+__global__ void k_leaf_list(const int* __restrict__ nchild, int nc, const uint32_t* __restrict__ off,
+                            int* __restrict__ leaves) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc && nchild[c] == 0) leaves[off[c]] = c;
+}
+
+__global__ void k_leaf_of(const int* __restrict__ leaves, int nl, const int* __restrict__ begin,
+                          const int* __restrict__ end, int* __restrict__ leaf_of) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= nl) return;
+  int c = leaves[w];
+  for (int i = begin[c] + lane; i < end[c]; i += 32) leaf_of[i] = c;
+}
+
+// r^2 of every particle about every ancestor centre; max via 64-bit atomics
+// (non-negative doubles order like their bit patterns), one atomic per
+// distinct cell per warp.
+__global__ void k_radius(const float4* __restrict__ A, int64_t n, const int* __restrict__ leaf_of,
+                         const int* __restrict__ parent, const double* __restrict__ center,
+                         unsigned long long* __restrict__ r2bits) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = i < n;
+  int c = valid ? leaf_of[i] : -1;
+  float4 a = valid ? A[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // all lanes walk until every lane is done
+  while (__any_sync(0xffffffffu, c >= 0)) {
+    unsigned long long v = 0ull;
+    if (c >= 0) {
+      double dx = __dsub_rn((double)a.x, center[3 * c]);
+      double dy = __dsub_rn((double)a.y, center[3 * c + 1]);
+      double dz = __dsub_rn((double)a.z, center[3 * c + 2]);
+      double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      v = (unsigned long long)__double_as_longlong(d2);
+    }
+    unsigned peers = __match_any_sync(0xffffffffu, c);
+    unsigned long long m = v;
+    // max over peers
+    for (int o = 0; o < 32; ++o) {
+      unsigned long long t = __shfl_sync(0xffffffffu, v, o);
+      if ((peers >> o) & 1u) m = m > t ? m : t;
+    }
+    int leader = __ffs(peers) - 1;
+    if (c >= 0 && (int)(threadIdx.x & 31) == leader) atomicMax(&r2bits[c], m);
+    c = c >= 0 ? parent[c] : -1;
+  }
+}
+
+__global__ void k_radius_final(const unsigned long long* __restrict__ r2bits, int nc, double* __restrict__ R) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) R[c] = __dsqrt_rn(__longlong_as_double((long long)r2bits[c]));
+}
+
+}  // namespace
+
+int grow_cells(fmm_plan p, int64_t need, cudaStream_t s) {
+  size_t ni = (size_t)need;
+  FMM_TRY(p->c_begin.grow_copy(ni * sizeof(int), s));
+  FMM_TRY(p->c_end.grow_copy(ni * sizeof(int), s));
+  FMM_TRY(p->c_level.grow_copy(ni * sizeof(int), s));
+  FMM_TRY(p->c_parent.grow_copy(ni * sizeof(int), s));
+  FMM_TRY(p->c_child.grow_copy(ni * sizeof(int), s));
+  FMM_TRY(p->c_nchild.grow_copy(ni * sizeof(int), s));
+  FMM_TRY(p->c_key.grow_copy(ni * sizeof(uint64_t), s));
+  return FMM_OK;
+}
+
+// Keys, sort, permutation into sorted SoA, octree, centres, radii.
+int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u,
+               cudaStream_t s) {
+  const int T = 256;
+  unsigned nb = (unsigned)((n + T - 1) / T);
+  double* box = p->scal.as<double>();
+  if (p->prm.periodic) {
+    k_set_box<<<1, 1, 0, s>>>(p->prm.box_min[0], p->prm.box_min[1], p->prm.box_min[2], p->prm.box_len, box);
+  } else {
+    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    FMM_TRY(p->scan_tmp.ensure((size_t)parts * 6 * sizeof(double)));
+    k_bbox_partial<<<parts, 256, 0, s>>>(pos, n, p->scan_tmp.as<double>());
+    k_bbox_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, box);
+  }
+  // sigma max (uniform: the value itself)
+  unsigned int* smax = reinterpret_cast<unsigned int*>(box + 8);
+  if (sig) {
+    FMM_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(unsigned int), s));
+    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    k_sigma_max<<<parts, 256, 0, s>>>(sig, n, smax);
+  }
+  uint64_t* k0 = p->keys0.as<uint64_t>();
+  uint64_t* k1 = p->keys1.as<uint64_t>();
+  uint32_t* v0 = p->vals0.as<uint32_t>();
+  uint32_t* v1 = p->vals1.as<uint32_t>();
+  k_keys<<<nb, T, 0, s>>>(pos, n, box, k0, v0);
+  FMM_CUDA_TRY(cudaGetLastError());
+  int second = 0;
+  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 63, &second, p->sort_hist, p->scan_tmp, s));
+  p->skeys = second ? k1 : k0;
+  p->sidx = second ? v1 : v0;
+  k_permute<<<nb, T, 0, s>>>(pos, gam, sig, sig_u, p->sidx, n, p->sortA.as<float4>(), p->sortB.as<float4>());
+  FMM_CUDA_TRY(cudaGetLastError());
+
+  // ---- octree, level by level
+  int64_t cap = std::max<int64_t>(64, 4 * n / std::max(1, p->prm.ncrit) + 64);
+  if ((int64_t)(p->c_begin.bytes / sizeof(int)) < cap) FMM_TRY(grow_cells(p, cap, s));
+  k_root<<<1, 1, 0, s>>>((int)n, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
+                         p->c_parent.as<int>(), p->c_key.as<uint64_t>());
+  p->level_begin.assign(1, 0);
+  int lb = 0, le = 1;
+  uint32_t* hcount = reinterpret_cast<uint32_t*>(p->pinned);
+  for (int l = 0;; ++l) {
+    p->level_begin.push_back(le);
+    int ncl = le - lb;
+    FMM_TRY(p->tcount.ensure((size_t)(ncl + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->tscan0.ensure((size_t)(ncl + 1) * sizeof(uint32_t)));
+    unsigned g = (unsigned)((ncl + T - 1) / T);
+    k_split_count<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_key.as<uint64_t>(),
+                                  lb, le, l, p->prm.ncrit, p->tcount.as<uint32_t>());
+    FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ncl,
+                               p->tscan0.as<uint32_t>() + ncl, p->scan_tmp, s));
+    FMM_CUDA_TRY(cudaMemcpyAsync(hcount, p->tscan0.as<uint32_t>() + ncl, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t nnew = hcount[0];
+    if (le + nnew > (int64_t)(p->c_begin.bytes / sizeof(int))) FMM_TRY(grow_cells(p, 2 * (le + nnew), s));
+    k_split_write<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
+                                  p->c_parent.as<int>(), p->c_child.as<int>(), p->c_nchild.as<int>(),
+                                  p->c_key.as<uint64_t>(), lb, le, l, p->tcount.as<uint32_t>(),
+                                  p->tscan0.as<uint32_t>());
+    FMM_CUDA_TRY(cudaGetLastError());
+    if (nnew == 0) break;
+    lb = le;
+    le = (int)(le + nnew);
+  }
+  // level_begin has one entry per level plus the end
+  const int nc = p->level_begin.back();
+  p->ncells = nc;
+  p->nlevels = (int)p->level_begin.size() - 1;
+
+  // ---- centres, leaves, radii
+  FMM_TRY(p->c_center.ensure((size_t)nc * 3 * sizeof(double)));
+  FMM_TRY(p->c_radius2.ensure((size_t)nc * sizeof(unsigned long long)));
+  FMM_TRY(p->c_radius.ensure((size_t)nc * sizeof(double)));
+  FMM_TRY(p->leaves.ensure((size_t)(nc + 1) * sizeof(int)));
+  FMM_TRY(p->tcount.ensure((size_t)(nc + 1) * sizeof(uint32_t)));
+  FMM_TRY(p->tscan0.ensure((size_t)(nc + 1) * sizeof(uint32_t)));
+  unsigned gc = (unsigned)((nc + T - 1) / T);
+  k_centers<<<gc, T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc, box, p->c_center.as<double>(),
+                             p->c_radius2.as<unsigned long long>());
+  k_leaf_flags<<<gc, T, 0, s>>>(p->c_nchild.as<int>(), nc, p->tcount.as<uint32_t>());
+  FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), nc, p->tscan0.as<uint32_t>() + nc,
+                             p->scan_tmp, s));
+  k_leaf_list<<<gc, T, 0, s>>>(p->c_nchild.as<int>(), nc, p->tscan0.as<uint32_t>(), p->leaves.as<int>());
+  FMM_CUDA_TRY(cudaMemcpyAsync(hcount, p->tscan0.as<uint32_t>() + nc, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  p->nleaves = hcount[0];
+  k_leaf_of<<<(unsigned)((p->nleaves * 32 + T - 1) / T), T, 0, s>>>(p->leaves.as<int>(), (int)p->nleaves,
+                                                                   p->c_begin.as<int>(), p->c_end.as<int>(),
+                                                                   p->leaf_of.as<int>());
+  k_radius<<<nb, T, 0, s>>>(p->sortA.as<float4>(), n, p->leaf_of.as<int>(), p->c_parent.as<int>(),
+                            p->c_center.as<double>(), p->c_radius2.as<unsigned long long>());
+  k_radius_final<<<gc, T, 0, s>>>(p->c_radius2.as<unsigned long long>(), nc, p->c_radius.as<double>());
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+}  // namespace fmm

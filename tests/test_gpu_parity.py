@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA path against the FP64 oracle (marked gpu).
+
+Integer work (Morton keys, sort order, cells, interaction lists) must match
+bit for bit; floating point within tolerances derived from FP32 arithmetic
+(unit roundoff 6e-8 times the growth of sums with ~1e4 terms and mild
+cancellation) -- rel-L2 2e-5 for u and 5e-5 for s against the oracle FMM on
+the same tree and lists; against the FP64 direct sum the FMM must stay
+within 1.5x the oracle FMM's own method error plus that FP32 allowance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_common import rel_l2, run_fmm, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = 2e-5
+TOL_S = 5e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3):
+    from oracle import fmm as ofmm
+    kw = {}
+    if w.get("periodic"):
+        kw = dict(periodic=True, box_min=w["box_min"], box_len=w["box_len"], images=images)
+    return ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), p, theta, ncrit, ksig=ksig, **kw)
+
+
+def _canon(lst, periodic):
+    a = np.asarray(lst, np.int64).reshape(-1, 3).copy()
+    if not periodic:
+        a[:, 2] = 13  # oracle numbers its single zero image 0; the ABI numbers it 13
+    return a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+
+
+def _check_tree_and_lists(plan, ref, periodic):
+    order, keys = plan.order()
+    assert np.array_equal(order.astype(np.int64), ref.order)
+    assert np.array_equal(keys, ref.keys)
+    c = plan.cells()
+    t = ref.tree
+    for f in ("begin", "end", "level", "parent", "nchild"):
+        assert np.array_equal(c[f].astype(np.int64), getattr(t, f)), f
+    cb = np.where(t.nchild > 0, t.child_begin, -1)
+    assert np.array_equal(c["child_begin"].astype(np.int64), cb)
+    assert np.array_equal(c["center"], t.center)
+    assert np.array_equal(c["radius"], t.radius)
+    p2p, m2l = plan.lists()
+    rp = ref.p2p.copy()
+    rm = ref.m2l.copy()
+    assert np.array_equal(_canon(p2p, True), _canon(rp, periodic) if not periodic else _canon(rp, True))
+    assert np.array_equal(_canon(m2l, True), _canon(rm, periodic) if not periodic else _canon(rm, True))
+
+
+def test_direct_all_pairs_matches_oracle():
+    import torch
+    from oracle import direct as od
+    from paper_1106_5273_gb300 import direct
+    w = workloads.jittered_lattice(12)  # 1728 blobs, ragged vs the 128-wide tiles
+    n = w["pos"].shape[0]
+    sig = np.linspace(0.5, 1.5, n).astype(np.float32) * w["sigma"]
+    for sarr in (None, sig):
+        u, s = direct(to_dev(w["pos"]), to_dev(w["gamma"]), sigma=to_dev(sarr) if sarr is not None else None,
+                      sigma_uniform=float(w["sigma"]))
+        torch.cuda.synchronize()
+        ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], sarr if sarr is not None else w["sigma"],
+                           skip_self=True)
+        assert rel_l2(u.cpu().numpy(), ud) < 2e-6
+        assert rel_l2(s.cpu().numpy(), sd) < 5e-6
+        # element-wise: every target within a small multiple of its own scale
+        err = np.abs(u.cpu().numpy() - ud).max(1) / (np.linalg.norm(ud, axis=1) + 1e-3 * np.linalg.norm(ud) / math.sqrt(n))
+        assert err.max() < 1e-4
+
+
+@pytest.mark.parametrize("m2l_mode", [1])
+def test_fmm_free_space_jittered_lattice(m2l_mode):
+    """4096 blobs on a jittered 16^3 lattice, p=6, theta=0.5, ncrit=32."""
+    from oracle import direct as od
+    w = workloads.jittered_lattice(16)
+    p, theta, ncrit = 6, 0.5, 32
+    plan, u, s = run_fmm(w, p, theta, ncrit, m2l_mode=m2l_mode)
+    ref = _oracle_fmm(w, p, theta, ncrit)
+    _check_tree_and_lists(plan, ref, False)
+    assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
+    ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], float(w["sigma"]), skip_self=True)
+    eu_cpu, es_cpu = rel_l2(ref.u, ud), rel_l2(ref.s, sd)
+    assert rel_l2(u, ud) <= 1.5 * eu_cpu + TOL_U
+    assert rel_l2(s, sd) <= 1.5 * es_cpu + TOL_S
+    st = plan.stats()
+    assert st.m2l_pairs == len(ref.m2l) and st.p2p_cell_pairs == len(ref.p2p)
+
+
+def test_fmm_periodic_taylor_green_small():
+    """16^3 Taylor-Green blobs in the periodic cube, p=6."""
+    from oracle import periodic as op
+    w = workloads.taylor_green(16)
+    p, theta, ncrit = 6, 0.4, 64
+    plan, u, s = run_fmm(w, p, theta, ncrit, m2l_mode=1)
+    ref = _oracle_fmm(w, p, theta, ncrit)
+    _check_tree_and_lists(plan, ref, True)
+    assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
+    ut, st_ = op.taylor_green(w["pos"].astype(np.float64), w["gamma"].astype(np.float64), float(w["sigma"]))
+    assert rel_l2(u, ut) < 1.5 * rel_l2(ref.u, ut) + TOL_U
+
+
+def test_fmm_periodic_random_matches_fourier():
+    from oracle import periodic as op
+    L = 2 * math.pi
+    c = workloads.random_cloud(600, seed=21, box=L, zero_net=True)
+    g = c["gamma"] - c["gamma"].astype(np.float64).mean(0).astype(np.float32)
+    w = dict(pos=c["pos"], gamma=g, sigma=np.float32(0.45), periodic=True, box_min=np.zeros(3), box_len=L)
+    plan, u, s = run_fmm(w, 6, 0.5, 16, m2l_mode=1)
+    ref = _oracle_fmm(w, 6, 0.5, 16)
+    _check_tree_and_lists(plan, ref, True)
+    assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
+    uf, sf = op.fourier(w["pos"], g, w["pos"], g, 0.45, L, 14)
+    assert rel_l2(u, uf) < 1.5 * rel_l2(ref.u, uf) + TOL_U
+
+
+def test_fmm_per_particle_sigma_and_plummer():
+    from oracle import direct as od
+    w = workloads.plummer(3000)
+    n = w["pos"].shape[0]
+    sig = (w["sigma"] * np.linspace(0.7, 1.3, n)).astype(np.float32)
+    plan, u, s = run_fmm(dict(w, sigma=1.0), 8, 0.5, 16, m2l_mode=1, sigma_arr=sig)
+    ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], sig, skip_self=True)
+    assert rel_l2(u, ud) < 2e-4 and rel_l2(s, sd) < 1e-3
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 257])
+def test_edge_sizes(n):
+    from oracle import direct as od
+    w = workloads.random_cloud(n, seed=30 + n)
+    w.update(sigma=np.float32(0.05))
+    if n == 0:
+        from paper_1106_5273_gb300 import Plan, Params
+        import torch
+        plan = Plan(4, Params.default(p=4, ncrit=8))
+        u, s = plan.eval(torch.zeros((0, 3), device="cuda"), torch.zeros((0, 3), device="cuda"), sigma_uniform=0.05)
+        assert u.shape == (0, 3)
+        return
+    plan, u, s = run_fmm(w, 8, 0.5, 8, m2l_mode=1)
+    ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], 0.05, skip_self=True)
+    if n == 1:
+        assert np.all(u == 0) and np.all(s == 0)
+    else:
+        assert rel_l2(u, ud) < 1e-3 and rel_l2(s, sd) < 3e-3
+
+
+def test_coincident_points_hit_depth_cap():
+    # every particle at the same point: the tree stops at level 21 with one
+    # over-full leaf; velocity is exactly zero (d = 0), stretching is the
+    # S(0) gamma_j x gamma_i sum.
+    from oracle import direct as od
+    n = 100
+    rng = np.random.default_rng(3)
+    pos = np.tile(np.array([[0.3, 0.2, 0.1]], np.float32), (n, 1))
+    gam = rng.normal(size=(n, 3)).astype(np.float32)
+    w = dict(pos=pos, gamma=gam, sigma=np.float32(0.1))
+    plan, u, s = run_fmm(w, 4, 0.5, 8, m2l_mode=1)
+    st = plan.stats()
+    assert st.nlevels == 22
+    assert np.all(u == 0)
+    ud, sd = od.direct(pos, gam, pos, gam, 0.1, skip_self=True)
+    assert rel_l2(s, sd) < 1e-5
+
+
+def test_deterministic_and_host_entry():
+    import torch
+    w = workloads.jittered_lattice(16)
+    plan, u1, s1 = run_fmm(w, 6, 0.5, 32, m2l_mode=1)
+    u2, s2 = plan.eval(to_dev(w["pos"]), to_dev(w["gamma"]), sigma_uniform=float(w["sigma"]))
+    torch.cuda.synchronize()
+    assert np.array_equal(u1, u2.cpu().numpy()) and np.array_equal(s1, s2.cpu().numpy())
+    uh, sh = plan.eval_host(w["pos"], w["gamma"], sigma_uniform=float(w["sigma"]))
+    assert np.array_equal(u1, uh) and np.array_equal(s1, sh)
