@@ -42,7 +42,8 @@ struct fmm_plan_s {
   fmm::DBuf c_begin, c_end, c_level, c_parent, c_child, c_nchild;  // int32
   fmm::DBuf c_key;                                                  // u64 level-local Morton index
   fmm::DBuf c_center, c_radius2, c_radius;                          // double[3], u64 bits, double
-  fmm::DBuf c_tile;                                                 // int32 tile*64+slot
+  fmm::DBuf c_tile;                                                 // int32 tile*64+slot of each cell
+  fmm::DBuf tile_cells;                                             // cell of each (tile, slot) position
   fmm::DBuf leaves;                                                 // leaf cell ids
   fmm::DBuf M, L;                                                   // [cells][3][P] FP32
   fmm::DBuf Mbf;                                                    // [cells][2][3][Kpad] BF16 hi/lo

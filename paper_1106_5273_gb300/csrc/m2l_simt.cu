@@ -15,7 +15,7 @@ constexpr int kRC = 32;  // output rows per pass
 __global__ void __launch_bounds__(192) k_m2l_simt(const int2* __restrict__ tile_range, LevelInfo li,
                                                   const int* __restrict__ st_slot, const int* __restrict__ st_src,
                                                   const float* __restrict__ T32, const float* __restrict__ M, int P,
-                                                  float* __restrict__ L) {
+                                                  const int* __restrict__ tcell, float* __restrict__ L) {
   extern __shared__ float sT[];  // [kRC][P]
   const int tile = blockIdx.x;
   const int2 rg = tile_range[tile];
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(192) k_m2l_simt(const int2* __restrict__ tile_
       __syncthreads();
     }
     if (slot < ncell) {
-      float* out = L + ((size_t)(first + slot) * 3 + comp) * P + r0;
+      float* out = L + ((size_t)tcell[first + slot] * 3 + comp) * P + r0;
       for (int i = 0; i < nr; ++i) out[i] = acc[i];
     }
   }
@@ -66,7 +66,7 @@ int m2l_simt(fmm_plan p, cudaStream_t s) {
   if (sh > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   k_m2l_simt<<<(unsigned)p->ntiles, 3 * kTile, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
                                                          p->st_src.as<int>(), p->T32.as<float>(), p->M.as<float>(),
-                                                         p->P, p->L.as<float>());
+                                                         p->P, p->tile_cells.as<int>(), p->L.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -1,13 +1,313 @@
 // M2L on the 5th-generation tensor cores (tcgen05), BF16x3 split products
-// with FP32 accumulation in tensor memory.
+// with FP32 accumulation in tensor memory (Sec. 3.1 M2L, batched per
+// translation vector).
+//
+// A step applies one translation operator T (P x P, P = p^2 <= 128) to the
+// multipoles of the 64 source cells paired with a tile of 64 target cells:
+//   D[128 x 192] += T[128 x K] . B[K x 192],  B column (comp, slot) = M~ of
+// the slot's source for that potential component (zero if the slot has no
+// source under this translation).  T = T_hi + T_lo and B = B_hi + B_lo in
+// BF16; D accumulates T_hi B_hi + T_hi B_lo + T_lo B_hi (the lo.lo term is
+// below FP32 resolution of the sum).  D lives in TMEM for all steps of the
+// tile; each target local expansion is written once.
+//
+// Per stage (one step, one 64-wide K chunk): A (T hi/lo, pre-swizzled in
+// global memory in the 128B-swizzle K-major layout) arrives by two 1-D bulk
+// copies on mbarrier fullA; 8 producer warps gather the B rows (128 B each)
+// and store them swizzled, then arrive on fullB; one thread issues the MMAs
+// and commits them to the stage's empty barrier.  Two stages.  Every wait is
+// bounded; on expiry the kernel records FMM_E_TIMEOUT, waits (bounded) for
+// its own bulk copies, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
 
+namespace {
+
+constexpr int kN = 3 * kTile;                               // 192 columns
+constexpr int kStages = 2;
+constexpr int kProducerWarps = 8;
+constexpr int kProducers = kProducerWarps * 32;
+constexpr int kThreads = kProducers + 32;                   // + control warp
+constexpr uint32_t kABytes = 128 * 128;                     // 128 rows x 64 bf16
+constexpr uint32_t kBBytes = kN * 128;                      // 192 rows x 64 bf16
+constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 80 KB
+constexpr uint32_t kBarOff = kStages * kStageBytes;
+constexpr int kTmemCols = 256;
+constexpr long long kSpin = 1ll << 24;
+constexpr int kGather = (2 * kN * 8) / kProducers;          // 16-byte items per producer thread (12)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t tx) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(tx)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the limit is reached (the caller aborts).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (long long i = 0; i < kSpin; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 1023) == 1023 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N = 192, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_m2l_tc(const int2* __restrict__ tile_range, LevelInfo li, const int* __restrict__ st_slot,
+             const int* __restrict__ st_src, const __nv_bfloat16* __restrict__ Tbf,
+             const __nv_bfloat16* __restrict__ Mbf, int P, int nkc, int ksteps_last, const int* __restrict__ tcell,
+             float* __restrict__ L, int* __restrict__ flag) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tile = blockIdx.x;
+  const int2 rg = tile_range[tile];
+  if (rg.y <= rg.x) return;  // no M2L for this tile: the whole CTA leaves before any barrier
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  // bars: fullA[2], fullB[2], empty[2], done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+  volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar0 = smem_u32(bars);
+  auto fullA = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+  auto fullB = [&](int s) { return bar0 + 8u * (uint32_t)(2 + s); };
+  auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(4 + s); };
+  const uint32_t done = bar0 + 8u * 6u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(fullA(s), 1);
+      mbar_init(fullB(s), kProducers);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == kProducerWarps) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int niter = (rg.y - rg.x) * nkc;
+
+  if (warp < kProducerWarps) {
+    // ---- producers: gather the B rows of each stage
+    for (int it = 0; it < niter; ++it) {
+      const int stage = it & 1;
+      const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+      if (!mbar_wait(empty(stage), ph ^ 1u, abort)) break;
+      const int st = rg.x + it / nkc, kc = it % nkc;
+      uint4 v[kGather];
+      int dst[kGather];
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) {
+        const int item = threadIdx.x + kProducers * q;
+        const int h = item / (kN * 8);
+        const int rem = item % (kN * 8);
+        const int n = rem >> 3, j = rem & 7;
+        const int comp = n / kTile, slot = n % kTile;
+        const int src = st_src[(size_t)st * kTile + slot];
+        v[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (src >= 0) {
+          const uint4* gp = reinterpret_cast<const uint4*>(Mbf + (((size_t)src * 2 + h) * 3 + comp) * 128 + kc * 64) + j;
+          v[q] = __ldg(gp);
+        }
+        dst[q] = (int)(stage * kStageBytes + 2 * kABytes + h * kBBytes + n * 128 + ((j ^ (n & 7)) << 4));
+      }
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) *reinterpret_cast<uint4*>(smem + dst[q]) = v[q];
+      fence_proxy_async();
+      mbar_arrive(fullB(stage));
+    }
+  } else if (lane == 0) {
+    // ---- control thread: operator copies and MMAs
+    int issued = 0;  // A copies issued for iterations [0, issued)
+    auto issue_A = [&](int it) -> bool {
+      const int stage = it & 1;
+      const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+      if (!mbar_wait(empty(stage), ph ^ 1u, abort)) return false;
+      const int st = rg.x + it / nkc, kc = it % nkc;
+      const size_t key = (size_t)st_slot[st];
+      const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * 2 + kc) * (128 * 64);
+      const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * 2 + kc) * (128 * 64);
+      const uint32_t a0 = sbase + stage * kStageBytes;
+      mbar_arrive_tx(fullA(stage), 2 * kABytes);
+      bulk_g2s(a0, hi, kABytes, fullA(stage));
+      bulk_g2s(a0 + kABytes, lo, kABytes, fullA(stage));
+      issued = it + 1;
+      return true;
+    };
+    bool ok = issue_A(0);
+    int consumed = 0;  // iterations whose A copy was observed complete
+    for (int it = 0; ok && it < niter; ++it) {
+      const int stage = it & 1;
+      const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+      if (it + 1 < niter && !issue_A(it + 1)) {
+        ok = false;
+        break;
+      }
+      if (!mbar_wait(fullA(stage), ph, abort)) {
+        ok = false;
+        break;
+      }
+      consumed = it + 1;
+      if (!mbar_wait(fullB(stage), ph, abort)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int kc = it % nkc;
+      const int ks = (kc == nkc - 1) ? ksteps_last : 4;
+      const uint32_t a_hi = sbase + stage * kStageBytes, a_lo = a_hi + kABytes;
+      const uint32_t b_hi = a_hi + 2 * kABytes, b_lo = b_hi + kBBytes;
+      for (int kk = 0; kk < ks; ++kk) {
+        const uint32_t off = (uint32_t)kk * 32u;
+        umma(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (it > 0 || kk > 0) ? 1u : 0u);
+        umma(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+        umma(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+      }
+      umma_commit(empty(stage));
+    }
+    if (ok) {
+      umma_commit(done);
+    } else {
+      *abort = 1;
+      // let our own in-flight bulk copies land and our MMAs finish before
+      // the tensor memory is freed and the CTA exits
+      volatile int never = 0;
+      for (int it = consumed; it < issued; ++it) mbar_wait(fullA(it & 1), (uint32_t)(it >> 1) & 1u, &never);
+      umma_commit(done);
+      mbar_wait(done, 0u, &never);
+      atomicExch(flag, FMM_E_TIMEOUT);
+    }
+  }
+  // ---- epilogue: warps 0-3 own TMEM lanes 0-127 (rows = output coefficients)
+  if (warp < 4) {
+    if (mbar_wait(done, 0u, abort)) {
+      tc_fence_after();
+      int l = 0;
+      while (l + 1 < li.nlevels && li.tile_begin[l + 1] <= tile) ++l;
+      const int first = li.level_begin[l] + (tile - li.tile_begin[l]) * kTile;
+      const int ncell = min(kTile, li.level_begin[l + 1] - first);
+      const int r = warp * 32 + lane;
+#pragma unroll 1
+      for (int cb = 0; cb < kN / 16; ++cb) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = cb * 16 + i;
+          const int comp = n / kTile, slot = n % kTile;
+          if (r < P && slot < ncell) L[((size_t)tcell[first + slot] * 3 + comp) * P + r] = v[i];
+        }
+      }
+    } else {
+      atomicExch(flag, FMM_E_TIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kProducerWarps) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
 int m2l_tensor(fmm_plan p, cudaStream_t s) {
-  (void)p;
-  (void)s;
-  return FMM_E_INVAL;
+  if (p->n_steps == 0) return FMM_OK;
+  if (p->P > 128) return FMM_E_INVAL;
+  LevelInfo li;
+  li.nlevels = p->nlevels;
+  for (int l = 0; l <= p->nlevels; ++l) {
+    li.level_begin[l] = p->level_begin[l];
+    li.tile_begin[l] = p->tile_begin[l];
+  }
+  const int ksteps = (p->P + 15) / 16;
+  const int nkc = (ksteps + 3) / 4;
+  const int last = ksteps - 4 * (nkc - 1);
+  const size_t sh = (size_t)kBarOff + 128 + 1024;
+  static bool attr = false;
+  if (!attr) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    attr = true;
+  }
+  k_m2l_tc<<<(unsigned)p->ntiles, kThreads, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
+                                                      p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
+                                                      p->Mbf.as<__nv_bfloat16>(), p->P, nkc, last,
+                                                      p->tile_cells.as<int>(), p->L.as<float>(), p->flags.as<int>());
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
 }
 
 }  // namespace fmm

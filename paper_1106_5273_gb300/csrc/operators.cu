@@ -179,21 +179,15 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, int nkeys, int p,
     else v = po == 0 ? -s * (B.im - A.im) : s * (B.re - A.re);
     T32[(size_t)key_id * P * P + e] = (float)v;
     if (tc) {
+      // [key][hi/lo][K chunk of 64][128 rows][64], 16-byte groups of a row
+      // stored in the 128-byte swizzle order (group j at j ^ (row & 7))
       __nv_bfloat16 hi = __double2bfloat16(v);
       __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
-      size_t base = (size_t)key_id * 2 * 128 * 128;
-      Tbf[base + (size_t)r * 128 + c] = hi;
-      Tbf[base + 128 * 128 + (size_t)r * 128 + c] = lo;
+      const int kc = c >> 6, j = (c & 63) >> 3, el = c & 7;
+      const size_t within = (size_t)r * 64 + (size_t)(((j ^ (r & 7)) << 3) + el);
+      Tbf[(((size_t)key_id * 2 + 0) * 2 + kc) * (128 * 64) + within] = hi;
+      Tbf[(((size_t)key_id * 2 + 1) * 2 + kc) * (128 * 64) + within] = lo;
     }
-  }
-}
-
-// zero padding of the BF16 operator tiles (rows >= P or cols >= P)
-__global__ void k_zero_bf(__nv_bfloat16* Tbf, int nkeys, int P) {
-  size_t total = (size_t)nkeys * 2 * 128 * 128;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    int c = (int)(i % 128), r = (int)((i / 128) % 128);
-    if (r >= P || c >= P) Tbf[i] = __float2bfloat16(0.f);
   }
 }
 
@@ -253,8 +247,9 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
   FMM_TRY(p->T32.ensure((size_t)p->n_keys * P * P * sizeof(float)));
   int tc = p->last_tc;
   if (tc) {
-    FMM_TRY(p->Tbf.ensure((size_t)p->n_keys * 2 * 128 * 128 * sizeof(__nv_bfloat16)));
-    k_zero_bf<<<1024, 256, 0, s>>>(p->Tbf.as<__nv_bfloat16>(), (int)p->n_keys, P);
+    const size_t tb = (size_t)p->n_keys * 2 * 128 * 128 * sizeof(__nv_bfloat16);
+    FMM_TRY(p->Tbf.ensure(tb));
+    FMM_CUDA_TRY(cudaMemsetAsync(p->Tbf.ptr, 0, tb, s));
   }
   k_build_m2l<<<(unsigned)p->n_keys, 256, 0, s>>>(p->ukeys.as<uint64_t>(), (int)p->n_keys, p->prm.p,
                                                    p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(), tc);

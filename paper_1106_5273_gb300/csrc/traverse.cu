@@ -206,13 +206,27 @@ __global__ void k_unique_write(const uint64_t* __restrict__ k, const uint32_t* _
   slot_of_pair[idx[i]] = s;
 }
 
-__global__ void k_cell_tiles(LevelInfo li, int nc, int* __restrict__ ctile) {
+// Tiles group the cells of one level by child octant (then Morton order):
+// cells at the same octant position have the same relative interaction
+// lists in a uniform region, so a tile's steps are nearly full.
+__global__ void k_tile_order_keys(const int* __restrict__ level, const uint64_t* __restrict__ ckey, int nc,
+                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
+  keys[c] = ((uint64_t)level[c] << 40) | ((ckey[c] & 7ull) << 32) | (uint64_t)c;
+  vals[c] = (uint32_t)c;
+}
+
+__global__ void k_cell_tiles(LevelInfo li, int nc, const uint32_t* __restrict__ order, int* __restrict__ ctile,
+                             int* __restrict__ tcell) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nc) return;
   int l = 0;
-  while (l + 1 < li.nlevels && li.level_begin[l + 1] <= c) ++l;
-  int r = c - li.level_begin[l];
+  while (l + 1 < li.nlevels && li.level_begin[l + 1] <= q) ++l;
+  int r = q - li.level_begin[l];
+  int c = (int)order[q];
   ctile[c] = (li.tile_begin[l] + r / kTile) * kTile + r % kTile;
+  tcell[q] = c;
 }
 
 __global__ void k_step_keys(const int4* __restrict__ raw, int n, const int* __restrict__ ctile,
@@ -366,7 +380,21 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     li.tile_begin[p->nlevels] = p->tile_begin[p->nlevels];
     p->ntiles = p->tile_begin[p->nlevels];
     FMM_TRY(p->c_tile.ensure((nc + 1) * sizeof(int)));
-    k_cell_tiles<<<(unsigned)((nc + T - 1) / T), T, 0, s>>>(li, nc, p->c_tile.as<int>());
+    FMM_TRY(p->tile_cells.ensure((nc + 1) * sizeof(int)));
+    FMM_TRY(p->lk0.ensure((nc + 1) * sizeof(uint64_t)));
+    FMM_TRY(p->lk1.ensure((nc + 1) * sizeof(uint64_t)));
+    FMM_TRY(p->lv0.ensure((nc + 1) * sizeof(uint32_t)));
+    FMM_TRY(p->lv1.ensure((nc + 1) * sizeof(uint32_t)));
+    {
+      unsigned gc = (unsigned)((nc + T - 1) / T);
+      k_tile_order_keys<<<gc, T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc, p->lk0.as<uint64_t>(),
+                                         p->lv0.as<uint32_t>());
+      int second = 0;
+      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                             p->lv1.as<uint32_t>(), nc, 0, 48, &second, p->sort_hist, p->scan_tmp, s));
+      uint32_t* ord = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      k_cell_tiles<<<gc, T, 0, s>>>(li, nc, ord, p->c_tile.as<int>(), p->tile_cells.as<int>());
+    }
     FMM_TRY(p->tile_range.ensure((p->ntiles + 1) * sizeof(int2)));
     FMM_CUDA_TRY(cudaMemsetAsync(p->tile_range.ptr, 0, (p->ntiles + 1) * sizeof(int2), s));
     p->n_keys = 0;

@@ -81,7 +81,7 @@ def test_direct_all_pairs_matches_oracle():
         assert err.max() < 1e-4
 
 
-@pytest.mark.parametrize("m2l_mode", [1])
+@pytest.mark.parametrize("m2l_mode", [1, 2])
 def test_fmm_free_space_jittered_lattice(m2l_mode):
     """4096 blobs on a jittered 16^3 lattice, p=6, theta=0.5, ncrit=32."""
     from oracle import direct as od
@@ -99,12 +99,13 @@ def test_fmm_free_space_jittered_lattice(m2l_mode):
     assert st.m2l_pairs == len(ref.m2l) and st.p2p_cell_pairs == len(ref.p2p)
 
 
-def test_fmm_periodic_taylor_green_small():
+@pytest.mark.parametrize("m2l_mode", [1, 2])
+def test_fmm_periodic_taylor_green_small(m2l_mode):
     """16^3 Taylor-Green blobs in the periodic cube, p=6."""
     from oracle import periodic as op
     w = workloads.taylor_green(16)
     p, theta, ncrit = 6, 0.4, 64
-    plan, u, s = run_fmm(w, p, theta, ncrit, m2l_mode=1)
+    plan, u, s = run_fmm(w, p, theta, ncrit, m2l_mode=m2l_mode)
     ref = _oracle_fmm(w, p, theta, ncrit)
     _check_tree_and_lists(plan, ref, True)
     assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
@@ -183,3 +184,30 @@ def test_deterministic_and_host_entry():
     assert np.array_equal(u1, u2.cpu().numpy()) and np.array_equal(s1, s2.cpu().numpy())
     uh, sh = plan.eval_host(w["pos"], w["gamma"], sigma_uniform=float(w["sigma"]))
     assert np.array_equal(u1, uh) and np.array_equal(s1, sh)
+
+
+@pytest.mark.parametrize("p", [4, 8, 10, 11])
+def test_tensor_m2l_matches_simt(p):
+    """tcgen05 BF16x3 M2L against the FP32 SIMT M2L on the same lists (1, 2 K-chunks, ragged K)."""
+    w = workloads.plummer(6000)
+    w["sigma"] = np.float32(0.002)
+    _, u1, s1 = run_fmm(w, p, 0.5, 32, m2l_mode=1)
+    plan, u2, s2 = run_fmm(w, p, 0.5, 32, m2l_mode=2)
+    assert plan.stats().m2l_tensor == 1 and plan.stats().m2l_pairs > 0
+    assert rel_l2(u2, u1) < 1e-5 and rel_l2(s2, s1) < 3e-5
+
+
+@pytest.mark.parametrize("m2l_mode", [2, 1])
+def test_full_size_taylor_green_128(m2l_mode):
+    """2,097,152 blobs, p=10, theta=0.4, ncrit=64, periodic: the accuracy gate
+    rel-L2(u) <= 1e-4 against the closed form (sampled targets for s)."""
+    from oracle import periodic as op
+    w = workloads.taylor_green(128)
+    plan, u, s = run_fmm(w, 10, 0.4, 64, m2l_mode=m2l_mode)
+    x = w["pos"].astype(np.float64)
+    g = w["gamma"].astype(np.float64)
+    ut, st_ = op.taylor_green(x, g, float(w["sigma"]))
+    assert rel_l2(u, ut) < 1e-4
+    assert rel_l2(s, st_) < 1e-3
+    stt = plan.stats()
+    assert stt.nleaves == 32768 and stt.m2l_tensor == (1 if m2l_mode == 2 else 0)
