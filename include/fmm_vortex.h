@@ -160,6 +160,10 @@ int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gam
                                    const float* sigma, float sigma_uniform, float* vel,
                                    float* dgamma, void* cuda_stream);
 
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all plans and entry points; for launch accounting in benchmarks). */
+int64_t fmm_kernel_launch_count(void);
+
 /* Enable (1) or disable (0) CUDA-event phase timing in fmm_stats. */
 int fmm_plan_set_timing(fmm_plan plan, int enable);
 

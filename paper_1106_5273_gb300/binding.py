@@ -76,6 +76,8 @@ for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+lib.fmm_kernel_launch_count.argtypes = []
+lib.fmm_kernel_launch_count.restype = ctypes.c_int64
 lib.fmm_plan_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
 lib.fmm_plan_get_order.argtypes = [_vp, _vp, _vp]
 lib.fmm_plan_get_cells.argtypes = [_vp] + [_vp] * 8
@@ -193,6 +195,11 @@ class Plan:
         m2l = np.zeros((s.m2l_pairs, 3), np.int32)
         _check(lib.fmm_plan_get_lists(self._h, p2p.ctypes.data, m2l.ctypes.data), "fmm_plan_get_lists")
         return p2p, m2l
+
+
+def kernel_launch_count():
+    """Kernels launched by the CUDA library since it was loaded."""
+    return int(lib.fmm_kernel_launch_count())
 
 
 def direct(pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None):

@@ -10,6 +10,9 @@
 
 namespace fmm {
 
+// Kernel launches issued by this library (host counter, not thread safe).
+extern int64_t g_launches;
+
 constexpr int kMaxLevel = 21;      // 63-bit Morton keys, 3 bits per level (Sec. 3.2)
 constexpr int kPMax = 16;          // expansion degrees 0..15
 constexpr int kNCoefMax = kPMax * kPMax;

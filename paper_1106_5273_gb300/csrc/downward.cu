@@ -176,12 +176,14 @@ int downward_pass(fmm_plan p, int64_t n, cudaStream_t s) {
   const int P = p->P;
   for (int l = 1; l < p->nlevels; ++l) {
     int lb = p->level_begin[l], le = p->level_begin[l + 1];
+    ++g_launches;
     k_l2l<<<le - lb, 128, 3 * P * sizeof(float), s>>>(lb, p->c_parent.as<int>(), p->c_key.as<uint64_t>(),
                                                       p->l2l_T.as<float>(), P, p->L.as<float>());
   }
   FMM_CUDA_TRY(cudaGetLastError());
   FMM_TRY(p->far_u.ensure((size_t)n * 3 * sizeof(float)));
   FMM_TRY(p->far_s.ensure((size_t)n * 3 * sizeof(float)));
+  ++g_launches;
   k_l2p<<<(unsigned)p->nleaves, 64, 8 * P * sizeof(float), s>>>(
       p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(), p->c_center.as<double>(),
       p->scal.as<double>(), p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_w.as<float>(),

@@ -9,6 +9,10 @@
 
 using namespace fmm;
 
+namespace fmm {
+int64_t g_launches = 0;
+}
+
 namespace {
 
 int check_params(const fmm_params* q) {
@@ -238,6 +242,8 @@ int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gam
   if (n == 0) return FMM_OK;
   return p2p_direct_all(n, pos, gam, sig, sig_u, vel, dg, (cudaStream_t)stream);
 }
+
+int64_t fmm_kernel_launch_count(void) { return fmm::g_launches; }
 
 int fmm_plan_set_timing(fmm_plan p, int enable) {
   if (!p) return FMM_E_INVAL;

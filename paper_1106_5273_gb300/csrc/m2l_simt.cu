@@ -64,6 +64,7 @@ int m2l_simt(fmm_plan p, cudaStream_t s) {
   }
   size_t sh = (size_t)kRC * p->P * sizeof(float);
   if (sh > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  ++g_launches;
   k_m2l_simt<<<(unsigned)p->ntiles, 3 * kTile, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
                                                          p->st_src.as<int>(), p->T32.as<float>(), p->M.as<float>(),
                                                          p->P, p->tile_cells.as<int>(), p->L.as<float>());

@@ -302,6 +302,7 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     attr = true;
   }
+  ++g_launches;
   k_m2l_tc<<<(unsigned)p->ntiles, kThreads, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
                                                       p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
                                                       p->Mbf.as<__nv_bfloat16>(), p->P, nkc, last,

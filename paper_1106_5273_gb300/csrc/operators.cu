@@ -251,6 +251,7 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
     FMM_TRY(p->Tbf.ensure(tb));
     FMM_CUDA_TRY(cudaMemsetAsync(p->Tbf.ptr, 0, tb, s));
   }
+  ++g_launches;
   k_build_m2l<<<(unsigned)p->n_keys, 256, 0, s>>>(p->ukeys.as<uint64_t>(), (int)p->n_keys, p->prm.p,
                                                    p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(), tc);
   FMM_CUDA_TRY(cudaGetLastError());
@@ -259,6 +260,7 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
 
 int apply_lattice(fmm_plan p, cudaStream_t s) {
   if (!p->prm.periodic || p->prm.images <= 1) return FMM_OK;
+  ++g_launches;
   k_apply_lattice<<<1, 512, 0, s>>>(p->lattice.as<double>(), p->P, p->L.as<float>(), p->M.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;

@@ -313,14 +313,17 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, float* vel, float* dg, 
   if (p->prm.periodic) {
     const int parts = 256;
     FMM_TRY(p->scan_tmp.ensure((size_t)parts * 3 * sizeof(double)));
+    ++g_launches;
     k_dipole_partial<<<parts, 256, 0, s>>>(p->sortA.as<float4>(), p->sortB.as<float4>(), n, scal,
                                            p->scan_tmp.as<double>());
+    ++g_launches;
     k_dipole_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, scal, scal + kScalDipole);
     dip = scal + kScalDipole;
   }
   const int bs = p2p_block(p->prm.ncrit);
   const float blen = p->prm.periodic ? (float)p->prm.box_len : 0.f;
   SigK K0 = make_sigk(ps ? 1.f : sig_u);
+  ++g_launches;
   if (ps)
     k_p2p<true><<<(unsigned)p->nleaves, bs, 0, s>>>(p->leaves.as<int>(), p->p2p_off.as<int2>(),
                                                      p->p2p_sorted.as<int2>(), p->c_begin.as<int>(), p->c_end.as<int>(),
@@ -341,6 +344,7 @@ int p2p_direct_all(int64_t n, const float* pos, const float* gam, const float* s
   const int bs = 128;
   unsigned g = (unsigned)((n + bs - 1) / bs);
   SigK K0 = make_sigk(sig ? 1.f : sig_u);
+  ++g_launches;
   if (sig) k_direct<true><<<g, bs, 0, s>>>(n, pos, gam, sig, K0, vel, dg);
   else k_direct<false><<<g, bs, 0, s>>>(n, pos, gam, sig, K0, vel, dg);
   FMM_CUDA_TRY(cudaGetLastError());

@@ -87,12 +87,15 @@ static void scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tot
                      cudaStream_t s) {
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb <= 1) {
+    ++g_launches;
     k_scan_apply<<<1, kScanThreads, 0, s>>>(in, n, out, nullptr, total_dev);
     return;
   }
   uint32_t* sums = tmp;
+  ++g_launches;
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
   scan_rec(sums, sums, nb, nullptr, tmp + nb + 1, s);
+  ++g_launches;
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, out, sums, total_dev);
 }
 
@@ -194,6 +197,7 @@ __global__ void k_iota(uint32_t* v, int64_t n) {
 
 int iota_u32(uint32_t* v, int64_t n, cudaStream_t s) {
   if (n <= 0) return FMM_OK;
+  ++g_launches;
   k_iota<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
@@ -212,9 +216,11 @@ int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64
   uint32_t* va = v0;
   uint32_t* vb = v1;
   for (int shift = bit_begin; shift < bit_end; shift += 8) {
+    ++g_launches;
     k_sort_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist.as<uint32_t>());
     FMM_TRY(exclusive_scan_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), (int64_t)256 * ntiles, nullptr,
                                scan_tmp, s));
+    ++g_launches;
     k_sort_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, ntiles, hist.as<uint32_t>());
     FMM_CUDA_TRY(cudaGetLastError());
     uint64_t* tk = ka;

@@ -299,6 +299,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
   FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int4), s));
   FMM_TRY(p->p2p_raw.grow_copy(cap_p * sizeof(int4), s));
+  ++g_launches;
   k_trav_init<<<1, 1, 0, s>>>(ta, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(), p->p2p_raw.as<int4>(), dcnt);
   FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -315,6 +316,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     uint32_t* cm = p->tscan0.as<uint32_t>();
     uint32_t* cp = p->tscan1.as<uint32_t>();
     uint32_t* cf = p->tscan2.as<uint32_t>();
+    ++g_launches;
     k_trav_classify<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf);
     FMM_TRY(exclusive_scan_u32(cm, cm, nf, dcnt + 0, p->scan_tmp, s));
     FMM_TRY(exclusive_scan_u32(cp, cp, nf, dcnt + 1, p->scan_tmp, s));
@@ -325,6 +327,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     FMM_TRY(p->m2l_raw.grow_copy((nm + am) * sizeof(int4), s));
     FMM_TRY(p->p2p_raw.grow_copy((np + ap) * sizeof(int4), s));
     FMM_TRY(nxt->ensure((af + 1) * sizeof(int4)));
+    ++g_launches;
     k_trav_emit<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf, (uint32_t)nm,
                                 (uint32_t)np, p->m2l_raw.as<int4>(), p->p2p_raw.as<int4>(), nxt->as<int4>());
     FMM_CUDA_TRY(cudaGetLastError());
@@ -347,6 +350,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     FMM_TRY(p->p2p_sorted.ensure((n + 1) * sizeof(int2)));
     FMM_TRY(p->p2p_off.ensure((p->nleaves + 1) * sizeof(int2)));
     unsigned g = (unsigned)((n + T - 1) / T);
+    ++g_launches;
     k_p2p_keys<<<g, T, 0, s>>>(p->p2p_raw.as<int4>(), n, p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
     int second = 0;
     FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
@@ -355,8 +359,10 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
     unsigned long long* dpairs = reinterpret_cast<unsigned long long*>(p->scal.as<double>() + kScalCount + 2);
     FMM_CUDA_TRY(cudaMemsetAsync(dpairs, 0, sizeof(unsigned long long), s));
+    ++g_launches;
     k_p2p_gather<<<g, T, 0, s>>>(p->p2p_raw.as<int4>(), sv, n, p->p2p_sorted.as<int2>(), p->c_begin.as<int>(),
                                  p->c_end.as<int>(), dpairs);
+    ++g_launches;
     k_p2p_offsets<<<(unsigned)((p->nleaves + T - 1) / T), T, 0, s>>>(p->leaves.as<int>(), (int)p->nleaves, sk, n,
                                                                      p->p2p_off.as<int2>());
     FMM_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(p->pinned) + 64, dpairs, sizeof(unsigned long long),
@@ -387,12 +393,14 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     FMM_TRY(p->lv1.ensure((nc + 1) * sizeof(uint32_t)));
     {
       unsigned gc = (unsigned)((nc + T - 1) / T);
+      ++g_launches;
       k_tile_order_keys<<<gc, T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc, p->lk0.as<uint64_t>(),
                                          p->lv0.as<uint32_t>());
       int second = 0;
       FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
                              p->lv1.as<uint32_t>(), nc, 0, 48, &second, p->sort_hist, p->scan_tmp, s));
       uint32_t* ord = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      ++g_launches;
       k_cell_tiles<<<gc, T, 0, s>>>(li, nc, ord, p->c_tile.as<int>(), p->tile_cells.as<int>());
     }
     FMM_TRY(p->tile_range.ensure((p->ntiles + 1) * sizeof(int2)));
@@ -410,6 +418,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       FMM_TRY(p->ukeys.ensure((n + 1) * sizeof(uint64_t)));
       unsigned g = (unsigned)((n + T - 1) / T);
       int* flag = p->flags.as<int>();
+      ++g_launches;
       k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_key.as<uint64_t>(),
                                  p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), flag);
       int second = 0;
@@ -417,8 +426,10 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
                              p->lv1.as<uint32_t>(), n, 0, 64, &second, p->sort_hist, p->scan_tmp, s));
       uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
       uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      ++g_launches;
       k_unique_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
       FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
+      ++g_launches;
       k_unique_write<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
                                      p->ukeys.as<uint64_t>(), p->m2l_slot.as<uint32_t>());
       FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -426,6 +437,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       p->n_keys = hc[0];
       if (p->n_keys >= (1 << 20)) return FMM_E_CAPACITY;
       // steps
+      ++g_launches;
       k_step_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_tile.as<int>(), p->m2l_slot.as<uint32_t>(),
                                   p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
       FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
@@ -433,6 +445,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
                              p->scan_tmp, s));
       sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
       sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      ++g_launches;
       k_step_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
       FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
       FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -442,9 +455,11 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       FMM_TRY(p->st_slot.ensure((p->n_steps + 1) * sizeof(int)));
       FMM_TRY(p->st_src.ensure((p->n_steps + 1) * kTile * sizeof(int)));
       FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (p->n_steps + 1) * kTile * sizeof(int), s));
+      ++g_launches;
       k_step_write<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
                                    p->m2l_raw.as<int4>(), p->st_tile.as<int>(), p->st_slot.as<int>(),
                                    p->st_src.as<int>());
+      ++g_launches;
       k_tile_ranges<<<(unsigned)((p->n_steps + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)p->n_steps,
                                                                        p->tile_range.as<int2>());
       FMM_CUDA_TRY(cudaGetLastError());

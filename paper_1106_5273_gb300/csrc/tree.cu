@@ -292,11 +292,14 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   unsigned nb = (unsigned)((n + T - 1) / T);
   double* box = p->scal.as<double>();
   if (p->prm.periodic) {
+    ++g_launches;
     k_set_box<<<1, 1, 0, s>>>(p->prm.box_min[0], p->prm.box_min[1], p->prm.box_min[2], p->prm.box_len, box);
   } else {
     int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
     FMM_TRY(p->scan_tmp.ensure((size_t)parts * 6 * sizeof(double)));
+    ++g_launches;
     k_bbox_partial<<<parts, 256, 0, s>>>(pos, n, p->scan_tmp.as<double>());
+    ++g_launches;
     k_bbox_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, box);
   }
   // sigma max (uniform: the value itself)
@@ -304,24 +307,28 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   if (sig) {
     FMM_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(unsigned int), s));
     int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    ++g_launches;
     k_sigma_max<<<parts, 256, 0, s>>>(sig, n, smax);
   }
   uint64_t* k0 = p->keys0.as<uint64_t>();
   uint64_t* k1 = p->keys1.as<uint64_t>();
   uint32_t* v0 = p->vals0.as<uint32_t>();
   uint32_t* v1 = p->vals1.as<uint32_t>();
+  ++g_launches;
   k_keys<<<nb, T, 0, s>>>(pos, n, box, k0, v0);
   FMM_CUDA_TRY(cudaGetLastError());
   int second = 0;
   FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 63, &second, p->sort_hist, p->scan_tmp, s));
   p->skeys = second ? k1 : k0;
   p->sidx = second ? v1 : v0;
+  ++g_launches;
   k_permute<<<nb, T, 0, s>>>(pos, gam, sig, sig_u, p->sidx, n, p->sortA.as<float4>(), p->sortB.as<float4>());
   FMM_CUDA_TRY(cudaGetLastError());
 
   // ---- octree, level by level
   int64_t cap = std::max<int64_t>(64, 4 * n / std::max(1, p->prm.ncrit) + 64);
   if ((int64_t)(p->c_begin.bytes / sizeof(int)) < cap) FMM_TRY(grow_cells(p, cap, s));
+  ++g_launches;
   k_root<<<1, 1, 0, s>>>((int)n, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
                          p->c_parent.as<int>(), p->c_key.as<uint64_t>());
   p->level_begin.assign(1, 0);
@@ -333,6 +340,7 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
     FMM_TRY(p->tcount.ensure((size_t)(ncl + 1) * sizeof(uint32_t)));
     FMM_TRY(p->tscan0.ensure((size_t)(ncl + 1) * sizeof(uint32_t)));
     unsigned g = (unsigned)((ncl + T - 1) / T);
+    ++g_launches;
     k_split_count<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_key.as<uint64_t>(),
                                   lb, le, l, p->prm.ncrit, p->tcount.as<uint32_t>());
     FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ncl,
@@ -342,6 +350,7 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     int64_t nnew = hcount[0];
     if (le + nnew > (int64_t)(p->c_begin.bytes / sizeof(int))) FMM_TRY(grow_cells(p, 2 * (le + nnew), s));
+    ++g_launches;
     k_split_write<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
                                   p->c_parent.as<int>(), p->c_child.as<int>(), p->c_nchild.as<int>(),
                                   p->c_key.as<uint64_t>(), lb, le, l, p->tcount.as<uint32_t>(),
@@ -364,20 +373,26 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   FMM_TRY(p->tcount.ensure((size_t)(nc + 1) * sizeof(uint32_t)));
   FMM_TRY(p->tscan0.ensure((size_t)(nc + 1) * sizeof(uint32_t)));
   unsigned gc = (unsigned)((nc + T - 1) / T);
+  ++g_launches;
   k_centers<<<gc, T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc, box, p->c_center.as<double>(),
                              p->c_radius2.as<unsigned long long>());
+  ++g_launches;
   k_leaf_flags<<<gc, T, 0, s>>>(p->c_nchild.as<int>(), nc, p->tcount.as<uint32_t>());
   FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), nc, p->tscan0.as<uint32_t>() + nc,
                              p->scan_tmp, s));
+  ++g_launches;
   k_leaf_list<<<gc, T, 0, s>>>(p->c_nchild.as<int>(), nc, p->tscan0.as<uint32_t>(), p->leaves.as<int>());
   FMM_CUDA_TRY(cudaMemcpyAsync(hcount, p->tscan0.as<uint32_t>() + nc, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));
   p->nleaves = hcount[0];
+  ++g_launches;
   k_leaf_of<<<(unsigned)((p->nleaves * 32 + T - 1) / T), T, 0, s>>>(p->leaves.as<int>(), (int)p->nleaves,
                                                                    p->c_begin.as<int>(), p->c_end.as<int>(),
                                                                    p->leaf_of.as<int>());
+  ++g_launches;
   k_radius<<<nb, T, 0, s>>>(p->sortA.as<float4>(), n, p->leaf_of.as<int>(), p->c_parent.as<int>(),
                             p->c_center.as<double>(), p->c_radius2.as<unsigned long long>());
+  ++g_launches;
   k_radius_final<<<gc, T, 0, s>>>(p->c_radius2.as<unsigned long long>(), nc, p->c_radius.as<double>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;

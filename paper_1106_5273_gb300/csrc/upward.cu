@@ -140,12 +140,14 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
   const int NC = pp * (pp + 1) / 2;
   size_t sh = (size_t)(kP2MChunk * P + kP2MChunk * 3 + 2 * kP2MChunk * NC) * sizeof(float);
   if (sh > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  ++g_launches;
   k_p2m<<<(unsigned)p->nleaves, 128, sh, s>>>(p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(),
                                               p->c_level.as<int>(), p->c_center.as<double>(), p->scal.as<double>(),
                                               p->sortA.as<float4>(), p->sortB.as<float4>(), pp, p->M.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   for (int l = p->nlevels - 2; l >= 0; --l) {
     int lb = p->level_begin[l], le = p->level_begin[l + 1];
+    ++g_launches;
     k_m2m<<<le - lb, 128, 3 * P * sizeof(float), s>>>(lb, p->c_child.as<int>(), p->c_nchild.as<int>(),
                                                       p->c_key.as<uint64_t>(), p->m2m_T.as<float>(), P,
                                                       p->M.as<float>());
@@ -153,6 +155,7 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
   FMM_CUDA_TRY(cudaGetLastError());
   if (p->last_tc) {
     FMM_TRY(p->Mbf.ensure((size_t)nc * 2 * 3 * 128 * sizeof(__nv_bfloat16)));
+    ++g_launches;
     k_split_bf16<<<2048, 256, 0, s>>>(p->M.as<float>(), nc, P, p->Mbf.as<__nv_bfloat16>());
     FMM_CUDA_TRY(cudaGetLastError());
   }
