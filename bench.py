@@ -29,10 +29,11 @@ METRIC = "FMM Biot-Savart+stretching particles/s at rel-L2<=1e-4"
 UNIT = "particles/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# FP32 flops per P2P pair counted from the CUDA source of pair_acc (FMA = 2):
-# difference 3, r^2 5, cutoff/S/T 26, gamma_j x d 9, u 6, sum S gamma_j 6,
-# T (gamma_i . d) 6, s 6.  Plus 2 MUFU ops (rsqrt, ex2).
-P2P_FLOPS_PER_PAIR = 67
+# FP32 flops per P2P pair counted from the CUDA source of pair_acc (FMA = 2),
+# per pair class: difference 3, r^2 5, S and T (near 21 / mid 20 / far 4),
+# gamma_j x d 9, u 6, sum S gamma_j 6, T (gamma_i . d) 6, s 6; plus MUFU ops
+# (rsqrt and ex2; far pairs rsqrt only).
+P2P_FLOPS = {"near": 62, "mid": 61, "far": 45}
 
 
 def parse():
@@ -251,7 +252,9 @@ def main():
     # roofline of the dominant kernel (P2P), from its CUDA-event time inside the step
     pairs = st.p2p_pairs
     p2p_t = sum(p2p_ms) / len(p2p_ms) * 1e-3
-    achieved = P2P_FLOPS_PER_PAIR * pairs / p2p_t / 1e12
+    flops = (P2P_FLOPS["near"] * st.p2p_pairs_near + P2P_FLOPS["mid"] * st.p2p_pairs_mid
+             + P2P_FLOPS["far"] * st.p2p_pairs_far)
+    achieved = flops / p2p_t / 1e12
     clk_mhz = 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
     traffic = None
@@ -279,14 +282,16 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": "k_p2p", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                         "flops_per_pair": P2P_FLOPS_PER_PAIR, "pairs_per_launch": pairs,
+                         "flops_per_pair": P2P_FLOPS, "pairs_per_launch": pairs,
+                         "pairs_by_class": {"near": st.p2p_pairs_near, "mid": st.p2p_pairs_mid,
+                                            "far": st.p2p_pairs_far},
                          "ms_per_launch": p2p_t * 1e3,
                          "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
             "paper_convention_tflops": 174 * pairs / p2p_t / 1e12,
             "phases_ms": {k: getattr(st, k) for k in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
                                                        "ms_downward", "ms_p2p", "ms_total")},
             "work": {k: getattr(st, k) for k in ("ncells", "nleaves", "nlevels", "p2p_cell_pairs", "p2p_pairs",
-                                                  "m2l_pairs", "m2l_steps", "m2l_keys", "m2l_tensor")},
+                                                  "m2l_pairs", "m2l_steps", "m2l_keys", "m2l_built", "m2l_tensor")},
             "clocks": clk,
             "cpu_baseline": cpu,
         }

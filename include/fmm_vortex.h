@@ -96,6 +96,10 @@ typedef struct {
   int64_t m2l_pairs;      /* (target cell, source cell, image) M2L entries */
   int64_t m2l_steps;      /* (64-cell target tile, translation) GEMM steps */
   int64_t m2l_keys;       /* distinct translation operators */
+  int64_t m2l_built;      /* operators built by this call (the rest came from the plan's cache) */
+  int64_t p2p_pairs_near; /* particle pairs evaluated with the full cutoff and series test */
+  int64_t p2p_pairs_mid;  /* ... with the full cutoff, rho^2 >= 2 guaranteed */
+  int64_t p2p_pairs_far;  /* ... with the singular kernel, rho >= 6.5 guaranteed */
   double ms_tree;         /* phase times in ms (CUDA events), if timing enabled */
   double ms_upward;
   double ms_traverse;

@@ -54,7 +54,9 @@ class Stats(ctypes.Structure):
                 ("nlevels", ctypes.c_int32), ("m2l_tensor", ctypes.c_int32),
                 ("p2p_cell_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("m2l_steps", ctypes.c_int64),
-                ("m2l_keys", ctypes.c_int64), ("ms_tree", ctypes.c_double),
+                ("m2l_keys", ctypes.c_int64), ("m2l_built", ctypes.c_int64),
+                ("p2p_pairs_near", ctypes.c_int64), ("p2p_pairs_mid", ctypes.c_int64),
+                ("p2p_pairs_far", ctypes.c_int64), ("ms_tree", ctypes.c_double),
                 ("ms_upward", ctypes.c_double), ("ms_traverse", ctypes.c_double),
                 ("ms_m2l", ctypes.c_double), ("ms_downward", ctypes.c_double),
                 ("ms_p2p", ctypes.c_double), ("ms_total", ctypes.c_double)]

@@ -79,13 +79,17 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   tm.mark();
   FMM_TRY(downward_pass(p, n, s));
   tm.mark();
-  FMM_TRY(p2p_near(p, n, sig_u, sig ? 1 : 0, vel, dg, s));
+  FMM_TRY(p2p_near(p, n, sig_u, sig ? 1 : 0, smax, vel, dg, s));
   tm.mark();
   // error flags raised by kernels
   int hf = 0;
   FMM_CUDA_TRY(cudaMemcpyAsync(p->pinned, p->flags.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(p->pinned) + 128, p->scal.as<double>() + kScalCount + 4,
+                               3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));
   memcpy(&hf, p->pinned, sizeof(int));
+  unsigned long long cls[3];
+  memcpy(cls, reinterpret_cast<char*>(p->pinned) + 128, sizeof(cls));
   if (hf != 0) return hf;
   fmm_stats& st = p->stats;
   st.n = n;
@@ -98,6 +102,10 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   st.m2l_pairs = p->n_m2l;
   st.m2l_steps = p->n_steps;
   st.m2l_keys = p->n_keys;
+  st.m2l_built = p->n_built;
+  st.p2p_pairs_near = (int64_t)cls[0];
+  st.p2p_pairs_mid = (int64_t)cls[1];
+  st.p2p_pairs_far = (int64_t)cls[2];
   if (p->timing && tm.k == 7) {
     float ms[6];
     for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
@@ -195,7 +203,7 @@ void fmm_plan_destroy(fmm_plan p) {
                   &p->c_nchild, &p->c_key, &p->c_center, &p->c_radius2, &p->c_radius, &p->c_tile, &p->tile_cells, &p->leaves,
                   &p->M, &p->L, &p->Mbf, &p->fr0, &p->fr1, &p->tcount, &p->tmask, &p->tscan0, &p->tscan1,
                   &p->tscan2, &p->p2p_raw, &p->m2l_raw, &p->lk0, &p->lk1, &p->lv0, &p->lv1, &p->p2p_sorted,
-                  &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf, &p->st_tile, &p->st_slot,
+                  &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf, &p->tmiss_keys, &p->tmiss_slots, &p->tslot_map, &p->st_tile, &p->st_slot,
                   &p->st_src, &p->tile_range, &p->scan_tmp, &p->sort_hist, &p->scal, &p->flags};
   for (DBuf* b : bufs) b->release();
   if (p->pinned) cudaFreeHost(p->pinned);

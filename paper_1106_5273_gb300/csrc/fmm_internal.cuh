@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -54,7 +55,13 @@ struct fmm_plan_s {
   fmm::DBuf lk0, lk1, lv0, lv1;                       // list sort ping-pong
   fmm::DBuf p2p_sorted, p2p_off;                      // int2 (b,o) by leaf, CSR offsets per leaf
   fmm::DBuf m2l_key, m2l_slot, ukeys;                 // per pair key, slot; unique keys
-  fmm::DBuf T32, Tbf;                                 // M2L operators
+  fmm::DBuf T32, Tbf;                                 // M2L operator cache [slot]: FP32, BF16 hi/lo
+  std::unordered_map<uint64_t, int> tcache;           // translation key -> cache slot
+  int64_t tcache_cap = 0;
+  fmm::DBuf tmiss_keys, tmiss_slots, tslot_map;       // keys to build, their slots; unique key -> slot
+  std::vector<uint64_t> h_keys;
+  std::vector<int> h_map;
+  int64_t n_built = 0;                                // operators built by the last evaluation
   fmm::DBuf st_tile, st_slot, st_src, tile_range;     // M2L steps
   // scratch
   fmm::DBuf scan_tmp, sort_hist;
@@ -93,7 +100,8 @@ int m2l_tensor(fmm_plan p, cudaStream_t s);
 // downward.cu
 int downward_pass(fmm_plan p, int64_t n, cudaStream_t s);
 // p2p.cu
-int p2p_near(fmm_plan p, int64_t n, float sig_u, int per_particle_sigma, float* vel, float* dg, cudaStream_t s);
+int p2p_near(fmm_plan p, int64_t n, float sig_u, int per_particle_sigma, double smax, float* vel, float* dg,
+             cudaStream_t s);
 int p2p_direct_all(int64_t n, const float* pos, const float* gam, const float* sig, float sig_u, float* vel,
                    float* dg, cudaStream_t s);
 }  // namespace fmm

@@ -3,7 +3,7 @@
 For x = rho/sqrt(2) >= 1 the P2P kernel writes
     g(rho) = 1 - exp(-x^2) * (erfcx(x) + 2x/sqrt(pi)),
 sharing exp(-x^2) with the Gaussian term of the stretching kernel, and
-approximates erfcx(x) = exp(x^2) erfc(x) by a degree-5 polynomial in
+approximates erfcx(x) = exp(x^2) erfc(x) by a degree-3 polynomial in
 y = 1/x on [1/XMAX, 1] (y comes from the rsqrt the kernel computes anyway;
 beyond XMAX = 4.6, exp(-x^2) F < 4e-9 and y is clamped).  The fit minimises
 the relative error of g (weight exp(-x^2)/g) by iteratively reweighted least
@@ -16,7 +16,7 @@ import numpy as np
 from scipy.special import erf, erfcx
 
 XMAX = 4.6
-DEG = 5
+DEG = 3
 
 
 def fit():

@@ -137,16 +137,17 @@ Mat lattice_matrix(int p, int images) {
 
 // ---- device: M2L operator per translation key
 
-__global__ void k_build_m2l(const uint64_t* __restrict__ keys, int nkeys, int p, float* __restrict__ T32,
-                            __nv_bfloat16* __restrict__ Tbf, int tc) {
+__global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __restrict__ slots, int nkeys, int p,
+                            float* __restrict__ T32, __nv_bfloat16* __restrict__ Tbf, int tc) {
   __shared__ cd I[(2 * kPMax - 1) * (2 * kPMax) / 2];
   __shared__ double nu[kNCoefMax];
   __shared__ double rp[kPMax];
   __shared__ int nmp[kNCoefMax];  // real index -> (n, m, part) packed
-  const int key_id = blockIdx.x;
-  if (key_id >= nkeys) return;
+  const int kid = blockIdx.x;
+  if (kid >= nkeys) return;
+  const int key_id = slots[kid];  // cache slot written by this block
   const int P = p * p;
-  uint64_t key = keys[key_id];
+  uint64_t key = keys[kid];
   int delta;
   double tau[3];
   m2l_key_decode(key, &delta, tau);
@@ -161,6 +162,10 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, int nkeys, int p,
     nu[r] = nu_d(n, m);
   }
   if (threadIdx.x < (unsigned)p) rp[threadIdx.x] = ldexp(1.0, delta * (int)threadIdx.x);
+  if (tc) {  // zero this slot's BF16 tiles (padding rows and columns stay zero)
+    uint4* z = reinterpret_cast<uint4*>(Tbf + (size_t)key_id * 2 * 128 * 128);
+    for (int i = threadIdx.x; i < 2 * 128 * 128 / 8; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
     int r = e / P, c = e % P;
@@ -241,20 +246,68 @@ int build_constant_operators(fmm_plan p) {
   return FMM_OK;
 }
 
+__global__ void k_remap_slots(int* __restrict__ st_slot, int64_t ns, const int* __restrict__ map) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ns) st_slot[i] = map[st_slot[i]];
+}
+
+// M2L operators are constants of (translation key, p): the plan keeps them in a
+// cache indexed by key and builds (in FP64, on the device) only the keys it has
+// not seen; the step list is then re-pointed from unique-key index to slot.
 int build_m2l_operators(fmm_plan p, cudaStream_t s) {
   const int P = p->P;
+  p->n_built = 0;
   if (p->n_keys == 0) return FMM_OK;
-  FMM_TRY(p->T32.ensure((size_t)p->n_keys * P * P * sizeof(float)));
-  int tc = p->last_tc;
-  if (tc) {
-    const size_t tb = (size_t)p->n_keys * 2 * 128 * 128 * sizeof(__nv_bfloat16);
-    FMM_TRY(p->Tbf.ensure(tb));
-    FMM_CUDA_TRY(cudaMemsetAsync(p->Tbf.ptr, 0, tb, s));
+  const int64_t nk = p->n_keys;
+  p->h_keys.resize(nk);
+  FMM_CUDA_TRY(cudaMemcpyAsync(p->h_keys.data(), p->ukeys.ptr, nk * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  const int tc = p->last_tc;
+  // bound the cache: start over when it would exceed 1 << 16 operators
+  if ((int64_t)p->tcache.size() + nk > (1 << 16)) p->tcache.clear();
+  p->h_map.resize(nk);
+  std::vector<uint64_t> miss_keys;
+  std::vector<int> miss_slots;
+  for (int64_t i = 0; i < nk; ++i) {
+    auto it = p->tcache.find(p->h_keys[i]);
+    if (it != p->tcache.end()) {
+      p->h_map[i] = it->second;
+    } else {
+      int slot = (int)p->tcache.size();
+      p->tcache.emplace(p->h_keys[i], slot);
+      p->h_map[i] = slot;
+      miss_keys.push_back(p->h_keys[i]);
+      miss_slots.push_back(slot);
+    }
   }
+  const int64_t need = (int64_t)p->tcache.size();
+  if (need > p->tcache_cap) {
+    int64_t cap = std::max<int64_t>(need, p->tcache_cap * 2);
+    FMM_TRY(p->T32.grow_copy((size_t)cap * P * P * sizeof(float), s));
+    FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * 128 * 128 * sizeof(__nv_bfloat16), s));
+    p->tcache_cap = cap;
+  }
+  if (!miss_keys.empty()) {
+    const int64_t nm = (int64_t)miss_keys.size();
+    FMM_TRY(p->tmiss_keys.ensure(nm * sizeof(uint64_t)));
+    FMM_TRY(p->tmiss_slots.ensure(nm * sizeof(int)));
+    FMM_CUDA_TRY(cudaMemcpyAsync(p->tmiss_keys.ptr, miss_keys.data(), nm * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    FMM_CUDA_TRY(cudaMemcpyAsync(p->tmiss_slots.ptr, miss_slots.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
+    ++g_launches;
+    k_build_m2l<<<(unsigned)nm, 256, 0, s>>>(p->tmiss_keys.as<uint64_t>(), p->tmiss_slots.as<int>(), (int)nm,
+                                             p->prm.p, p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(), 1);
+    FMM_CUDA_TRY(cudaGetLastError());
+    p->n_built = nm;
+  }
+  (void)tc;
+  FMM_TRY(p->tslot_map.ensure(nk * sizeof(int)));
+  FMM_CUDA_TRY(cudaMemcpyAsync(p->tslot_map.ptr, p->h_map.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s));
   ++g_launches;
-  k_build_m2l<<<(unsigned)p->n_keys, 256, 0, s>>>(p->ukeys.as<uint64_t>(), (int)p->n_keys, p->prm.p,
-                                                   p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(), tc);
+  k_remap_slots<<<(unsigned)((p->n_steps + 255) / 256), 256, 0, s>>>(p->st_slot.as<int>(), p->n_steps,
+                                                                    p->tslot_map.as<int>());
   FMM_CUDA_TRY(cudaGetLastError());
+  // the host vectors above are read by the copies before they change again
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
   return FMM_OK;
 }
 

@@ -13,8 +13,12 @@
 // self pair is skipped explicitly (its exact value is zero).  Periodic image
 // pairs form the exact FP32 difference first and then add the image shift.
 //
-// One CTA per target leaf, one thread per target particle; the source leaves
-// of the leaf's list are staged through shared memory.
+// One warp per target leaf, two target particles per lane (one when ncrit <=
+// 32); the source leaves of the leaf's list are staged through shared memory
+// in double-buffered chunks.  Each (source leaf, image) entry is classified by
+// a lower bound on its pair distances: the singular kernel where g = 1 to FP32
+// precision (rho >= 6.5), the cutoff without the series test (rho^2 >= 2), or
+// the full form.
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -23,11 +27,17 @@ namespace {
 
 constexpr int kMaxBlock = 128;
 constexpr float kInv4Pi = 0.0795774715459476679f;
-constexpr float kTwoOverSqrtPi = 1.12837916709551257f;
 constexpr float kYmin = 1.0f / 4.6f;
-// erfcx(1/y) ~ sum c_k y^k on [1/4.6, 1] (gen_cutoff_fit.py)
-constexpr float kE0 = -6.087852495e-03f, kE1 = 6.146454486e-01f, kE2 = -1.593122702e-01f,
-                kE3 = -8.516227039e-02f, kE4 = 8.483457562e-02f, kE5 = -2.133410796e-02f;
+// erfcx(1/y) ~ sum c_k y^k on [1/4.6, 1] (gen_cutoff_fit.py, degree 3)
+constexpr float kE0 = -1.202012900e-02f, kE1 = 6.541014877e-01f, kE2 = -2.626216807e-01f,
+                kE3 = 4.812366022e-02f;
+// Source-leaf classes by a lower bound d_min on the pair distance:
+//   kFar : d_min >= 6.5 sigma_max: 1 - g < 4e-9 and exp(-rho^2/2) < 1e-9, so
+//          S = 1/r^3 and T = -3/r^5 exactly in FP32 (singular kernel);
+//   kMid : d_min >= sqrt2 sigma_max: rho^2 >= 2, no series branch needed;
+//   kNear: anything closer (series branch when rho^2 < 2).
+constexpr int kNear = 0, kMid = 1, kFar = 2;
+constexpr double kFarRho = 6.5, kMidRho = 1.4142135623730951;
 
 constexpr double ser_coef(int k) {  // c (-1)^k / (2^k k! (2k+3))
   double d = 2.0 * k + 3.0;
@@ -54,8 +64,8 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 // Constants of one core width sigma.
 struct SigK {
   float kq;   // -log2(e) / (2 sigma^2)
-  float kx;   // 1 / (sqrt2 sigma)
-  float ky;   // sqrt2 sigma
+  float kxc;  // sqrt(2/pi) / sigma   (2x/sqrt(pi) = r kxc)
+  float ky;   // sqrt2 sigma          (1/x = ky / r)
   float kc;   // sqrt(2/pi) / sigma^3
   float ku;   // 1 / sigma^2
   float is3;  // 1 / sigma^3
@@ -67,7 +77,7 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   SigK k;
   double s = (double)sigma;
   k.kq = (float)(-1.4426950408889634 / (2.0 * s * s));
-  k.kx = (float)(1.0 / (1.4142135623730951 * s));
+  k.kxc = (float)(0.79788456080286535588 / s);
   k.ky = (float)(1.4142135623730951 * s);
   k.kc = (float)(0.79788456080286535588 / (s * s * s));
   k.ku = (float)(1.0 / (s * s));
@@ -77,28 +87,36 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   return k;
 }
 
+// S = g/r^3 and T = S'(r)/r for one pair (see the file header).
+template <int MODE>
 __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float& T) {
   const float rinv = rsqrt_approx(r2);
+  const float rinv2 = rinv * rinv;
+  if (MODE == kFar) {
+    S = rinv2 * rinv;
+    T = -3.f * S * rinv2;
+    return;
+  }
   const float q = ex2_approx(r2 * K.kq);
   const float r = r2 * rinv;
-  const float x = r * K.kx;
   const float y = fmaxf(rinv * K.ky, kYmin);
-  float F = fmaf(fmaf(fmaf(fmaf(fmaf(kE5, y, kE4), y, kE3), y, kE2), y, kE1), y, kE0);
-  F = fmaf(x, kTwoOverSqrtPi, F);
+  float F = fmaf(fmaf(fmaf(kE3, y, kE2), y, kE1), y, kE0);
+  F = fmaf(r, K.kxc, F);
   const float g = fmaf(-q, F, 1.f);
-  const float rinv2 = rinv * rinv;
   S = g * rinv2 * rinv;
   T = fmaf(K.kc, q, -3.f * S) * rinv2;
-  const float u = r2 * K.ku;
-  if (u < 2.f) {
-    float sS = cSer[kSerTerms - 1], sT = (float)(kSerTerms - 1) * cSer[kSerTerms - 1];
+  if (MODE == kNear) {
+    const float u = r2 * K.ku;
+    if (u < 2.f) {
+      float sS = cSer[kSerTerms - 1], sT = (float)(kSerTerms - 1) * cSer[kSerTerms - 1];
 #pragma unroll
-    for (int k = kSerTerms - 2; k >= 0; --k) {
-      sS = fmaf(sS, u, cSer[k]);
-      if (k >= 1) sT = fmaf(sT, u, (float)k * cSer[k]);
+      for (int k = kSerTerms - 2; k >= 0; --k) {
+        sS = fmaf(sS, u, cSer[k]);
+        if (k >= 1) sT = fmaf(sT, u, (float)k * cSer[k]);
+      }
+      S = sS * K.is3;
+      T = sT * K.is5;
     }
-    S = sS * K.is3;
-    T = sT * K.is5;
   }
 }
 
@@ -106,11 +124,12 @@ struct Acc {
   float ux, uy, uz, sx, sy, sz, ax, ay, az;
 };
 
+template <int MODE>
 __device__ __forceinline__ void pair_acc(float dx, float dy, float dz, const float4& gj, float gix, float giy,
                                          float giz, const SigK& K, Acc& a) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   float S, T;
-  pair_ST(r2, K, S, T);
+  pair_ST<MODE>(r2, K, S, T);
   const float cx = fmaf(gj.y, dz, -gj.z * dy);
   const float cy = fmaf(gj.z, dx, -gj.x * dz);
   const float cz = fmaf(gj.x, dy, -gj.y * dx);
@@ -126,80 +145,182 @@ __device__ __forceinline__ void pair_acc(float dx, float dy, float dz, const flo
   a.sz = fmaf(td, cz, a.sz);
 }
 
-// MODE 0: plain, 1: with image shift, 2: own leaf (skip the self pair)
-template <bool PS, int MODE>
-__device__ __forceinline__ void source_loop(const float4* sA, const float4* sB, const SigK* sK, int cnt, float xi,
-                                            float yi, float zi, float gix, float giy, float giz, float shx, float shy,
-                                            float shz, int self_j, const SigK& K0, Acc& a) {
-#pragma unroll 4
+// Targets held by one thread.
+template <int TPT>
+struct Tgt {
+  float x[TPT], y[TPT], z[TPT], gx[TPT], gy[TPT], gz[TPT];
+  int self[TPT];  // staged index of the target itself in the current chunk, or -1
+  Acc a[TPT];
+};
+
+template <bool PS, int MODE, bool SHIFT, bool SELF, int TPT>
+__device__ __forceinline__ void run_chunk(const float4* sA, const float4* sB, const SigK* sK, int cnt, Tgt<TPT>& t,
+                                          float shx, float shy, float shz, const SigK& K0) {
+#pragma unroll 2
   for (int j = 0; j < cnt; ++j) {
     const float4 xj = sA[j];
     const float4 gj = sB[j];
-    float dx = xi - xj.x, dy = yi - xj.y, dz = zi - xj.z;
-    if (MODE == 1) {
-      dx += shx;
-      dy += shy;
-      dz += shz;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      float dx = t.x[q] - xj.x, dy = t.y[q] - xj.y, dz = t.z[q] - xj.z;
+      if (SHIFT) {
+        dx += shx;
+        dy += shy;
+        dz += shz;
+      }
+      if (SELF && j == t.self[q]) continue;
+      pair_acc<MODE>(dx, dy, dz, gj, t.gx[q], t.gy[q], t.gz[q], PS ? sK[j] : K0, t.a[q]);
     }
-    if (MODE == 2 && j == self_j) continue;
-    if (PS) pair_acc(dx, dy, dz, gj, gix, giy, giz, sK[j], a);
-    else pair_acc(dx, dy, dz, gj, gix, giy, giz, K0, a);
   }
 }
 
-template <bool PS>
-__global__ void __launch_bounds__(kMaxBlock) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
-                                                   const int2* __restrict__ list, const int* __restrict__ begin,
-                                                   const int* __restrict__ end, const float4* __restrict__ A,
-                                                   const float4* __restrict__ B, const float* __restrict__ far_u,
-                                                   const float* __restrict__ far_s, const uint32_t* __restrict__ sidx,
-                                                   float blen, SigK K0, const double* __restrict__ dip,
-                                                   float* __restrict__ vel, float* __restrict__ dg) {
-  __shared__ float4 sA[kMaxBlock], sB[kMaxBlock];
-  __shared__ SigK sK[PS ? kMaxBlock : 1];
+template <bool PS, int TPT>
+__device__ __forceinline__ void dispatch_chunk(int mode, bool shift, bool self, const float4* sA, const float4* sB,
+                                               const SigK* sK, int cnt, Tgt<TPT>& t, float shx, float shy, float shz,
+                                               const SigK& K0) {
+  if (self) {
+    run_chunk<PS, kNear, false, true, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
+  } else if (mode == kFar) {
+    if (shift) run_chunk<PS, kFar, true, false, TPT>(sA, sB, sK, cnt, t, shx, shy, shz, K0);
+    else run_chunk<PS, kFar, false, false, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
+  } else if (mode == kMid) {
+    if (shift) run_chunk<PS, kMid, true, false, TPT>(sA, sB, sK, cnt, t, shx, shy, shz, K0);
+    else run_chunk<PS, kMid, false, false, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
+  } else {
+    if (shift) run_chunk<PS, kNear, true, false, TPT>(sA, sB, sK, cnt, t, shx, shy, shz, K0);
+    else run_chunk<PS, kNear, false, false, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
+  }
+}
+
+// Class of a (target leaf, source leaf, image) entry from FP64 centres and
+// radii: d_min = |X_A - X_B - o L| - R_A - R_B bounds every pair distance.
+__device__ __forceinline__ int entry_mode(const double* center, const double* radius, int a, int b, int img,
+                                          double blen, double smax) {
+  double d2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    int o = q == 0 ? img / 9 - 1 : (q == 1 ? (img / 3) % 3 - 1 : img % 3 - 1);
+    double dd = center[3 * a + q] - (center[3 * b + q] + o * blen);
+    d2 += dd * dd;
+  }
+  double dmin = sqrt(d2) - radius[a] - radius[b];
+  if (dmin >= kFarRho * smax * (1.0 + 1e-6)) return kFar;
+  if (dmin >= kMidRho * smax * (1.0 + 1e-6)) return kMid;
+  return kNear;
+}
+
+// One warp per target leaf, TPT targets per lane; source chunks of 32*TPT
+// particles double-buffered (the next chunk is loaded into registers while the
+// current one is computed from shared memory).
+template <bool PS, int TPT>
+__global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
+                                            const int2* __restrict__ list, const int* __restrict__ begin,
+                                            const int* __restrict__ end, const double* __restrict__ center,
+                                            const double* __restrict__ radius, const float4* __restrict__ A,
+                                            const float4* __restrict__ B, const float* __restrict__ far_u,
+                                            const float* __restrict__ far_s, const uint32_t* __restrict__ sidx,
+                                            float blen, double blen_d, double smax, SigK K0,
+                                            const double* __restrict__ dip, float* __restrict__ vel,
+                                            float* __restrict__ dg) {
+  constexpr int CH = 32 * TPT;
+  __shared__ float4 sA[2][CH], sB[2][CH];
+  __shared__ SigK sK[2][PS ? CH : 1];
+  const int lane = threadIdx.x;
   const int leaf = leaves[blockIdx.x];
   const int tb = begin[leaf], te = end[leaf];
   const int2 rg = off[blockIdx.x];
   const float dux = dip ? (float)dip[0] : 0.f, duy = dip ? (float)dip[1] : 0.f, duz = dip ? (float)dip[2] : 0.f;
-  for (int t0 = tb; t0 < te; t0 += blockDim.x) {
-    const int i = t0 + threadIdx.x;
-    const bool valid = i < te;
-    float4 xi = valid ? A[i] : make_float4(0.f, 0.f, 0.f, 1.f);
-    float4 gi = valid ? B[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    Acc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int e = rg.x; e < rg.y; ++e) {
-      const int2 ent = list[e];
-      const int src = ent.x, img = ent.y;
-      const int sb = begin[src], se = end[src];
-      const float shx = -(float)(img / 9 - 1) * blen;
-      const float shy = -(float)((img / 3) % 3 - 1) * blen;
-      const float shz = -(float)(img % 3 - 1) * blen;
-      const bool self = (src == leaf) && img == kImageZero;
-      for (int c0 = sb; c0 < se; c0 += blockDim.x) {
-        const int cnt = min((int)blockDim.x, se - c0);
-        __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-          float4 xa = A[c0 + threadIdx.x];
-          sA[threadIdx.x] = xa;
-          sB[threadIdx.x] = B[c0 + threadIdx.x];
-          if (PS) sK[threadIdx.x] = make_sigk(xa.w);
-        }
-        __syncthreads();
-        if (valid) {
-          if (self)
-            source_loop<PS, 2>(sA, sB, sK, cnt, xi.x, xi.y, xi.z, gi.x, gi.y, gi.z, 0.f, 0.f, 0.f, i - c0, K0, a);
-          else if (img != kImageZero)
-            source_loop<PS, 1>(sA, sB, sK, cnt, xi.x, xi.y, xi.z, gi.x, gi.y, gi.z, shx, shy, shz, -1, K0, a);
-          else
-            source_loop<PS, 0>(sA, sB, sK, cnt, xi.x, xi.y, xi.z, gi.x, gi.y, gi.z, 0.f, 0.f, 0.f, -1, K0, a);
+  float4 ra[TPT], rb[TPT];
+  for (int t0 = tb; t0 < te; t0 += CH) {
+    Tgt<TPT> t;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int i = t0 + lane + 32 * q;
+      float4 xi = i < te ? A[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+      float4 gi = i < te ? B[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      t.x[q] = xi.x;
+      t.y[q] = xi.y;
+      t.z[q] = xi.z;
+      t.gx[q] = gi.x;
+      t.gy[q] = gi.y;
+      t.gz[q] = gi.z;
+      t.a[q] = Acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    }
+    // chunk cursor over (list entry, first particle of the chunk)
+    int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0;
+    int buf = 0;
+    if (cur_e < rg.y) {
+      const int se = end[list[cur_e].x];
+      cur_cnt = min(CH, se - cur_c0);
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        const int j = lane + 32 * q;
+        if (j < cur_cnt) {
+          sA[0][j] = A[cur_c0 + j];
+          sB[0][j] = B[cur_c0 + j];
+          if (PS) sK[0][j] = make_sigk(sA[0][j].w);
         }
       }
     }
-    if (valid) {
+    __syncwarp();
+    while (cur_e < rg.y) {
+      // next chunk: advance the cursor and prefetch into registers
+      int ne = cur_e, nc0 = cur_c0 + CH;
+      if (nc0 >= end[list[ne].x]) {
+        ++ne;
+        nc0 = ne < rg.y ? begin[list[ne].x] : 0;
+      }
+      int ncnt = 0;
+      if (ne < rg.y) {
+        ncnt = min(CH, end[list[ne].x] - nc0);
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+          const int j = lane + 32 * q;
+          if (j < ncnt) {
+            ra[q] = A[nc0 + j];
+            rb[q] = B[nc0 + j];
+          }
+        }
+      }
+      // compute the current chunk
+      const int2 ent = list[cur_e];
+      const int img = ent.y;
+      const bool shift = img != kImageZero;
+      const bool self = (ent.x == leaf) && !shift;
+      const int mode = entry_mode(center, radius, leaf, ent.x, img, blen_d, smax);
+      const float shx = -(float)(img / 9 - 1) * blen;
+      const float shy = -(float)((img / 3) % 3 - 1) * blen;
+      const float shz = -(float)(img % 3 - 1) * blen;
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) t.self[q] = self ? (t0 + lane + 32 * q) - cur_c0 : -1;
+      dispatch_chunk<PS, TPT>(mode, shift, self, sA[buf], sB[buf], sK[buf], cur_cnt, t, shx, shy, shz, K0);
+      __syncwarp();
+      buf ^= 1;
+      if (ne < rg.y) {
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+          const int j = lane + 32 * q;
+          if (j < ncnt) {
+            sA[buf][j] = ra[q];
+            sB[buf][j] = rb[q];
+            if (PS) sK[buf][j] = make_sigk(ra[q].w);
+          }
+        }
+      }
+      __syncwarp();
+      cur_e = ne;
+      cur_c0 = nc0;
+      cur_cnt = ncnt;
+    }
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int i = t0 + lane + 32 * q;
+      if (i >= te) continue;
+      const Acc& a = t.a[q];
       const uint32_t o = sidx[i];
-      const float sx = a.sx + (a.ay * gi.z - a.az * gi.y);
-      const float sy = a.sy + (a.az * gi.x - a.ax * gi.z);
-      const float sz = a.sz + (a.ax * gi.y - a.ay * gi.x);
+      const float sx = a.sx + (a.ay * t.gz[q] - a.az * t.gy[q]);
+      const float sy = a.sy + (a.az * t.gx[q] - a.ax * t.gz[q]);
+      const float sz = a.sz + (a.ax * t.gy[q] - a.ay * t.gx[q]);
       if (vel) {
         vel[3 * o] = far_u[3 * i] + kInv4Pi * a.ux + dux;
         vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * a.uy + duy;
@@ -214,7 +335,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_p2p(const int* __restrict__ leave
   }
 }
 
-// All pairs of one array, free space, self pair skipped.
+// All pairs of one array, free space, self pair skipped (near class throughout).
 template <bool PS>
 __global__ void __launch_bounds__(kMaxBlock) k_direct(int64_t n, const float* __restrict__ pos,
                                                       const float* __restrict__ gam, const float* __restrict__ sig,
@@ -223,16 +344,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_direct(int64_t n, const float* __
   __shared__ SigK sK[PS ? kMaxBlock : 1];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < n;
-  float xi = 0.f, yi = 0.f, zi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  Tgt<1> t;
+  t.x[0] = t.y[0] = t.z[0] = t.gx[0] = t.gy[0] = t.gz[0] = 0.f;
   if (valid) {
-    xi = pos[3 * i];
-    yi = pos[3 * i + 1];
-    zi = pos[3 * i + 2];
-    gx = gam[3 * i];
-    gy = gam[3 * i + 1];
-    gz = gam[3 * i + 2];
+    t.x[0] = pos[3 * i];
+    t.y[0] = pos[3 * i + 1];
+    t.z[0] = pos[3 * i + 2];
+    t.gx[0] = gam[3 * i];
+    t.gy[0] = gam[3 * i + 1];
+    t.gz[0] = gam[3 * i + 2];
   }
-  Acc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  t.a[0] = Acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int64_t c0 = 0; c0 < n; c0 += blockDim.x) {
     const int cnt = (int)min((int64_t)blockDim.x, n - c0);
     __syncthreads();
@@ -245,22 +367,23 @@ __global__ void __launch_bounds__(kMaxBlock) k_direct(int64_t n, const float* __
     }
     __syncthreads();
     if (valid) {
-      if (i >= c0 && i < c0 + cnt)
-        source_loop<PS, 2>(sA, sB, sK, cnt, xi, yi, zi, gx, gy, gz, 0.f, 0.f, 0.f, (int)(i - c0), K0, a);
-      else
-        source_loop<PS, 0>(sA, sB, sK, cnt, xi, yi, zi, gx, gy, gz, 0.f, 0.f, 0.f, -1, K0, a);
+      const bool self = i >= c0 && i < c0 + cnt;
+      t.self[0] = self ? (int)(i - c0) : -1;
+      if (self) run_chunk<PS, kNear, false, true, 1>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
+      else run_chunk<PS, kNear, false, false, 1>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
     }
   }
   if (valid) {
+    const Acc& a = t.a[0];
     if (vel) {
       vel[3 * i] = kInv4Pi * a.ux;
       vel[3 * i + 1] = kInv4Pi * a.uy;
       vel[3 * i + 2] = kInv4Pi * a.uz;
     }
     if (dg) {
-      dg[3 * i] = kInv4Pi * (a.sx + (a.ay * gz - a.az * gy));
-      dg[3 * i + 1] = kInv4Pi * (a.sy + (a.az * gx - a.ax * gz));
-      dg[3 * i + 2] = kInv4Pi * (a.sz + (a.ax * gy - a.ay * gx));
+      dg[3 * i] = kInv4Pi * (a.sx + (a.ay * t.gz[0] - a.az * t.gy[0]));
+      dg[3 * i + 1] = kInv4Pi * (a.sy + (a.az * t.gx[0] - a.ax * t.gz[0]));
+      dg[3 * i + 2] = kInv4Pi * (a.sz + (a.ax * t.gy[0] - a.ay * t.gx[0]));
     }
   }
 }
@@ -300,14 +423,33 @@ __global__ void k_dipole_final(const double* __restrict__ part, int nb, const do
   dip[threadIdx.x] = -s / (3.0 * L * L * L);
 }
 
-int p2p_block(int ncrit) {
-  int b = ((ncrit + 31) / 32) * 32;
-  return b < 32 ? 32 : (b > kMaxBlock ? kMaxBlock : b);
+
+// Pair counts per class (near, mid, far) for the work statistics.
+__global__ void k_p2p_classes(const int* __restrict__ leaves, const int2* __restrict__ off,
+                              const int2* __restrict__ list, const int* __restrict__ begin,
+                              const int* __restrict__ end, const double* __restrict__ center,
+                              const double* __restrict__ radius, double blen_d, double smax,
+                              unsigned long long* __restrict__ counts) {
+  const int leaf = leaves[blockIdx.x];
+  const int2 rg = off[blockIdx.x];
+  const unsigned long long nt = (unsigned long long)(end[leaf] - begin[leaf]);
+  unsigned long long c[3] = {0ull, 0ull, 0ull};
+  for (int e = rg.x + (int)threadIdx.x; e < rg.y; e += 32) {
+    const int2 ent = list[e];
+    const int m = (ent.x == leaf && ent.y == kImageZero) ? kNear
+                                                         : entry_mode(center, radius, leaf, ent.x, ent.y, blen_d, smax);
+    c[m] += nt * (unsigned long long)(end[ent.x] - begin[ent.x]);
+  }
+  for (int q = 0; q < 3; ++q) {
+    unsigned long long v = c[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && v) atomicAdd(&counts[q], v);
+  }
 }
 
 }  // namespace
 
-int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, float* vel, float* dg, cudaStream_t s) {
+int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel, float* dg, cudaStream_t s) {
   const double* dip = nullptr;
   double* scal = p->scal.as<double>();
   if (p->prm.periodic) {
@@ -320,21 +462,34 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, float* vel, float* dg, 
     k_dipole_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, scal, scal + kScalDipole);
     dip = scal + kScalDipole;
   }
-  const int bs = p2p_block(p->prm.ncrit);
   const float blen = p->prm.periodic ? (float)p->prm.box_len : 0.f;
+  const double blen_d = p->prm.periodic ? p->prm.box_len : 0.0;
   SigK K0 = make_sigk(ps ? 1.f : sig_u);
+  const unsigned g = (unsigned)p->nleaves;
+  const int* leaves = p->leaves.as<int>();
+  const int2* off = p->p2p_off.as<int2>();
+  const int2* list = p->p2p_sorted.as<int2>();
+  const int* cb = p->c_begin.as<int>();
+  const int* ce = p->c_end.as<int>();
+  const double* cc = p->c_center.as<double>();
+  const double* cr = p->c_radius.as<double>();
+  const float4* A = p->sortA.as<float4>();
+  const float4* B = p->sortB.as<float4>();
+  const float* fu = p->far_u.as<float>();
+  const float* fs = p->far_s.as<float>();
   ++g_launches;
-  if (ps)
-    k_p2p<true><<<(unsigned)p->nleaves, bs, 0, s>>>(p->leaves.as<int>(), p->p2p_off.as<int2>(),
-                                                     p->p2p_sorted.as<int2>(), p->c_begin.as<int>(), p->c_end.as<int>(),
-                                                     p->sortA.as<float4>(), p->sortB.as<float4>(), p->far_u.as<float>(),
-                                                     p->far_s.as<float>(), p->sidx, blen, K0, dip, vel, dg);
-  else
-    k_p2p<false><<<(unsigned)p->nleaves, bs, 0, s>>>(p->leaves.as<int>(), p->p2p_off.as<int2>(),
-                                                      p->p2p_sorted.as<int2>(), p->c_begin.as<int>(),
-                                                      p->c_end.as<int>(), p->sortA.as<float4>(), p->sortB.as<float4>(),
-                                                      p->far_u.as<float>(), p->far_s.as<float>(), p->sidx, blen, K0, dip,
-                                                      vel, dg);
+  if (p->prm.ncrit > 32) {
+    if (ps) k_p2p<true, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
+    else k_p2p<false, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
+  } else {
+    if (ps) k_p2p<true, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
+    else k_p2p<false, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
+  }
+  FMM_CUDA_TRY(cudaGetLastError());
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
+  FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
+  ++g_launches;
+  k_p2p_classes<<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, blen_d, smax, cnt);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

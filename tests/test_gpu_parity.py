@@ -182,6 +182,8 @@ def test_deterministic_and_host_entry():
     u2, s2 = plan.eval(to_dev(w["pos"]), to_dev(w["gamma"]), sigma_uniform=float(w["sigma"]))
     torch.cuda.synchronize()
     assert np.array_equal(u1, u2.cpu().numpy()) and np.array_equal(s1, s2.cpu().numpy())
+    # the second evaluation reuses every cached M2L operator
+    assert plan.stats().m2l_built == 0 and plan.stats().m2l_keys > 0
     uh, sh = plan.eval_host(w["pos"], w["gamma"], sigma_uniform=float(w["sigma"]))
     assert np.array_equal(u1, uh) and np.array_equal(s1, sh)
 
