@@ -164,6 +164,37 @@ int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gam
                                    const float* sigma, float sigma_uniform, float* vel,
                                    float* dgamma, void* cuda_stream);
 
+/*
+ * Allocation-free Morton ordering, for callers that cannot call cudaMalloc:
+ * code under a memory manager that owns every device allocation (a framework
+ * caching allocator, a fixed device-memory budget) or code that must not
+ * trigger the implicit device-wide synchronization cudaMalloc / cudaFree can
+ * cause.  The paper has no counterpart of this entry point.
+ *
+ * Computes the cube (free space: as the plans do; periodic: the given cube),
+ * the 63-bit Morton key of every position (21 bits per axis, x most
+ * significant) and a stable sort of (key, index):
+ *   pos[n][3]     device float32 positions (input)
+ *   periodic      0: free-space cube from the bounding box; 1: box_min/box_len
+ *   box_min[3]    HOST array, read only when periodic
+ *   keys_out[n]   device, the sorted keys
+ *   order_out[n]  device, sorted position -> input index
+ * Identical results to the ordering fmm_eval_velocity_stretching computes
+ * (see fmm_plan_get_order).  Allocates nothing: every temporary lives in one
+ * static device array of about 12.4 MB that exists on every GPU that loads
+ * the library until the process exits.  n must be <= FMM_NOALLOC_MAX_N;
+ * larger n returns FMM_E_CAPACITY and launches nothing.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents; calls whose GPU work overlaps (other
+ * streams, other threads) race on it and give undefined results.  Nothing in
+ * the array needs to start at zero.  Asynchronous on cuda_stream.
+ */
+#define FMM_NOALLOC_MAX_N (1 << 20)
+int fmm_morton_order_noalloc(int64_t n, const float* pos, int periodic, const double* box_min,
+                             double box_len, uint64_t* keys_out, uint32_t* order_out,
+                             void* cuda_stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all plans and entry points; for launch accounting in benchmarks). */
 int64_t fmm_kernel_launch_count(void);

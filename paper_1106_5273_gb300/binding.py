@@ -78,6 +78,7 @@ for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+lib.fmm_morton_order_noalloc.argtypes = [_i64, _vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
 lib.fmm_kernel_launch_count.argtypes = []
 lib.fmm_kernel_launch_count.restype = ctypes.c_int64
 lib.fmm_plan_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
@@ -197,6 +198,23 @@ class Plan:
         m2l = np.zeros((s.m2l_pairs, 3), np.int32)
         _check(lib.fmm_plan_get_lists(self._h, p2p.ctypes.data, m2l.ctypes.data), "fmm_plan_get_lists")
         return p2p, m2l
+
+
+NOALLOC_MAX_N = 1 << 20
+
+
+def morton_order_noalloc(pos, keys_out, order_out, periodic=False, box_min=None, box_len=0.0, stream=None):
+    """fmm_morton_order_noalloc: Morton keys + stable sort without any allocation.
+
+    pos: float32 CUDA tensor [n,3]; keys_out: int64 CUDA tensor [n] (holds the
+    uint64 keys); order_out: int32 CUDA tensor [n] (holds uint32 indices).
+    """
+    n = pos.shape[0]
+    bm = (ctypes.c_double * 3)(*(box_min if box_min is not None else (0.0, 0.0, 0.0)))
+    _check(lib.fmm_morton_order_noalloc(n, _dptr(pos, name="pos"), 1 if periodic else 0, bm, float(box_len),
+                                        ctypes.c_void_p(keys_out.data_ptr()), ctypes.c_void_p(order_out.data_ptr()),
+                                        _stream_ptr(stream)), "fmm_morton_order_noalloc")
+    return keys_out, order_out
 
 
 def kernel_launch_count():

@@ -235,3 +235,44 @@ int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64
 }
 
 }  // namespace fmm
+
+namespace fmm {
+
+// Variants of the scan and sort above that take their scratch as raw device
+// pointers (for callers that provide all memory): scan_tmp must hold
+// scan_scratch_words(n) words, hist 256 * ceil(n/4096) words.
+size_t scan_scratch_words(int64_t n) {
+  size_t need = 0;
+  for (int64_t m = n;;) {
+    int64_t nb = (m + kScanTile - 1) / kScanTile;
+    if (nb <= 1) break;
+    need += (size_t)(nb + 1);
+    m = nb;
+  }
+  return need + 1;
+}
+
+int radix_sort_u64_raw(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bit_begin,
+                       int bit_end, int* in_second, uint32_t* hist, uint32_t* scan_tmp, cudaStream_t s) {
+  *in_second = 0;
+  if (n <= 1) return FMM_OK;
+  int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+  uint64_t* ka = k0;
+  uint64_t* kb = k1;
+  uint32_t* va = v0;
+  uint32_t* vb = v1;
+  for (int shift = bit_begin; shift < bit_end; shift += 8) {
+    ++g_launches;
+    k_sort_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist);
+    scan_rec(hist, hist, (int64_t)256 * ntiles, nullptr, scan_tmp, s);
+    ++g_launches;
+    k_sort_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, ntiles, hist);
+    FMM_CUDA_TRY(cudaGetLastError());
+    std::swap(ka, kb);
+    std::swap(va, vb);
+    *in_second ^= 1;
+  }
+  return FMM_OK;
+}
+
+}  // namespace fmm

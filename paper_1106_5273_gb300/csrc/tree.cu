@@ -399,3 +399,27 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
 }
 
 }  // namespace fmm
+
+namespace fmm {
+
+// Cube and Morton keys into caller-provided memory (same arithmetic as
+// build_tree): partials holds 1024*6 doubles, box 4 doubles.
+int morton_keys_raw(int64_t n, const float* pos, int periodic, const double* box_min, double box_len,
+                    uint64_t* keys, uint32_t* idx, double* partials, double* box, cudaStream_t s) {
+  if (periodic) {
+    ++g_launches;
+    k_set_box<<<1, 1, 0, s>>>(box_min[0], box_min[1], box_min[2], box_len, box);
+  } else {
+    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    ++g_launches;
+    k_bbox_partial<<<parts, 256, 0, s>>>(pos, n, partials);
+    ++g_launches;
+    k_bbox_final<<<1, 32, 0, s>>>(partials, parts, box);
+  }
+  ++g_launches;
+  k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, box, keys, idx);
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+}  // namespace fmm
