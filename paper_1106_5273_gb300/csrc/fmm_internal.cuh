@@ -43,6 +43,7 @@ struct fmm_plan_s {
   fmm::DBuf c_begin, c_end, c_level, c_parent, c_child, c_nchild;  // int32
   fmm::DBuf c_key;                                                  // u64 level-local Morton index
   fmm::DBuf c_center, c_radius2, c_radius;                          // double[3], u64 bits, double
+  fmm::DBuf c_cf;                                                   // float4 (centre, radius) rounded to FP32
   fmm::DBuf c_tile;                                                 // int32 tile*64+slot of each cell
   fmm::DBuf tile_cells;                                             // cell of each (tile, slot) position
   fmm::DBuf leaves;                                                 // leaf cell ids
@@ -63,6 +64,7 @@ struct fmm_plan_s {
   std::vector<int> h_map;
   int64_t n_built = 0;                                // operators built by the last evaluation
   fmm::DBuf st_tile, st_slot, st_src, tile_range;     // M2L steps
+  fmm::DBuf st_ckey, st_fkey;                         // compact / full translation key per step
   // scratch
   fmm::DBuf scan_tmp, sort_hist;
   fmm::DBuf scal;   // small scalars (see kScal*)

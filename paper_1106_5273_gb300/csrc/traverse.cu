@@ -13,6 +13,8 @@
 // Outputs: P2P entries grouped by target leaf (CSR), and M2L entries grouped
 // into steps = (tile of 64 consecutive target cells of one level, translation
 // key), each step carrying the source cell of every tile slot (or -1).
+#include <climits>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -22,23 +24,46 @@ namespace {
 struct TravArgs {
   const double* center;
   const double* radius;
+  const float4* cf;  // FP32 copies of centre and radius
   const int* nchild;
   const int* child;
   double theta, ksig, smax, blen;
+  float thetaf, ksf, blenf, slack0;  // slack0 = 2e-6 * (largest coordinate magnitude + box length)
 };
 
-__device__ inline int interact(const TravArgs& t, int a, int b, int o) {
+// The MAC exactly as the oracle evaluates it: FP64, explicitly rounded, fixed order.
+__device__ inline bool mac_fp64(const TravArgs& t, int a, int b, int o) {
   double sh[3] = {(double)(o / 9 - 1) * t.blen, (double)((o / 3) % 3 - 1) * t.blen, (double)(o % 3 - 1) * t.blen};
-  double d2 = 0.0;
   double dx = __dsub_rn(t.center[3 * a], __dadd_rn(t.center[3 * b], sh[0]));
   double dy = __dsub_rn(t.center[3 * a + 1], __dadd_rn(t.center[3 * b + 1], sh[1]));
   double dz = __dsub_rn(t.center[3 * a + 2], __dadd_rn(t.center[3 * b + 2], sh[2]));
-  d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   double dist = __dsqrt_rn(d2);
   double sr = __dadd_rn(t.radius[a], t.radius[b]);
-  if (sr < __dmul_rn(t.theta, dist) && __dsub_rn(dist, sr) >= __dmul_rn(t.ksig, t.smax)) return 0;  // M2L
-  if (t.nchild[a] == 0 && t.nchild[b] == 0) return 1;                                                // P2P
-  return 2;                                                                                          // push
+  return sr < __dmul_rn(t.theta, dist) && __dsub_rn(dist, sr) >= __dmul_rn(t.ksig, t.smax);
+}
+
+// FP32 screen with a bound on its rounding error (centres and radii rounded
+// to FP32, shift, differences, square root: well below slack); only pairs
+// inside the slack of a decision boundary take the FP64 test, so every
+// decision equals the FP64 one.
+__device__ inline int interact(const TravArgs& t, int a, int b, int o) {
+  const float4 A = t.cf[a], B = t.cf[b];
+  const float sx = (float)(o / 9 - 1) * t.blenf, sy = (float)((o / 3) % 3 - 1) * t.blenf,
+              sz = (float)(o % 3 - 1) * t.blenf;
+  const float dx = A.x - (B.x + sx), dy = A.y - (B.y + sy), dz = A.z - (B.z + sz);
+  const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float sr = A.w + B.w;
+  const float slack = t.slack0 + 1e-6f * (d + sr + t.ksf);
+  const float v1 = t.thetaf * d - sr;  // M2L needs v1 > 0
+  const float v2 = d - sr - t.ksf;     // and v2 >= 0
+  bool m2l;
+  if (v1 <= -slack || v2 <= -slack) m2l = false;
+  else if (v1 > slack && v2 > slack) m2l = true;
+  else m2l = mac_fp64(t, a, b, o);
+  if (m2l) return 0;                                          // M2L
+  if (t.nchild[a] == 0 && t.nchild[b] == 0) return 1;        // P2P
+  return 2;                                                   // push
 }
 
 // Initial pairs (root, root + o L), one thread, in image order.
@@ -191,19 +216,98 @@ __global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __res
   vals[i] = (uint32_t)i;
 }
 
+// Field ranges of the translation keys (delta, tx, ty, tz) for the compact
+// encoding of the step sort.
+__global__ void k_key_ranges(const uint64_t* __restrict__ keys, int n, int* __restrict__ rng) {
+  int lo[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX}, hi[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    const int f[4] = {(int)(k >> 57) - 32, (int)key_field(k, 38), (int)key_field(k, 19), (int)key_field(k, 0)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lo[q] = min(lo[q], f[q]);
+      hi[q] = max(hi[q], f[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&rng[2 * q], lo[q]);
+      atomicMax(&rng[2 * q + 1], hi[q]);
+    }
+  }
+}
+
+struct KeyPack {
+  int lo[4];
+  int shift[4];  // bit position of each field in the compact key
+  int bits;      // total compact key bits
+};
+
+__device__ inline uint64_t compact_key(uint64_t k, const KeyPack& kp) {
+  const int f[4] = {(int)(k >> 57) - 32, (int)key_field(k, 38), (int)key_field(k, 19), (int)key_field(k, 0)};
+  uint64_t c = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c |= (uint64_t)(f[q] - kp.lo[q]) << kp.shift[q];
+  return c;
+}
+
+// (tile, compact key, slot in tile) sort keys of the M2L pairs.
+__global__ void k_step_keys2(const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
+                             const int* __restrict__ ctile, KeyPack kp, uint64_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int ts = ctile[raw[i].x];
+  const uint64_t tile = (uint64_t)(ts / kTile), s_in = (uint64_t)(ts % kTile);
+  keys[i] = (tile << (kp.bits + 6)) | (compact_key(fkeys[i], kp) << 6) | s_in;
+  vals[i] = (uint32_t)i;
+}
+
+__global__ void k_step_write2(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
+                              const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
+                              const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int kbits,
+                              int* __restrict__ st_tile, uint64_t* __restrict__ st_ckey,
+                              uint64_t* __restrict__ st_fkey, int* __restrict__ st_src) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t s = e[i] + f[i] - 1u;
+  const uint64_t key = k[i];
+  if (f[i]) {
+    st_tile[s] = (int)(key >> (kbits + 6));
+    st_ckey[s] = (key >> 6) & ((1ull << kbits) - 1ull);
+    st_fkey[s] = fkeys[idx[i]];
+  }
+  st_src[(size_t)s * kTile + (key & 63ull)] = raw[idx[i]].y;
+}
+
+__global__ void k_step_slots(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, int ns,
+                             const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
+                             const uint64_t* __restrict__ st_fkey, uint64_t* __restrict__ ukeys,
+                             int* __restrict__ st_slot) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  const uint32_t slot = e[i] + f[i] - 1u;
+  if (f[i]) ukeys[slot] = st_fkey[sidx[i]];
+  st_slot[sidx[i]] = (int)slot;
+}
+
+__global__ void k_copy_u64_iota(const uint64_t* __restrict__ in, int n, uint64_t* __restrict__ out,
+                                uint32_t* __restrict__ idx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    out[i] = in[i];
+    idx[i] = (uint32_t)i;
+  }
+}
+
 __global__ void k_unique_flags(const uint64_t* __restrict__ k, int n, uint32_t* __restrict__ f) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) f[i] = (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
-}
-
-__global__ void k_unique_write(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
-                               const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
-                               uint64_t* __restrict__ ukeys, uint32_t* __restrict__ slot_of_pair) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t s = e[i] + f[i] - 1u;
-  if (f[i]) ukeys[s] = k[i];
-  slot_of_pair[idx[i]] = s;
 }
 
 // Tiles group the cells of one level by child octant (then Morton order):
@@ -229,34 +333,9 @@ __global__ void k_cell_tiles(LevelInfo li, int nc, const uint32_t* __restrict__ 
   tcell[q] = c;
 }
 
-__global__ void k_step_keys(const int4* __restrict__ raw, int n, const int* __restrict__ ctile,
-                            const uint32_t* __restrict__ slot, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int ts = ctile[raw[i].x];
-  uint64_t tile = (uint64_t)(ts / kTile), s_in = (uint64_t)(ts % kTile);
-  keys[i] = (tile << 26) | ((uint64_t)slot[i] << 6) | s_in;
-  vals[i] = (uint32_t)i;
-}
-
 __global__ void k_step_flags(const uint64_t* __restrict__ k, int n, uint32_t* __restrict__ f) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) f[i] = (i == 0 || (k[i] >> 6) != (k[i - 1] >> 6)) ? 1u : 0u;
-}
-
-__global__ void k_step_write(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
-                             const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
-                             const int4* __restrict__ raw, int* __restrict__ st_tile, int* __restrict__ st_slot,
-                             int* __restrict__ st_src) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t s = e[i] + f[i] - 1u;
-  uint64_t key = k[i];
-  if (f[i]) {
-    st_tile[s] = (int)(key >> 26);
-    st_slot[s] = (int)((key >> 6) & 0xfffffull);
-  }
-  st_src[(size_t)s * kTile + (key & 63ull)] = raw[idx[i]].y;
 }
 
 __global__ void k_tile_ranges(const int* __restrict__ st_tile, int ns, int2* __restrict__ tr) {
@@ -281,12 +360,24 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   TravArgs ta;
   ta.center = p->c_center.as<double>();
   ta.radius = p->c_radius.as<double>();
+  ta.cf = p->c_cf.as<float4>();
   ta.nchild = p->c_nchild.as<int>();
   ta.child = p->c_child.as<int>();
   ta.theta = (double)p->prm.theta;
   ta.ksig = (double)p->prm.sigma_sep;
   ta.smax = smax;
   ta.blen = p->prm.periodic ? p->prm.box_len : 0.0;
+  {
+    double hbox[4];
+    FMM_CUDA_TRY(cudaMemcpyAsync(hbox, p->scal.as<double>() + kScalBox, sizeof(hbox), cudaMemcpyDeviceToHost, s));
+    FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    double cmax = 0.0;
+    for (int q = 0; q < 3; ++q) cmax = std::max(cmax, std::max(std::fabs(hbox[q]), std::fabs(hbox[q] + hbox[3])));
+    ta.thetaf = (float)ta.theta;
+    ta.ksf = (float)(ta.ksig * ta.smax);
+    ta.blenf = (float)ta.blen;
+    ta.slack0 = (float)(2e-6 * (cmax + hbox[3]));
+  }
   const int nimg = p->prm.periodic ? 27 : 1;
   const int img0 = p->prm.periodic ? 0 : kImageZero;
   uint32_t* hc = reinterpret_cast<uint32_t*>(p->pinned);
@@ -412,56 +503,85 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       FMM_TRY(p->lk1.ensure((n + 1) * sizeof(uint64_t)));
       FMM_TRY(p->lv0.ensure((n + 1) * sizeof(uint32_t)));
       FMM_TRY(p->lv1.ensure((n + 1) * sizeof(uint32_t)));
-      FMM_TRY(p->m2l_slot.ensure((n + 1) * sizeof(uint32_t)));
+      FMM_TRY(p->m2l_key.ensure((n + 1) * sizeof(uint64_t)));
       FMM_TRY(p->tcount.ensure((n + 1) * sizeof(uint32_t)));
       FMM_TRY(p->tscan0.ensure((n + 1) * sizeof(uint32_t)));
-      FMM_TRY(p->ukeys.ensure((n + 1) * sizeof(uint64_t)));
       unsigned g = (unsigned)((n + T - 1) / T);
       int* flag = p->flags.as<int>();
+      // 1. full translation keys and their field ranges
       ++g_launches;
       k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_key.as<uint64_t>(),
-                                 p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), flag);
+                                 p->m2l_key.as<uint64_t>(), p->lv0.as<uint32_t>(), flag);
+      int* drng = reinterpret_cast<int*>(p->scal.as<double>() + kScalCount + 8);
+      const int init[8] = {INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN};
+      int* hr = reinterpret_cast<int*>(reinterpret_cast<char*>(p->pinned) + 256);
+      memcpy(hr, init, sizeof(init));
+      FMM_CUDA_TRY(cudaMemcpyAsync(drng, hr, sizeof(init), cudaMemcpyHostToDevice, s));
+      ++g_launches;
+      k_key_ranges<<<std::min<unsigned>(g, 1024u), T, 0, s>>>(p->m2l_key.as<uint64_t>(), n, drng);
+      FMM_CUDA_TRY(cudaMemcpyAsync(hr, drng, sizeof(init), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA_TRY(cudaStreamSynchronize(s));
+      KeyPack kp;
+      int sh = 0;
+      for (int q = 3; q >= 0; --q) {
+        kp.lo[q] = hr[2 * q];
+        int range = hr[2 * q + 1] - hr[2 * q];
+        int b = 0;
+        while ((1ll << b) <= (long long)range) ++b;
+        kp.shift[q] = sh;
+        sh += b;
+      }
+      kp.bits = sh;
+      int tb = 1;
+      while ((1ll << tb) < (long long)p->ntiles) ++tb;
+      if (tb + kp.bits + 6 > 63) return FMM_E_DEPTH;
+      // 2. sort pairs by (tile, compact key, slot): consecutive runs are the steps
+      ++g_launches;
+      k_step_keys2<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
+                                   p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
       int second = 0;
       FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
-                             p->lv1.as<uint32_t>(), n, 0, 64, &second, p->sort_hist, p->scan_tmp, s));
+                             p->lv1.as<uint32_t>(), n, 0, tb + kp.bits + 6, &second, p->sort_hist, p->scan_tmp, s));
       uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
       uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
-      ++g_launches;
-      k_unique_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
-      FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
-      ++g_launches;
-      k_unique_write<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
-                                     p->ukeys.as<uint64_t>(), p->m2l_slot.as<uint32_t>());
-      FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-      FMM_CUDA_TRY(cudaStreamSynchronize(s));
-      p->n_keys = hc[0];
-      if (p->n_keys >= (1 << 20)) return FMM_E_CAPACITY;
-      // steps
-      ++g_launches;
-      k_step_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_tile.as<int>(), p->m2l_slot.as<uint32_t>(),
-                                  p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
-      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
-                             p->lv1.as<uint32_t>(), n, 0, 26 + bits_for(p->ntiles), &second, p->sort_hist,
-                             p->scan_tmp, s));
-      sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
-      sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
       ++g_launches;
       k_step_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
       FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
       FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
       FMM_CUDA_TRY(cudaStreamSynchronize(s));
       p->n_steps = hc[0];
-      FMM_TRY(p->st_tile.ensure((p->n_steps + 1) * sizeof(int)));
-      FMM_TRY(p->st_slot.ensure((p->n_steps + 1) * sizeof(int)));
-      FMM_TRY(p->st_src.ensure((p->n_steps + 1) * kTile * sizeof(int)));
-      FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (p->n_steps + 1) * kTile * sizeof(int), s));
+      const int64_t ns = p->n_steps;
+      FMM_TRY(p->st_tile.ensure((ns + 1) * sizeof(int)));
+      FMM_TRY(p->st_slot.ensure((ns + 1) * sizeof(int)));
+      FMM_TRY(p->st_src.ensure((ns + 1) * kTile * sizeof(int)));
+      FMM_TRY(p->st_ckey.ensure((ns + 1) * sizeof(uint64_t)));
+      FMM_TRY(p->st_fkey.ensure((ns + 1) * sizeof(uint64_t)));
+      FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (ns + 1) * kTile * sizeof(int), s));
       ++g_launches;
-      k_step_write<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
-                                   p->m2l_raw.as<int4>(), p->st_tile.as<int>(), p->st_slot.as<int>(),
-                                   p->st_src.as<int>());
+      k_step_write2<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
+                                    p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), kp.bits, p->st_tile.as<int>(),
+                                    p->st_ckey.as<uint64_t>(), p->st_fkey.as<uint64_t>(), p->st_src.as<int>());
       ++g_launches;
-      k_tile_ranges<<<(unsigned)((p->n_steps + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)p->n_steps,
-                                                                       p->tile_range.as<int2>());
+      k_tile_ranges<<<(unsigned)((ns + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)ns, p->tile_range.as<int2>());
+      // 3. distinct translations among the steps -> operator slots
+      FMM_TRY(p->ukeys.ensure((ns + 1) * sizeof(uint64_t)));
+      unsigned gs = (unsigned)((ns + T - 1) / T);
+      ++g_launches;
+      k_copy_u64_iota<<<gs, T, 0, s>>>(p->st_ckey.as<uint64_t>(), (int)ns, p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
+      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                             p->lv1.as<uint32_t>(), ns, 0, std::max(kp.bits, 1), &second, p->sort_hist, p->scan_tmp,
+                             s));
+      sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
+      sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      ++g_launches;
+      k_unique_flags<<<gs, T, 0, s>>>(sk, (int)ns, p->tcount.as<uint32_t>());
+      FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ns, dcnt, p->scan_tmp, s));
+      ++g_launches;
+      k_step_slots<<<gs, T, 0, s>>>(sk, sv, (int)ns, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
+                                    p->st_fkey.as<uint64_t>(), p->ukeys.as<uint64_t>(), p->st_slot.as<int>());
+      FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA_TRY(cudaStreamSynchronize(s));
+      p->n_keys = hc[0];
       FMM_CUDA_TRY(cudaGetLastError());
     }
   }

@@ -266,9 +266,13 @@ __global__ void k_radius(const float4* __restrict__ A, int64_t n, const int* __r
   }
 }
 
-__global__ void k_radius_final(const unsigned long long* __restrict__ r2bits, int nc, double* __restrict__ R) {
+__global__ void k_radius_final(const unsigned long long* __restrict__ r2bits, int nc, const double* __restrict__ center,
+                               double* __restrict__ R, float4* __restrict__ cf) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < nc) R[c] = __dsqrt_rn(__longlong_as_double((long long)r2bits[c]));
+  if (c >= nc) return;
+  const double r = __dsqrt_rn(__longlong_as_double((long long)r2bits[c]));
+  R[c] = r;
+  cf[c] = make_float4((float)center[3 * c], (float)center[3 * c + 1], (float)center[3 * c + 2], (float)r);
 }
 
 }  // namespace
@@ -393,7 +397,9 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   k_radius<<<nb, T, 0, s>>>(p->sortA.as<float4>(), n, p->leaf_of.as<int>(), p->c_parent.as<int>(),
                             p->c_center.as<double>(), p->c_radius2.as<unsigned long long>());
   ++g_launches;
-  k_radius_final<<<gc, T, 0, s>>>(p->c_radius2.as<unsigned long long>(), nc, p->c_radius.as<double>());
+  FMM_TRY(p->c_cf.ensure((size_t)nc * sizeof(float4)));
+  k_radius_final<<<gc, T, 0, s>>>(p->c_radius2.as<unsigned long long>(), nc, p->c_center.as<double>(),
+                                  p->c_radius.as<double>(), p->c_cf.as<float4>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
