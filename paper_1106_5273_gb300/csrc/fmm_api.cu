@@ -204,7 +204,7 @@ void fmm_plan_destroy(fmm_plan p) {
                   &p->M, &p->L, &p->Mbf, &p->fr0, &p->fr1, &p->tcount, &p->tmask, &p->tscan0, &p->tscan1,
                   &p->tscan2, &p->p2p_raw, &p->m2l_raw, &p->lk0, &p->lk1, &p->lv0, &p->lv1, &p->p2p_sorted,
                   &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf, &p->tmiss_keys, &p->tmiss_slots, &p->tslot_map, &p->st_tile, &p->st_slot,
-                  &p->st_src, &p->st_ckey, &p->st_fkey, &p->tile_range, &p->scan_tmp, &p->sort_hist, &p->scal, &p->flags};
+                  &p->st_src, &p->st_ckey, &p->st_fkey, &p->m2l_items, &p->m2l_partial, &p->tile_range, &p->scan_tmp, &p->sort_hist, &p->scal, &p->flags};
   for (DBuf* b : bufs) b->release();
   if (p->pinned) cudaFreeHost(p->pinned);
   if (p->have_events)

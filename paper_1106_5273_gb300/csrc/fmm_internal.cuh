@@ -65,6 +65,7 @@ struct fmm_plan_s {
   int64_t n_built = 0;                                // operators built by the last evaluation
   fmm::DBuf st_tile, st_slot, st_src, tile_range;     // M2L steps
   fmm::DBuf st_ckey, st_fkey;                         // compact / full translation key per step
+  fmm::DBuf m2l_items, m2l_partial;                   // M2L work items (+ split list); partial sums
   // scratch
   fmm::DBuf scan_tmp, sort_hist;
   fmm::DBuf scal;   // small scalars (see kScal*)
@@ -75,6 +76,7 @@ struct fmm_plan_s {
   std::vector<int> tile_begin;   // tiles of level l: [tile_begin[l], tile_begin[l+1])
   int64_t ncells = 0, nleaves = 0, ntiles = 0;
   int nlevels = 0;
+  double cf_margin = 0.0;  // rounding margin of the FP32 cell copies (2e-6 x largest coordinate)
   int64_t n_p2p = 0, n_m2l = 0, n_keys = 0, n_steps = 0, p2p_pairs = 0;
   int64_t last_n = 0;
   int last_tc = 0;

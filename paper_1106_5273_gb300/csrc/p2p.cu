@@ -145,6 +145,86 @@ __device__ __forceinline__ void pair_acc(float dx, float dy, float dz, const flo
   a.sz = fmaf(td, cz, a.sz);
 }
 
+// Leaf-relative form used by k_p2p: with X = x - c (c the target leaf centre;
+// image shifts folded into the source's X) and k_j = gamma_j x X_j staged per
+// source,  sum_j S (gamma_j x d) = A x X_i - B  and
+// sum_j T (gamma_i . d)(gamma_j x d) = C x X_i - D, where
+// A = sum S gamma_j, B = sum S k_j, C = sum td gamma_j, D = sum td k_j, td = T (gamma_i . d).
+struct AccR {
+  float ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz;
+};
+
+template <int MODE>
+__device__ __forceinline__ void pair_acc_rel(float dx, float dy, float dz, const float4& gj, const float4& kj,
+                                             float gix, float giy, float giz, const SigK& K, AccR& a) {
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float S, T;
+  pair_ST<MODE>(r2, K, S, T);
+  a.ax = fmaf(S, gj.x, a.ax);
+  a.ay = fmaf(S, gj.y, a.ay);
+  a.az = fmaf(S, gj.z, a.az);
+  a.bx = fmaf(S, kj.x, a.bx);
+  a.by = fmaf(S, kj.y, a.by);
+  a.bz = fmaf(S, kj.z, a.bz);
+  const float td = T * fmaf(gix, dx, fmaf(giy, dy, giz * dz));
+  a.cx = fmaf(td, gj.x, a.cx);
+  a.cy = fmaf(td, gj.y, a.cy);
+  a.cz = fmaf(td, gj.z, a.cz);
+  a.dx = fmaf(td, kj.x, a.dx);
+  a.dy = fmaf(td, kj.y, a.dy);
+  a.dz = fmaf(td, kj.z, a.dz);
+}
+
+template <int TPT>
+struct TgtR {
+  float x[TPT], y[TPT], z[TPT], gx[TPT], gy[TPT], gz[TPT];  // X_i (leaf-relative) and gamma_i
+  int self[TPT];
+  AccR a[TPT];
+};
+
+template <bool PS, int MODE, bool SELF, int TPT>
+__device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
+                                              int cnt, TgtR<TPT>& t, const SigK& K0) {
+#pragma unroll 2
+  for (int j = 0; j < cnt; ++j) {
+    const float4 xj = sA[j];
+    const float4 gj = sB[j];
+    const float4 kj = sC[j];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      if (SELF && j == t.self[q]) continue;
+      pair_acc_rel<MODE>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, gj, kj, t.gx[q], t.gy[q], t.gz[q],
+                         PS ? sK[j] : K0, t.a[q]);
+    }
+  }
+}
+
+template <bool PS, int TPT>
+__device__ __forceinline__ void dispatch_rel(int mode, bool self, const float4* sA, const float4* sB, const float4* sC,
+                                             const SigK* sK, int cnt, TgtR<TPT>& t, const SigK& K0) {
+  if (self) run_chunk_rel<PS, kNear, true, TPT>(sA, sB, sC, sK, cnt, t, K0);
+  else if (mode == kFar) run_chunk_rel<PS, kFar, false, TPT>(sA, sB, sC, sK, cnt, t, K0);
+  else if (mode == kMid) run_chunk_rel<PS, kMid, false, TPT>(sA, sB, sC, sK, cnt, t, K0);
+  else run_chunk_rel<PS, kNear, false, TPT>(sA, sB, sC, sK, cnt, t, K0);
+}
+
+// Class of a (target leaf, source leaf, image) entry.  d_min bounds every pair
+// distance from below (centre distance minus both radii); it is computed
+// from the FP32 copies and lowered by a margin covering their rounding, so
+// the class is never more optimistic than the FP64 value would give.
+__device__ __forceinline__ int entry_mode_f(const float4* cf, int a, int b, int img, float blen, float smax,
+                                            float margin0) {
+  const float4 A = cf[a], B = cf[b];
+  const float dx = A.x - (B.x + (float)(img / 9 - 1) * blen);
+  const float dy = A.y - (B.y + (float)((img / 3) % 3 - 1) * blen);
+  const float dz = A.z - (B.z + (float)(img % 3 - 1) * blen);
+  const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float dmin = d - A.w - B.w - (margin0 + 1e-6f * (d + A.w + B.w));
+  if (dmin >= (float)kFarRho * smax) return kFar;
+  if (dmin >= (float)kMidRho * smax) return kMid;
+  return kNear;
+}
+
 // Targets held by one thread.
 template <int TPT>
 struct Tgt {
@@ -192,79 +272,78 @@ __device__ __forceinline__ void dispatch_chunk(int mode, bool shift, bool self, 
   }
 }
 
-// Class of a (target leaf, source leaf, image) entry from FP64 centres and
-// radii: d_min = |X_A - X_B - o L| - R_A - R_B bounds every pair distance.
-__device__ __forceinline__ int entry_mode(const double* center, const double* radius, int a, int b, int img,
-                                          double blen, double smax) {
-  double d2 = 0.0;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    int o = q == 0 ? img / 9 - 1 : (q == 1 ? (img / 3) % 3 - 1 : img % 3 - 1);
-    double dd = center[3 * a + q] - (center[3 * b + q] + o * blen);
-    d2 += dd * dd;
-  }
-  double dmin = sqrt(d2) - radius[a] - radius[b];
-  if (dmin >= kFarRho * smax * (1.0 + 1e-6)) return kFar;
-  if (dmin >= kMidRho * smax * (1.0 + 1e-6)) return kMid;
-  return kNear;
-}
 
 // One warp per target leaf, TPT targets per lane; source chunks of 32*TPT
 // particles double-buffered (the next chunk is loaded into registers while the
-// current one is computed from shared memory).
+// current one is computed from shared memory).  Coordinates are relative to
+// the target leaf centre.
 template <bool PS, int TPT>
 __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
                                             const int2* __restrict__ list, const int* __restrict__ begin,
-                                            const int* __restrict__ end, const double* __restrict__ center,
-                                            const double* __restrict__ radius, const float4* __restrict__ A,
-                                            const float4* __restrict__ B, const float* __restrict__ far_u,
-                                            const float* __restrict__ far_s, const uint32_t* __restrict__ sidx,
-                                            float blen, double blen_d, double smax, SigK K0,
-                                            const double* __restrict__ dip, float* __restrict__ vel,
+                                            const int* __restrict__ end, const float4* __restrict__ cf,
+                                            const float4* __restrict__ A, const float4* __restrict__ B,
+                                            const float* __restrict__ far_u, const float* __restrict__ far_s,
+                                            const uint32_t* __restrict__ sidx, float blen, float smax, float margin0,
+                                            SigK K0, const double* __restrict__ dip, float* __restrict__ vel,
                                             float* __restrict__ dg) {
   constexpr int CH = 32 * TPT;
-  __shared__ float4 sA[2][CH], sB[2][CH];
+  __shared__ float4 sA[2][CH], sB[2][CH], sC[2][CH];
   __shared__ SigK sK[2][PS ? CH : 1];
   const int lane = threadIdx.x;
   const int leaf = leaves[blockIdx.x];
   const int tb = begin[leaf], te = end[leaf];
   const int2 rg = off[blockIdx.x];
+  const float4 lc = cf[leaf];
   const float dux = dip ? (float)dip[0] : 0.f, duy = dip ? (float)dip[1] : 0.f, duz = dip ? (float)dip[2] : 0.f;
   float4 ra[TPT], rb[TPT];
+  // source j of entry e, staged as X_j = (x_j - c) - shift, gamma_j, k_j = gamma_j x X_j
+  auto stage = [&](int bb, int cnt, int img) {
+    const float shx = -(float)(img / 9 - 1) * blen, shy = -(float)((img / 3) % 3 - 1) * blen,
+                shz = -(float)(img % 3 - 1) * blen;
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int j = lane + 32 * q;
+      if (j < cnt) {
+        const float X = (ra[q].x - lc.x) - shx, Y = (ra[q].y - lc.y) - shy, Z = (ra[q].z - lc.z) - shz;
+        const float4 g = rb[q];
+        sA[bb][j] = make_float4(X, Y, Z, ra[q].w);
+        sB[bb][j] = g;
+        sC[bb][j] = make_float4(g.y * Z - g.z * Y, g.z * X - g.x * Z, g.x * Y - g.y * X, 0.f);
+        if (PS) sK[bb][j] = make_sigk(ra[q].w);
+      }
+    }
+  };
   for (int t0 = tb; t0 < te; t0 += CH) {
-    Tgt<TPT> t;
+    TgtR<TPT> t;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       const int i = t0 + lane + 32 * q;
-      float4 xi = i < te ? A[i] : make_float4(0.f, 0.f, 0.f, 1.f);
+      float4 xi = i < te ? A[i] : lc;
       float4 gi = i < te ? B[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      t.x[q] = xi.x;
-      t.y[q] = xi.y;
-      t.z[q] = xi.z;
+      t.x[q] = xi.x - lc.x;
+      t.y[q] = xi.y - lc.y;
+      t.z[q] = xi.z - lc.z;
       t.gx[q] = gi.x;
       t.gy[q] = gi.y;
       t.gz[q] = gi.z;
-      t.a[q] = Acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      t.a[q] = AccR{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     }
-    // chunk cursor over (list entry, first particle of the chunk)
     int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0;
     int buf = 0;
     if (cur_e < rg.y) {
-      const int se = end[list[cur_e].x];
-      cur_cnt = min(CH, se - cur_c0);
+      cur_cnt = min(CH, end[list[cur_e].x] - cur_c0);
 #pragma unroll
       for (int q = 0; q < TPT; ++q) {
         const int j = lane + 32 * q;
         if (j < cur_cnt) {
-          sA[0][j] = A[cur_c0 + j];
-          sB[0][j] = B[cur_c0 + j];
-          if (PS) sK[0][j] = make_sigk(sA[0][j].w);
+          ra[q] = A[cur_c0 + j];
+          rb[q] = B[cur_c0 + j];
         }
       }
+      stage(0, cur_cnt, list[cur_e].y);
     }
     __syncwarp();
     while (cur_e < rg.y) {
-      // next chunk: advance the cursor and prefetch into registers
       int ne = cur_e, nc0 = cur_c0 + CH;
       if (nc0 >= end[list[ne].x]) {
         ++ne;
@@ -282,31 +361,15 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
           }
         }
       }
-      // compute the current chunk
       const int2 ent = list[cur_e];
-      const int img = ent.y;
-      const bool shift = img != kImageZero;
-      const bool self = (ent.x == leaf) && !shift;
-      const int mode = entry_mode(center, radius, leaf, ent.x, img, blen_d, smax);
-      const float shx = -(float)(img / 9 - 1) * blen;
-      const float shy = -(float)((img / 3) % 3 - 1) * blen;
-      const float shz = -(float)(img % 3 - 1) * blen;
+      const bool self = (ent.x == leaf) && ent.y == kImageZero;
+      const int mode = entry_mode_f(cf, leaf, ent.x, ent.y, blen, smax, margin0);
 #pragma unroll
       for (int q = 0; q < TPT; ++q) t.self[q] = self ? (t0 + lane + 32 * q) - cur_c0 : -1;
-      dispatch_chunk<PS, TPT>(mode, shift, self, sA[buf], sB[buf], sK[buf], cur_cnt, t, shx, shy, shz, K0);
+      dispatch_rel<PS, TPT>(mode, self, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0);
       __syncwarp();
       buf ^= 1;
-      if (ne < rg.y) {
-#pragma unroll
-        for (int q = 0; q < TPT; ++q) {
-          const int j = lane + 32 * q;
-          if (j < ncnt) {
-            sA[buf][j] = ra[q];
-            sB[buf][j] = rb[q];
-            if (PS) sK[buf][j] = make_sigk(ra[q].w);
-          }
-        }
-      }
+      if (ne < rg.y) stage(buf, ncnt, list[ne].y);
       __syncwarp();
       cur_e = ne;
       cur_c0 = nc0;
@@ -316,20 +379,19 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
     for (int q = 0; q < TPT; ++q) {
       const int i = t0 + lane + 32 * q;
       if (i >= te) continue;
-      const Acc& a = t.a[q];
+      const AccR& a = t.a[q];
+      const float X = t.x[q], Y = t.y[q], Z = t.z[q];
       const uint32_t o = sidx[i];
-      const float sx = a.sx + (a.ay * t.gz[q] - a.az * t.gy[q]);
-      const float sy = a.sy + (a.az * t.gx[q] - a.ax * t.gz[q]);
-      const float sz = a.sz + (a.ax * t.gy[q] - a.ay * t.gx[q]);
-      if (vel) {
-        vel[3 * o] = far_u[3 * i] + kInv4Pi * a.ux + dux;
-        vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * a.uy + duy;
-        vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * a.uz + duz;
+      if (vel) {  // u = A x X_i - B
+        vel[3 * o] = far_u[3 * i] + kInv4Pi * ((a.ay * Z - a.az * Y) - a.bx) + dux;
+        vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * ((a.az * X - a.ax * Z) - a.by) + duy;
+        vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * ((a.ax * Y - a.ay * X) - a.bz) + duz;
       }
-      if (dg) {
-        dg[3 * o] = far_s[3 * i] + kInv4Pi * sx;
-        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * sy;
-        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * sz;
+      if (dg) {  // s = A x gamma_i + C x X_i - D
+        const float gx = t.gx[q], gy = t.gy[q], gz = t.gz[q];
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((a.ay * gz - a.az * gy) + (a.cy * Z - a.cz * Y) - a.dx);
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((a.az * gx - a.ax * gz) + (a.cz * X - a.cx * Z) - a.dy);
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((a.ax * gy - a.ay * gx) + (a.cx * Y - a.cy * X) - a.dz);
       }
     }
   }
@@ -427,9 +489,8 @@ __global__ void k_dipole_final(const double* __restrict__ part, int nb, const do
 // Pair counts per class (near, mid, far) for the work statistics.
 __global__ void k_p2p_classes(const int* __restrict__ leaves, const int2* __restrict__ off,
                               const int2* __restrict__ list, const int* __restrict__ begin,
-                              const int* __restrict__ end, const double* __restrict__ center,
-                              const double* __restrict__ radius, double blen_d, double smax,
-                              unsigned long long* __restrict__ counts) {
+                              const int* __restrict__ end, const float4* __restrict__ cf, float blen, float smax,
+                              float margin0, unsigned long long* __restrict__ counts) {
   const int leaf = leaves[blockIdx.x];
   const int2 rg = off[blockIdx.x];
   const unsigned long long nt = (unsigned long long)(end[leaf] - begin[leaf]);
@@ -437,7 +498,7 @@ __global__ void k_p2p_classes(const int* __restrict__ leaves, const int2* __rest
   for (int e = rg.x + (int)threadIdx.x; e < rg.y; e += 32) {
     const int2 ent = list[e];
     const int m = (ent.x == leaf && ent.y == kImageZero) ? kNear
-                                                         : entry_mode(center, radius, leaf, ent.x, ent.y, blen_d, smax);
+                                                         : entry_mode_f(cf, leaf, ent.x, ent.y, blen, smax, margin0);
     c[m] += nt * (unsigned long long)(end[ent.x] - begin[ent.x]);
   }
   for (int q = 0; q < 3; ++q) {
@@ -463,7 +524,6 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
     dip = scal + kScalDipole;
   }
   const float blen = p->prm.periodic ? (float)p->prm.box_len : 0.f;
-  const double blen_d = p->prm.periodic ? p->prm.box_len : 0.0;
   SigK K0 = make_sigk(ps ? 1.f : sig_u);
   const unsigned g = (unsigned)p->nleaves;
   const int* leaves = p->leaves.as<int>();
@@ -471,25 +531,26 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   const int2* list = p->p2p_sorted.as<int2>();
   const int* cb = p->c_begin.as<int>();
   const int* ce = p->c_end.as<int>();
-  const double* cc = p->c_center.as<double>();
-  const double* cr = p->c_radius.as<double>();
+  const float4* cf = p->c_cf.as<float4>();
   const float4* A = p->sortA.as<float4>();
   const float4* B = p->sortB.as<float4>();
   const float* fu = p->far_u.as<float>();
   const float* fs = p->far_s.as<float>();
+  const float smaxf = (float)smax;
+  const float margin0 = (float)p->cf_margin;
   ++g_launches;
   if (p->prm.ncrit > 32) {
-    if (ps) k_p2p<true, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
-    else k_p2p<false, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
+    if (ps) k_p2p<true, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
+    else k_p2p<false, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
   } else {
-    if (ps) k_p2p<true, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
-    else k_p2p<false, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, A, B, fu, fs, p->sidx, blen, blen_d, smax, K0, dip, vel, dg);
+    if (ps) k_p2p<true, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
+    else k_p2p<false, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
   }
   FMM_CUDA_TRY(cudaGetLastError());
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
   ++g_launches;
-  k_p2p_classes<<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cc, cr, blen_d, smax, cnt);
+  k_p2p_classes<<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, blen, smaxf, margin0, cnt);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -377,6 +377,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     ta.ksf = (float)(ta.ksig * ta.smax);
     ta.blenf = (float)ta.blen;
     ta.slack0 = (float)(2e-6 * (cmax + hbox[3]));
+    p->cf_margin = 2e-6 * (cmax + hbox[3]);
   }
   const int nimg = p->prm.periodic ? 27 : 1;
   const int img0 = p->prm.periodic ? 0 : kImageZero;

@@ -159,8 +159,8 @@ def test_edge_sizes(n):
 
 def test_coincident_points_hit_depth_cap():
     # every particle at the same point: the tree stops at level 21 with one
-    # over-full leaf; velocity is exactly zero (d = 0), stretching is the
-    # S(0) gamma_j x gamma_i sum.
+    # over-full leaf; the velocity is zero (d = 0; the leaf-relative sums give
+    # it to rounding), the stretching is the S(0) gamma_j x gamma_i sum.
     from oracle import direct as od
     n = 100
     rng = np.random.default_rng(3)
@@ -170,8 +170,8 @@ def test_coincident_points_hit_depth_cap():
     plan, u, s = run_fmm(w, 4, 0.5, 8, m2l_mode=1)
     st = plan.stats()
     assert st.nlevels == 22
-    assert np.all(u == 0)
     ud, sd = od.direct(pos, gam, pos, gam, 0.1, skip_self=True)
+    assert np.abs(u).max() <= 1e-7 * np.abs(sd).max()
     assert rel_l2(s, sd) < 1e-5
 
 
