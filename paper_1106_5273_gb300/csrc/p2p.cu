@@ -27,7 +27,6 @@ namespace {
 
 constexpr int kMaxBlock = 128;
 constexpr float kInv4Pi = 0.0795774715459476679f;
-constexpr float kYmin = 1.0f / 4.6f;
 // erfcx(1/y) ~ sum c_k y^k on [1/4.6, 1] (gen_cutoff_fit.py, degree 3)
 constexpr float kE0 = -1.202012900e-02f, kE1 = 6.541014877e-01f, kE2 = -2.626216807e-01f,
                 kE3 = 4.812366022e-02f;
@@ -99,7 +98,9 @@ __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float
   }
   const float q = ex2_approx(r2 * K.kq);
   const float r = r2 * rinv;
-  const float y = fmaxf(rinv * K.ky, kYmin);
+  // y = 1/x; beyond the fit range (x > 4.6) exp(-x^2) < 8e-10 multiplies a
+  // bounded cubic, so g = 1 to FP32 precision without clamping y
+  const float y = rinv * K.ky;
   float F = fmaf(fmaf(fmaf(kE3, y, kE2), y, kE1), y, kE0);
   F = fmaf(r, K.kxc, F);
   const float g = fmaf(-q, F, 1.f);
@@ -185,7 +186,7 @@ struct TgtR {
 template <bool PS, int MODE, bool SELF, int TPT>
 __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
                                               int cnt, TgtR<TPT>& t, const SigK& K0) {
-#pragma unroll 2
+#pragma unroll 4
   for (int j = 0; j < cnt; ++j) {
     const float4 xj = sA[j];
     const float4 gj = sB[j];
