@@ -13,6 +13,11 @@ taylor_green(...) Closed form for strengths gamma_j = omega_TG(x_j) h^3 on a
                   full lattice: the blob velocity equals u_TG exp(-3 sigma^2/2)
                   at the lattice points (all modes have |k|^2 = 3; aliases are
                   damped by exp(-sigma^2 (2 pi/h)^2 / 2)).
+spectral_field    Velocity and stretching of blobs whose strengths sample a
+                  band-limited periodic vorticity (modes k, |k| < n/2) on the
+                  full lattice: the blob field is the mode sum damped by
+                  exp(-sigma^2 |k|^2 / 2) (aliases are damped to e^{-28} at
+                  sigma = 1.2 h).
 cubic_image_sum   Brute-force sum over a cube of (2M+1)^3 images, i.e. the
                   lattice sum taken in cubic order, which differs from the
                   Fourier form by the uniform term of dipole_velocity().
@@ -114,3 +119,24 @@ def dipole_velocity(xs, gs, box_len):
     xs = np.asarray(xs, np.float64)
     gs = np.asarray(gs, np.float64)
     return np.cross(xs, gs).sum(0) / (3.0 * float(box_len) ** 3)
+
+
+def spectral_field(modes, uhat, x, gamma, sigma):
+    """u, s at x[n,3] for the field sum_k uhat(k) e^{ik.x} + c.c., damped by exp(-sigma^2 k^2/2).
+
+    modes: integer wave vectors [m,3] (one of each +-k pair); uhat: [m,3].
+    s = (gamma . grad) u uses the strengths gamma [n,3] at the same points.
+    """
+    k = np.asarray(modes, np.float64)
+    c = np.asarray(uhat) * np.exp(-0.5 * float(sigma) ** 2 * (k * k).sum(1))[:, None]
+    x = np.asarray(x, np.float64)
+    g = np.asarray(gamma, np.float64)
+    u = np.zeros((x.shape[0], 3))
+    s = np.zeros((x.shape[0], 3))
+    for c0 in range(0, k.shape[0], 2048):
+        kc = k[c0:c0 + 2048]
+        ph = np.exp(1j * (x @ kc.T))  # [n, m]
+        cc = c[c0:c0 + 2048]
+        u += 2.0 * np.real(ph @ cc)
+        s += 2.0 * np.real((ph * (1j * (g @ kc.T))) @ cc)
+    return u, s

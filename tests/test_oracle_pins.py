@@ -208,6 +208,20 @@ def test_taylor_green_closed_form_matches_fourier():
     assert np.linalg.norm(sf - st) < 1e-6 * np.linalg.norm(st)
 
 
+def test_spectral_field_matches_fourier_sum_of_the_blobs():
+    # the generator's modes give the exact blob field up to FP32 rounding of gamma
+    w = workloads.random_spectrum(12, k0=2.0, kmax=4)
+    x = w["pos"].astype(np.float64)
+    g = w["gamma"].astype(np.float64)
+    sig = float(w["sigma"])
+    uf, sf = periodic.fourier(x, g, x, g, sig, w["box_len"], 8)
+    us, ss = periodic.spectral_field(w["modes"], w["uhat"], x, g, sig)
+    assert np.linalg.norm(us - uf) < 2e-6 * np.linalg.norm(uf)
+    assert np.linalg.norm(ss - sf) < 2e-6 * np.linalg.norm(sf)
+    # a random field carries a net dipole, unlike Taylor-Green
+    assert np.linalg.norm(periodic.dipole_velocity(x - np.pi, g, w["box_len"])) > 1e-3 * np.abs(uf).max()
+
+
 # ---------------------------------------------------------------- cartesian ---
 
 def test_taylor_coefficients_of_inverse_r():

@@ -65,7 +65,14 @@ def taylor_green(n=128):
 
 
 def random_spectrum(n=64, k0=4.0, seed=BASE_SEED + 3, kmax=None):
-    """Random-phase solenoidal field on an n^3 lattice; returns modes too."""
+    """Random-phase solenoidal field on an n^3 lattice; returns its Fourier modes too.
+
+    Modes k (integer wave vectors, one of each +-k pair) with |k| <= kmax carry
+    u_hat(k) = P_perp(k) xi(k) sqrt(E(k) / (4 pi k^2)), xi complex Gaussian,
+    E(k) = k^4 exp(-2 (k/k0)^2), scaled to u_rms = 1; the vorticity at the
+    lattice points (i+1/2)h is the real part of 2 sum_k i k x u_hat e^{i k.x},
+    evaluated by an inverse FFT (the half-cell offset as a phase factor).
+    """
     g = rng(seed)
     L = 2.0 * math.pi
     h = L / n
@@ -76,7 +83,6 @@ def random_spectrum(n=64, k0=4.0, seed=BASE_SEED + 3, kmax=None):
     k = np.stack([KX.ravel(), KY.ravel(), KZ.ravel()], 1).astype(np.float64)
     kk = np.sqrt((k * k).sum(1))
     keep = (kk > 0) & (kk <= kmax)
-    # one representative per +-k pair (Hermitian symmetry)
     first = (k[:, 0] > 0) | ((k[:, 0] == 0) & (k[:, 1] > 0)) | ((k[:, 0] == 0) & (k[:, 1] == 0) & (k[:, 2] > 0))
     keep &= first
     k = k[keep]
@@ -85,26 +91,24 @@ def random_spectrum(n=64, k0=4.0, seed=BASE_SEED + 3, kmax=None):
     xi = g.standard_normal((k.shape[0], 3)) + 1j * g.standard_normal((k.shape[0], 3))
     khat = k / kk[:, None]
     xi = xi - (xi * khat).sum(1)[:, None] * khat  # solenoidal projection
-    amp = np.sqrt(E / (4.0 * math.pi * kk ** 2))
-    uhat = xi * amp[:, None]
-    i = (np.arange(n) + 0.5) * h
-    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    uhat = xi * np.sqrt(E / (4.0 * math.pi * kk ** 2))[:, None]
+    # u_rms over the lattice = sqrt(2 sum |u_hat|^2) for a sum over +-k pairs
+    uhat /= math.sqrt(2.0 * (np.abs(uhat) ** 2).sum())
+    what = 1j * np.cross(k, uhat)
+    # grid spectrum: f(x_i) = sum_k [c(k) e^{i k h/2}] e^{i k . (i h)}, both k and -k
+    ki = k.astype(np.int64)
+    grid = np.zeros((3, n, n, n), np.complex128)
+    ph = np.exp(0.5j * h * k.sum(1))
+    for sgn, coef, pf in ((1, what, ph), (-1, np.conj(what), np.conj(ph))):
+        idx = tuple((sgn * ki[:, a]) % n for a in range(3))
+        for c in range(3):
+            np.add.at(grid[c], idx, coef[:, c] * pf)
+    w = np.stack([np.real(np.fft.ifftn(grid[c])) * n ** 3 for c in range(3)], -1).reshape(-1, 3)
+    i1 = (np.arange(n) + 0.5) * h
+    X, Y, Z = np.meshgrid(i1, i1, i1, indexing="ij")
     pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
-    pos32 = pos.astype(np.float32)
-    x = pos32.astype(np.float64)
-    u = np.zeros_like(x)
-    w = np.zeros_like(x)
-    for c0 in range(0, k.shape[0], 256):
-        kc = k[c0:c0 + 256]
-        ph = np.exp(1j * (x @ kc.T))
-        uc = uhat[c0:c0 + 256]
-        u += 2.0 * np.real(ph @ uc)
-        w += 2.0 * np.real(ph @ (1j * np.cross(kc, uc)))
-    scale = 1.0 / math.sqrt((u * u).sum(1).mean())
-    uhat *= scale
-    w *= scale
     gamma = w * h ** 3
-    return dict(pos=pos32, gamma=gamma.astype(np.float32), sigma=np.float32(1.2 * h),
+    return dict(pos=pos.astype(np.float32), gamma=gamma.astype(np.float32), sigma=np.float32(1.2 * h),
                 periodic=True, box_min=np.zeros(3), box_len=L, p=10, theta=0.4, ncrit=64,
                 images=3, modes=k, uhat=uhat, name="random-spectrum-%d^3" % n)
 
