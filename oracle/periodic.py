@@ -16,8 +16,10 @@ taylor_green(...) Closed form for strengths gamma_j = omega_TG(x_j) h^3 on a
 spectral_field    Velocity and stretching of blobs whose strengths sample a
                   band-limited periodic vorticity (modes k, |k| < n/2) on the
                   full lattice: the blob field is the mode sum damped by
-                  exp(-sigma^2 |k|^2 / 2) (aliases are damped to e^{-28} at
-                  sigma = 1.2 h).
+                  exp(-sigma^2 |k|^2 / 2), up to lattice aliases k + (2 pi/h) m,
+                  m != 0, damped by exp(-sigma^2 (2 pi/h - kmax)^2 / 2)
+                  (1.5e-6 at n = 64, sigma = 1.2 h, kmax = 20, times the
+                  spectrum's own e^-50 at |k| = 20).
 cubic_image_sum   Brute-force sum over a cube of (2M+1)^3 images, i.e. the
                   lattice sum taken in cubic order, which differs from the
                   Fourier form by the uniform term of dipole_velocity().

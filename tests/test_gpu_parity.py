@@ -127,6 +127,34 @@ def test_fmm_periodic_random_matches_fourier():
     assert rel_l2(u, uf) < 1.5 * rel_l2(ref.u, uf) + TOL_U
 
 
+def _spectrum_check(n, sample=4096):
+    """Random-phase spectrum blobs (E ~ k^4 exp(-2 (k/k0)^2), k0 = 4) in the
+    periodic cube, p=10, theta=0.4, ncrit=64, 3^3 images + lattice operator,
+    against the exact blob field of the generating modes on sampled targets.
+    The field carries a net dipole sum x x gamma, so this pins the dipole term."""
+    from oracle import periodic as op
+    w = workloads.random_spectrum(n)
+    plan, u, s = run_fmm(w, 10, 0.4, 64, m2l_mode=0)
+    N = w["pos"].shape[0]
+    idx = np.random.default_rng(7).choice(N, size=min(sample, N), replace=False)
+    us, ss = op.spectral_field(w["modes"], w["uhat"], w["pos"][idx].astype(np.float64),
+                               w["gamma"][idx].astype(np.float64), float(w["sigma"]))
+    eu, es = rel_l2(u[idx], us), rel_l2(s[idx], ss)
+    assert eu < 1e-4, eu
+    assert es < 1e-3, es
+    return plan
+
+
+def test_fmm_random_spectrum_64():
+    _spectrum_check(64)
+
+
+def test_fmm_random_spectrum_512_full_size():
+    """134,217,728 blobs (512^3): the full-size spectrum workload, sampled targets."""
+    plan = _spectrum_check(512)
+    assert plan.stats().n == 512 ** 3
+
+
 def test_fmm_per_particle_sigma_and_plummer():
     from oracle import direct as od
     w = workloads.plummer(3000)
