@@ -149,6 +149,41 @@ int fmm_eval_velocity_stretching_host(fmm_plan plan, int64_t n, const float* pos
                                       float sigma_uniform, float* vel, float* dgamma,
                                       void* cuda_stream);
 
+/*
+ * Batched evaluation: nprob independent problems (no interaction between
+ * them) in one pass of the method -- one forest of octrees, one traversal,
+ * one set of kernel launches for all of them.  Problem k owns the particles
+ * [offsets[k], offsets[k+1]) of the concatenated arrays.
+ *   offsets[nprob+1]  HOST int64, offsets[0] = 0, non-decreasing,
+ *                     offsets[nprob] = n <= n_max; empty problems are allowed
+ *   pos, gamma        device [n][3] float32, concatenated
+ *   sigma             device [n] per-particle core widths, or NULL ...
+ *   sigma_prob        ... then HOST [nprob] float32, one core width per problem (> 0)
+ *   boxes             HOST [nprob][4] double (box_min xyz, side) of each
+ *                     periodic cube when the plan is periodic; ignored (may
+ *                     be NULL) for a free-space plan, where every problem gets
+ *                     its own bounding cube as in fmm_eval_velocity_stretching
+ *   vel, dgamma       device [n][3] float32 outputs (either may be NULL)
+ * The plan supplies p, theta, ncrit, images, sigma_sep and m2l_mode for all
+ * problems.  The tree of each problem stops at level FMM_BATCH_DEPTH (16)
+ * instead of 21.  The result of each problem does not depend on the other
+ * problems of the batch: every sum runs in a fixed order and every constant
+ * (cube, sigma, class bounds, dipole term) is the problem's own, so a problem
+ * gives bit-identical outputs alone (nprob = 1) and in any batch.
+ * nprob <= FMM_BATCH_MAX.  Returns FMM_E_INVAL for bad offsets, sigma or
+ * boxes.  Same stream and blocking behaviour as fmm_eval_velocity_stretching.
+ * (Sec. 3's method applied to many problems at once; the paper has no batch.)
+ */
+#define FMM_BATCH_MAX (1 << 15)
+#define FMM_BATCH_DEPTH 16
+int fmm_eval_batch(fmm_plan plan, int32_t nprob, const int64_t* offsets, const float* pos, const float* gamma,
+                   const float* sigma, const float* sigma_prob, const double* boxes, float* vel,
+                   float* dgamma, void* cuda_stream);
+
+/* Bytes of device memory the plan holds now (its workspace grows to the
+ * largest evaluation seen and is kept for the next one). */
+int64_t fmm_plan_device_bytes(fmm_plan plan);
+
 /* Release every resource of the plan (synchronizes the device). NULL is ok. */
 void fmm_plan_destroy(fmm_plan plan);
 

@@ -78,6 +78,9 @@ for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+lib.fmm_eval_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+lib.fmm_plan_device_bytes.argtypes = [_vp]
+lib.fmm_plan_device_bytes.restype = _i64
 lib.fmm_morton_order_noalloc.argtypes = [_i64, _vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
 lib.fmm_kernel_launch_count.argtypes = []
 lib.fmm_kernel_launch_count.restype = ctypes.c_int64
@@ -164,6 +167,33 @@ class Plan:
             vel.ctypes.data, dgamma.ctypes.data, _stream_ptr(stream)), "fmm_eval_velocity_stretching_host")
         return vel, dgamma
 
+    def eval_batch(self, offsets, pos, gamma, sigma=None, sigma_prob=None, boxes=None, vel=None, dgamma=None,
+                   stream=None):
+        """fmm_eval_batch: problems k = [offsets[k], offsets[k+1]) of the concatenated torch CUDA
+        tensors; sigma_prob (one core width per problem) and boxes ([nprob, 4] periodic cubes)
+        are host arrays.  Returns (vel, dgamma)."""
+        import numpy as np
+        import torch
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        nprob = off.shape[0] - 1
+        n = pos.shape[0]
+        if vel is None:
+            vel = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        if dgamma is None:
+            dgamma = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        sp = None if sigma_prob is None else np.ascontiguousarray(sigma_prob, dtype=np.float32)
+        bx = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64)
+        _check(lib.fmm_eval_batch(
+            self._h, nprob, off.ctypes.data, _dptr(pos, name="pos"), _dptr(gamma, name="gamma"),
+            _dptr(sigma, name="sigma"), None if sp is None else sp.ctypes.data,
+            None if bx is None else bx.ctypes.data, _dptr(vel, name="vel"), _dptr(dgamma, name="dgamma"),
+            _stream_ptr(stream)), "fmm_eval_batch")
+        return vel, dgamma
+
+    def device_bytes(self):
+        """Device memory the plan holds (fmm_plan_device_bytes)."""
+        return int(lib.fmm_plan_device_bytes(self._h))
+
     def set_timing(self, on=True):
         _check(lib.fmm_plan_set_timing(self._h, 1 if on else 0), "fmm_plan_set_timing")
 
@@ -201,6 +231,8 @@ class Plan:
 
 
 NOALLOC_MAX_N = 1 << 20
+BATCH_MAX = 1 << 15
+BATCH_DEPTH = 16
 
 
 def morton_order_noalloc(pos, keys_out, order_out, periodic=False, box_min=None, box_len=0.0, stream=None):

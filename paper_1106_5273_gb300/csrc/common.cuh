@@ -4,14 +4,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/fmm_vortex.h"
 
 namespace fmm {
 
-// Kernel launches issued by this library (host counter, not thread safe).
-extern int64_t g_launches;
+// Kernel launches issued by this library (all host threads).
+extern std::atomic<int64_t> g_launches;
 
 constexpr int kMaxLevel = 21;      // 63-bit Morton keys, 3 bits per level (Sec. 3.2)
 constexpr int kPMax = 16;          // expansion degrees 0..15

@@ -53,6 +53,7 @@ __device__ inline float2 lget(const float* Lp, int N, int M) {
 __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, const int* __restrict__ begin,
                                             const int* __restrict__ end, const int* __restrict__ level,
                                             const double* __restrict__ center, const double* __restrict__ box,
+                                            const int* __restrict__ cseg,
                                             const float4* __restrict__ A, const float4* __restrict__ B,
                                             const float* __restrict__ L, const float* __restrict__ Wg, int p,
                                             float* __restrict__ far_u, float* __restrict__ far_s) {
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, cons
   for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) sW[i] = Wg[i];
   __syncthreads();
   const int b = begin[leaf], e = end[leaf];
-  const double a = box[3] * ldexp(1.0, -level[leaf]);
+  const double a = box[4 * (cseg ? cseg[leaf] : 0) + 3] * ldexp(1.0, -level[leaf]);
   const float inv_a = (float)(1.0 / a);
   const double cx = center[3 * leaf], cy = center[3 * leaf + 1], cz = center[3 * leaf + 2];
   const int on[5] = {1, 1, 2, 2, 2}, om[5] = {0, 1, 0, 1, 2};
@@ -186,7 +187,8 @@ int downward_pass(fmm_plan p, int64_t n, cudaStream_t s) {
   ++g_launches;
   k_l2p<<<(unsigned)p->nleaves, 64, 8 * P * sizeof(float), s>>>(
       p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(), p->c_center.as<double>(),
-      p->scal.as<double>(), p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_w.as<float>(),
+      p->batched ? p->seg_box.as<double>() : p->scal.as<double>(), p->batched ? p->c_seg.as<int>() : nullptr,
+      p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_w.as<float>(),
       p->prm.p, p->far_u.as<float>(), p->far_s.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;

@@ -2,6 +2,7 @@
 //   tree (keys, sort, octree, radii) -> P2M/M2M -> traversal -> M2L
 //   (+ periodic lattice) -> L2L/L2P -> P2P + combine,
 // every step a kernel on the caller's stream (Sec. 3.1, Algorithms 1-2).
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -10,7 +11,7 @@
 using namespace fmm;
 
 namespace fmm {
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
 }
 
 namespace {
@@ -27,6 +28,19 @@ int check_params(const fmm_params* q) {
   return FMM_OK;
 }
 
+std::vector<DBuf*> plan_buffers(fmm_plan p) {
+  return {&p->m2m_T, &p->l2l_T, &p->l2p_w, &p->lattice, &p->keys0, &p->keys1, &p->vals0, &p->vals1,
+          &p->sortA, &p->sortB, &p->far_u, &p->far_s, &p->leaf_of, &p->in_pos, &p->in_gam, &p->in_sig,
+          &p->out_vel, &p->out_dg, &p->c_begin, &p->c_end, &p->c_level, &p->c_parent, &p->c_child,
+          &p->c_nchild, &p->c_key, &p->c_center, &p->c_radius2, &p->c_radius, &p->c_cf, &p->c_tile,
+          &p->tile_cells, &p->leaves, &p->M, &p->L, &p->Mbf, &p->fr0, &p->fr1, &p->tcount, &p->tmask,
+          &p->tscan0, &p->tscan1, &p->tscan2, &p->p2p_raw, &p->m2l_raw, &p->lk0, &p->lk1, &p->lv0, &p->lv1,
+          &p->p2p_sorted, &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf,
+          &p->tmiss_keys, &p->tmiss_slots, &p->tslot_map, &p->st_tile, &p->st_slot, &p->st_src, &p->st_ckey,
+          &p->st_fkey, &p->m2l_items, &p->m2l_partial, &p->tile_range, &p->scan_tmp, &p->sort_hist, &p->scal,
+          &p->flags, &p->seg_off, &p->seg_box, &p->seg_sig, &p->seg_smax, &p->seg_mac, &p->seg_p2p, &p->c_seg};
+}
+
 struct Timer {
   fmm_plan p;
   cudaStream_t s;
@@ -36,11 +50,12 @@ struct Timer {
   }
 };
 
+// sg: nullptr for one problem, else the (non-empty) problems of a batch.
 int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u, float* vel,
-                float* dg, cudaStream_t s) {
+                float* dg, cudaStream_t s, const SegSpec* sg = nullptr) {
   if (n < 0 || n > p->n_max) return FMM_E_INVAL;
   if (n > 0 && (!pos || !gam)) return FMM_E_INVAL;
-  if (!sig && !(sig_u > 0.f)) return FMM_E_INVAL;
+  if (!sg && !sig && !(sig_u > 0.f)) return FMM_E_INVAL;
   memset(&p->stats, 0, sizeof(p->stats));
   p->last_n = n;
   p->ncells = p->nleaves = 0;
@@ -53,12 +68,15 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   if (p->prm.m2l_mode == FMM_M2L_TENSOR && !p->tc_ok) return FMM_E_INVAL;
   Timer tm{p, s};
   tm.mark();
-  FMM_TRY(build_tree(p, n, pos, gam, sig, sig_u, s));
+  if (sg) FMM_TRY(build_forest(p, n, pos, gam, sig, *sg, s));
+  else FMM_TRY(build_tree(p, n, pos, gam, sig, sig_u, s));
   tm.mark();
   FMM_TRY(upward_pass(p, s));
   tm.mark();
   double smax = (double)sig_u;
-  if (sig) {
+  if (sg) {
+    FMM_TRY(segment_tables(p, sig ? 1 : 0, s));
+  } else if (sig) {
     unsigned int bits = 0;
     FMM_CUDA_TRY(cudaMemcpyAsync(&bits, p->scal.as<double>() + kScalSigma, sizeof(unsigned int),
                                  cudaMemcpyDeviceToHost, s));
@@ -197,19 +215,56 @@ int fmm_plan_create(const fmm_params* prm, int64_t n_max, fmm_plan* out) {
 void fmm_plan_destroy(fmm_plan p) {
   if (!p) return;
   cudaDeviceSynchronize();
-  DBuf* bufs[] = {&p->m2m_T, &p->l2l_T, &p->l2p_w, &p->lattice, &p->keys0, &p->keys1, &p->vals0, &p->vals1,
-                  &p->sortA, &p->sortB, &p->far_u, &p->far_s, &p->leaf_of, &p->in_pos, &p->in_gam, &p->in_sig,
-                  &p->out_vel, &p->out_dg, &p->c_begin, &p->c_end, &p->c_level, &p->c_parent, &p->c_child,
-                  &p->c_nchild, &p->c_key, &p->c_center, &p->c_radius2, &p->c_radius, &p->c_cf, &p->c_tile, &p->tile_cells, &p->leaves,
-                  &p->M, &p->L, &p->Mbf, &p->fr0, &p->fr1, &p->tcount, &p->tmask, &p->tscan0, &p->tscan1,
-                  &p->tscan2, &p->p2p_raw, &p->m2l_raw, &p->lk0, &p->lk1, &p->lv0, &p->lv1, &p->p2p_sorted,
-                  &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf, &p->tmiss_keys, &p->tmiss_slots, &p->tslot_map, &p->st_tile, &p->st_slot,
-                  &p->st_src, &p->st_ckey, &p->st_fkey, &p->m2l_items, &p->m2l_partial, &p->tile_range, &p->scan_tmp, &p->sort_hist, &p->scal, &p->flags};
-  for (DBuf* b : bufs) b->release();
+  for (DBuf* b : plan_buffers(p)) b->release();
   if (p->pinned) cudaFreeHost(p->pinned);
+  if (p->seg_pinned) cudaFreeHost(p->seg_pinned);
   if (p->have_events)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(p->ev[i]);
   delete p;
+}
+
+int64_t fmm_plan_device_bytes(fmm_plan p) {
+  if (!p) return 0;
+  int64_t t = 0;
+  for (DBuf* b : plan_buffers(p)) t += (int64_t)b->bytes;
+  return t;
+}
+
+int fmm_eval_batch(fmm_plan p, int32_t nprob, const int64_t* offsets, const float* pos, const float* gam,
+                   const float* sig, const float* sigma_prob, const double* boxes, float* vel, float* dg,
+                   void* stream) {
+  if (!p || nprob < 0 || nprob > FMM_BATCH_MAX || (nprob > 0 && !offsets)) return FMM_E_INVAL;
+  if (nprob == 0) return eval_device(p, 0, pos, gam, sig, 1.f, vel, dg, (cudaStream_t)stream);
+  if (offsets[0] != 0) return FMM_E_INVAL;
+  for (int i = 0; i < nprob; ++i)
+    if (offsets[i + 1] < offsets[i]) return FMM_E_INVAL;
+  const int64_t n = offsets[nprob];
+  if (n > p->n_max) return FMM_E_INVAL;
+  if (n == 0) return eval_device(p, 0, pos, gam, sig, 1.f, vel, dg, (cudaStream_t)stream);
+  if (!sig && !sigma_prob) return FMM_E_INVAL;
+  if (p->prm.periodic && !boxes) return FMM_E_INVAL;
+  // the non-empty problems, in order
+  std::vector<int> off(1, 0);
+  std::vector<float> sg_sig;
+  std::vector<double> sg_box;
+  for (int i = 0; i < nprob; ++i) {
+    if (offsets[i + 1] == offsets[i]) continue;
+    if (!sig) {
+      if (!(sigma_prob[i] > 0.f) || !std::isfinite(sigma_prob[i])) return FMM_E_INVAL;
+      sg_sig.push_back(sigma_prob[i]);
+    }
+    if (p->prm.periodic) {
+      if (!(boxes[4 * i + 3] > 0.0)) return FMM_E_INVAL;
+      for (int q = 0; q < 4; ++q) sg_box.push_back(boxes[4 * i + q]);
+    }
+    off.push_back((int)offsets[i + 1]);
+  }
+  SegSpec spec;
+  spec.nseg = (int)off.size() - 1;
+  spec.h_off = off.data();
+  spec.h_sigma = sig ? nullptr : sg_sig.data();
+  spec.h_box = p->prm.periodic ? sg_box.data() : nullptr;
+  return eval_device(p, n, pos, gam, sig, 0.f, vel, dg, (cudaStream_t)stream, spec.nseg > 0 ? &spec : nullptr);
 }
 
 int fmm_eval_velocity_stretching(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig,

@@ -15,6 +15,25 @@ constexpr int kScalBox = 0;     // box_min[3], box_len
 constexpr int kScalDipole = 4;  // dipole velocity correction [3] (double)
 constexpr int kScalSigma = 8;   // float bits of max sigma (per-particle sigma)
 constexpr int kScalCount = 16;  // u32 counters area
+constexpr int kBatchBits = 16;  // Morton bits per axis of a batched evaluation (depth cap 16)
+constexpr int kMaxBatch = 1 << (63 - 3 * kBatchBits);  // problems per batched evaluation
+
+// Per-problem tables of a batched evaluation (one entry per non-empty problem).
+struct SegMac {  // traversal: image shift and regularisation MAC (Sec. 3.3)
+  double blen, smax;
+  float blenf, ksf, slack0, pad;
+};
+struct SegP2P {  // near field: core width, class bounds, dipole correction
+  float sigma, smax, blen, margin;
+  float dip[3], pad;
+};
+// Host description of a batch (problems concatenated; nullptr = one problem).
+struct SegSpec {
+  int nseg;
+  const int* h_off;      // [nseg+1] particle ranges of the problems
+  const float* h_sigma;  // [nseg] uniform sigma per problem, or nullptr (per-particle sigma)
+  const double* h_box;   // [nseg][4] periodic cubes (min xyz, side), or nullptr (free space)
+};
 }  // namespace fmm
 
 // Plan: parameters, constant operator tables, and the grow-only workspace.
@@ -26,6 +45,19 @@ struct fmm_plan_s {
   int device = 0;
   int timing = 0;
   int tc_ok = 0;  // tensor-core M2L usable for this p
+  // batched evaluation (several independent problems in one tree forest)
+  int batched = 0;         // 1 while the last evaluation was a batch
+  int nseg = 1;            // problems (non-empty) of the last evaluation
+  int kbits = fmm::kMaxLevel;  // Morton bits per axis
+  fmm::DBuf seg_off;       // int32 [nseg+1]
+  fmm::DBuf seg_box;       // double [nseg][4]
+  fmm::DBuf seg_sig;       // float [nseg] uniform sigma (batch with uniform sigma)
+  fmm::DBuf seg_smax;      // u32 float bits [nseg] largest sigma
+  fmm::DBuf seg_mac;       // SegMac [nseg]
+  fmm::DBuf seg_p2p;       // SegP2P [nseg]
+  fmm::DBuf c_seg;         // int32 problem of each cell
+  void* seg_pinned = nullptr;  // host staging of the problem tables
+  size_t seg_pinned_bytes = 0;
   // constant operator tables (device)
   fmm::DBuf m2m_T;    // [8][P(k)][P(r)] FP32 transposed M2M matrices by child octant
   fmm::DBuf l2l_T;    // [8][P(k)][P(r)] FP32 transposed L2L matrices by child octant
@@ -90,6 +122,9 @@ namespace fmm {
 int grow_cells(fmm_plan p, int64_t need, cudaStream_t s);
 int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u,
                cudaStream_t s);
+int upload_segments(fmm_plan p, const SegSpec& sg, cudaStream_t s);
+int build_forest(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, const SegSpec& sg,
+                 cudaStream_t s);
 // operators.cu
 int build_constant_operators(fmm_plan p);
 int build_m2l_operators(fmm_plan p, cudaStream_t s);
@@ -98,6 +133,8 @@ int apply_lattice(fmm_plan p, cudaStream_t s);
 int upward_pass(fmm_plan p, cudaStream_t s);
 // traverse.cu
 int traverse(fmm_plan p, double sigma_max_host, cudaStream_t s);
+// per-problem MAC and near-field tables of a batch (after the forest is built)
+int segment_tables(fmm_plan p, int per_particle_sigma, cudaStream_t s);
 // m2l.cu
 int m2l_simt(fmm_plan p, cudaStream_t s);
 int m2l_tensor(fmm_plan p, cudaStream_t s);

@@ -196,13 +196,15 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
   }
 }
 
+// One CTA per root cell (one per problem; the normalised operator does not
+// depend on the cube size): L[root][c][r] += sum_k A[r][k] M[root][c][k]
 __global__ void k_apply_lattice(const double* __restrict__ A, int P, float* __restrict__ L, const float* __restrict__ M) {
-  // root cell 0: L[0][c][r] += sum_k A[r][k] M[0][c][k]
+  const size_t root = (size_t)blockIdx.x * 3 * P;
   for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) {
     int c = e / P, r = e % P;
     double acc = 0.0;
-    for (int k = 0; k < P; ++k) acc += A[(size_t)r * P + k] * (double)M[c * P + k];
-    L[c * P + r] += (float)acc;
+    for (int k = 0; k < P; ++k) acc += A[(size_t)r * P + k] * (double)M[root + c * P + k];
+    L[root + c * P + r] += (float)acc;
   }
 }
 
@@ -314,7 +316,8 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
 int apply_lattice(fmm_plan p, cudaStream_t s) {
   if (!p->prm.periodic || p->prm.images <= 1) return FMM_OK;
   ++g_launches;
-  k_apply_lattice<<<1, 512, 0, s>>>(p->lattice.as<double>(), p->P, p->L.as<float>(), p->M.as<float>());
+  k_apply_lattice<<<p->batched ? p->nseg : 1, 512, 0, s>>>(p->lattice.as<double>(), p->P, p->L.as<float>(),
+                                                           p->M.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -278,14 +278,17 @@ __device__ __forceinline__ void dispatch_chunk(int mode, bool shift, bool self, 
 // particles double-buffered (the next chunk is loaded into registers while the
 // current one is computed from shared memory).  Coordinates are relative to
 // the target leaf centre.
-template <bool PS, int TPT>
+// SEG: a batch of problems; the leaf's problem supplies sigma, the class
+// bounds, the image shift and the dipole correction instead of the arguments.
+template <bool PS, int TPT, bool SEG>
 __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
                                             const int2* __restrict__ list, const int* __restrict__ begin,
                                             const int* __restrict__ end, const float4* __restrict__ cf,
                                             const float4* __restrict__ A, const float4* __restrict__ B,
                                             const float* __restrict__ far_u, const float* __restrict__ far_s,
                                             const uint32_t* __restrict__ sidx, float blen, float smax, float margin0,
-                                            SigK K0, const double* __restrict__ dip, float* __restrict__ vel,
+                                            SigK K0, const double* __restrict__ dip, const int* __restrict__ cseg,
+                                            const SegP2P* __restrict__ sp, float* __restrict__ vel,
                                             float* __restrict__ dg) {
   constexpr int CH = 32 * TPT;
   __shared__ float4 sA[2][CH], sB[2][CH], sC[2][CH];
@@ -295,7 +298,17 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
   const int tb = begin[leaf], te = end[leaf];
   const int2 rg = off[blockIdx.x];
   const float4 lc = cf[leaf];
-  const float dux = dip ? (float)dip[0] : 0.f, duy = dip ? (float)dip[1] : 0.f, duz = dip ? (float)dip[2] : 0.f;
+  float dux = dip ? (float)dip[0] : 0.f, duy = dip ? (float)dip[1] : 0.f, duz = dip ? (float)dip[2] : 0.f;
+  if (SEG) {
+    const SegP2P q = sp[cseg[leaf]];
+    if (!PS) K0 = make_sigk(q.sigma);
+    blen = q.blen;
+    smax = q.smax;
+    margin0 = q.margin;
+    dux = q.dip[0];
+    duy = q.dip[1];
+    duz = q.dip[2];
+  }
   float4 ra[TPT], rb[TPT];
   // source j of entry e, staged as X_j = (x_j - c) - shift, gamma_j, k_j = gamma_j x X_j
   auto stage = [&](int bb, int cnt, int img) {
@@ -486,13 +499,47 @@ __global__ void k_dipole_final(const double* __restrict__ part, int nb, const do
   dip[threadIdx.x] = -s / (3.0 * L * L * L);
 }
 
+// The same correction for each problem of a batch (one CTA per problem over
+// its sorted particle range), stored with the problem's near-field constants.
+__global__ void __launch_bounds__(256) k_dipole_seg(const float4* __restrict__ A, const float4* __restrict__ B,
+                                                    const int* __restrict__ off, const double* __restrict__ box,
+                                                    SegP2P* __restrict__ sp) {
+  const int sg = blockIdx.x;
+  const double* bx = box + 4 * sg;
+  const double L = bx[3];
+  const double c0x = bx[0] + 0.5 * L, c0y = bx[1] + 0.5 * L, c0z = bx[2] + 0.5 * L;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int i = off[sg] + threadIdx.x; i < off[sg + 1]; i += blockDim.x) {
+    float4 x = A[i], g = B[i];
+    double X = (double)x.x - c0x, Y = (double)x.y - c0y, Z = (double)x.z - c0z;
+    s[0] += Y * g.z - Z * g.y;
+    s[1] += Z * g.x - X * g.z;
+    s[2] += X * g.y - Y * g.x;
+  }
+  __shared__ double sh[3][256];
+  for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) sp[sg].dip[threadIdx.x] = (float)(-sh[threadIdx.x][0] / (3.0 * L * L * L));
+}
 
 // Pair counts per class (near, mid, far) for the work statistics.
 __global__ void k_p2p_classes(const int* __restrict__ leaves, const int2* __restrict__ off,
                               const int2* __restrict__ list, const int* __restrict__ begin,
                               const int* __restrict__ end, const float4* __restrict__ cf, float blen, float smax,
-                              float margin0, unsigned long long* __restrict__ counts) {
+                              float margin0, const int* __restrict__ cseg, const SegP2P* __restrict__ sp,
+                              unsigned long long* __restrict__ counts) {
   const int leaf = leaves[blockIdx.x];
+  if (cseg) {
+    const SegP2P q = sp[cseg[leaf]];
+    blen = q.blen;
+    smax = q.smax;
+    margin0 = q.margin;
+  }
   const int2 rg = off[blockIdx.x];
   const unsigned long long nt = (unsigned long long)(end[leaf] - begin[leaf]);
   unsigned long long c[3] = {0ull, 0ull, 0ull};
@@ -514,7 +561,13 @@ __global__ void k_p2p_classes(const int* __restrict__ leaves, const int2* __rest
 int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel, float* dg, cudaStream_t s) {
   const double* dip = nullptr;
   double* scal = p->scal.as<double>();
-  if (p->prm.periodic) {
+  const int* cseg = p->batched ? p->c_seg.as<int>() : nullptr;
+  SegP2P* sp = p->batched ? p->seg_p2p.as<SegP2P>() : nullptr;
+  if (p->prm.periodic && p->batched) {
+    ++g_launches;
+    k_dipole_seg<<<p->nseg, 256, 0, s>>>(p->sortA.as<float4>(), p->sortB.as<float4>(), p->seg_off.as<int>(),
+                                         p->seg_box.as<double>(), sp);
+  } else if (p->prm.periodic) {
     const int parts = 256;
     FMM_TRY(p->scan_tmp.ensure((size_t)parts * 3 * sizeof(double)));
     ++g_launches;
@@ -539,19 +592,34 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   const float* fs = p->far_s.as<float>();
   const float smaxf = (float)smax;
   const float margin0 = (float)p->cf_margin;
+  const bool two = p->prm.ncrit > 32;
   ++g_launches;
-  if (p->prm.ncrit > 32) {
-    if (ps) k_p2p<true, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
-    else k_p2p<false, 2><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
+#define FMM_P2P_LAUNCH(PS_, TPT_, SEG_)                                                                         \
+  k_p2p<PS_, TPT_, SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, \
+                                          margin0, K0, dip, cseg, sp, vel, dg)
+  if (cseg) {
+    if (two) {
+      if (ps) FMM_P2P_LAUNCH(true, 2, true);
+      else FMM_P2P_LAUNCH(false, 2, true);
+    } else {
+      if (ps) FMM_P2P_LAUNCH(true, 1, true);
+      else FMM_P2P_LAUNCH(false, 1, true);
+    }
   } else {
-    if (ps) k_p2p<true, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
-    else k_p2p<false, 1><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, K0, dip, vel, dg);
+    if (two) {
+      if (ps) FMM_P2P_LAUNCH(true, 2, false);
+      else FMM_P2P_LAUNCH(false, 2, false);
+    } else {
+      if (ps) FMM_P2P_LAUNCH(true, 1, false);
+      else FMM_P2P_LAUNCH(false, 1, false);
+    }
   }
+#undef FMM_P2P_LAUNCH
   FMM_CUDA_TRY(cudaGetLastError());
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
   ++g_launches;
-  k_p2p_classes<<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, blen, smaxf, margin0, cnt);
+  k_p2p_classes<<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, blen, smaxf, margin0, cseg, sp, cnt);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -27,20 +27,22 @@ struct TravArgs {
   const float4* cf;  // FP32 copies of centre and radius
   const int* nchild;
   const int* child;
+  const int* cseg;    // batch: problem of each cell (nullptr: one problem, the scalars below)
+  const SegMac* sm;   // batch: per-problem shift and MAC constants
   double theta, ksig, smax, blen;
   float thetaf, ksf, blenf, slack0;  // slack0 = 2e-6 * (largest coordinate magnitude + box length)
 };
 
 // The MAC exactly as the oracle evaluates it: FP64, explicitly rounded, fixed order.
-__device__ inline bool mac_fp64(const TravArgs& t, int a, int b, int o) {
-  double sh[3] = {(double)(o / 9 - 1) * t.blen, (double)((o / 3) % 3 - 1) * t.blen, (double)(o % 3 - 1) * t.blen};
+__device__ inline bool mac_fp64(const TravArgs& t, int a, int b, int o, double blen, double smax) {
+  double sh[3] = {(double)(o / 9 - 1) * blen, (double)((o / 3) % 3 - 1) * blen, (double)(o % 3 - 1) * blen};
   double dx = __dsub_rn(t.center[3 * a], __dadd_rn(t.center[3 * b], sh[0]));
   double dy = __dsub_rn(t.center[3 * a + 1], __dadd_rn(t.center[3 * b + 1], sh[1]));
   double dz = __dsub_rn(t.center[3 * a + 2], __dadd_rn(t.center[3 * b + 2], sh[2]));
   double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   double dist = __dsqrt_rn(d2);
   double sr = __dadd_rn(t.radius[a], t.radius[b]);
-  return sr < __dmul_rn(t.theta, dist) && __dsub_rn(dist, sr) >= __dmul_rn(t.ksig, t.smax);
+  return sr < __dmul_rn(t.theta, dist) && __dsub_rn(dist, sr) >= __dmul_rn(t.ksig, smax);
 }
 
 // FP32 screen with a bound on its rounding error (centres and radii rounded
@@ -48,39 +50,77 @@ __device__ inline bool mac_fp64(const TravArgs& t, int a, int b, int o) {
 // inside the slack of a decision boundary take the FP64 test, so every
 // decision equals the FP64 one.
 __device__ inline int interact(const TravArgs& t, int a, int b, int o) {
+  double blen = t.blen, smax = t.smax;
+  float blenf = t.blenf, ksf = t.ksf, slack0 = t.slack0;
+  if (t.cseg) {  // both cells belong to one problem
+    const SegMac m = t.sm[t.cseg[a]];
+    blen = m.blen;
+    smax = m.smax;
+    blenf = m.blenf;
+    ksf = m.ksf;
+    slack0 = m.slack0;
+  }
   const float4 A = t.cf[a], B = t.cf[b];
-  const float sx = (float)(o / 9 - 1) * t.blenf, sy = (float)((o / 3) % 3 - 1) * t.blenf,
-              sz = (float)(o % 3 - 1) * t.blenf;
+  const float sx = (float)(o / 9 - 1) * blenf, sy = (float)((o / 3) % 3 - 1) * blenf,
+              sz = (float)(o % 3 - 1) * blenf;
   const float dx = A.x - (B.x + sx), dy = A.y - (B.y + sy), dz = A.z - (B.z + sz);
   const float d = sqrtf(dx * dx + dy * dy + dz * dz);
   const float sr = A.w + B.w;
-  const float slack = t.slack0 + 1e-6f * (d + sr + t.ksf);
+  const float slack = slack0 + 1e-6f * (d + sr + ksf);
   const float v1 = t.thetaf * d - sr;  // M2L needs v1 > 0
-  const float v2 = d - sr - t.ksf;     // and v2 >= 0
+  const float v2 = d - sr - ksf;       // and v2 >= 0
   bool m2l;
   if (v1 <= -slack || v2 <= -slack) m2l = false;
   else if (v1 > slack && v2 > slack) m2l = true;
-  else m2l = mac_fp64(t, a, b, o);
+  else m2l = mac_fp64(t, a, b, o, blen, smax);
   if (m2l) return 0;                                          // M2L
   if (t.nchild[a] == 0 && t.nchild[b] == 0) return 1;        // P2P
   return 2;                                                   // push
 }
 
-// Initial pairs (root, root + o L), one thread, in image order.
-__global__ void k_trav_init(TravArgs t, int nimg, int img0, int4* fr, int4* m2l, int4* p2p, uint32_t* cnt) {
-  if (threadIdx.x || blockIdx.x) return;
-  uint32_t nm = 0, np = 0, nf = 0;
-  for (int q = 0; q < nimg; ++q) {
-    int o = img0 + q;
-    int ty = interact(t, 0, 0, o);
-    int4 v = make_int4(0, 0, o, 0);
-    if (ty == 0) m2l[nm++] = v;
-    else if (ty == 1) p2p[np++] = v;
-    else fr[nf++] = v;
+// Initial pairs (root r, root r + o L) for every root (one per problem) and
+// image, in (root, image) order; one CTA, order-preserving compaction.
+__global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int nimg, int img0, int4* fr, int4* m2l,
+                                                    int4* p2p, uint32_t* cnt) {
+  __shared__ uint32_t wsum[3][32];
+  __shared__ uint32_t base[3];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid < 3) base[tid] = 0;
+  __syncthreads();
+  const int total = nroot * nimg;
+  for (int c0 = 0; c0 < total; c0 += 1024) {
+    const int q = c0 + tid;
+    int ty = -1;
+    int4 v = make_int4(0, 0, 0, 0);
+    if (q < total) {
+      const int r = q / nimg, o = img0 + q % nimg;
+      ty = interact(t, r, r, o);
+      v = make_int4(r, r, o, 0);
+    }
+    uint32_t rank[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const unsigned b = __ballot_sync(0xffffffffu, ty == k);
+      rank[k] = __popc(b & ((1u << lane) - 1u));
+      if (lane == 0) wsum[k][w] = __popc(b);
+    }
+    __syncthreads();
+    if (tid < 3) {  // exclusive scan of the warp totals
+      uint32_t acc = base[tid];
+      for (int i = 0; i < 32; ++i) {
+        const uint32_t x = wsum[tid][i];
+        wsum[tid][i] = acc;
+        acc += x;
+      }
+      base[tid] = acc;
+    }
+    __syncthreads();
+    if (ty == 0) m2l[wsum[0][w] + rank[0]] = v;
+    else if (ty == 1) p2p[wsum[1][w] + rank[1]] = v;
+    else if (ty == 2) fr[wsum[2][w] + rank[2]] = v;
+    __syncthreads();
   }
-  cnt[0] = nm;
-  cnt[1] = np;
-  cnt[2] = nf;
+  if (tid < 3) cnt[tid] = base[tid];
 }
 
 __device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, int& c0, int& nc) {
@@ -180,8 +220,9 @@ __global__ void k_p2p_offsets(const int* __restrict__ leaves, int nl, const uint
 
 // ---- M2L steps
 
-__device__ inline void cell_ijk(uint64_t key, long long ijk[3]) {
-  uint64_t k = key;
+// Integer cell coordinates of a level-l cell (the bits above 3l hold the problem).
+__device__ inline void cell_ijk(uint64_t key, int l, long long ijk[3]) {
+  uint64_t k = key & ((1ull << (3 * l)) - 1ull);
   long long r[3] = {0, 0, 0};
   for (int b = 0; b < kMaxLevel; ++b) {
     r[0] |= (long long)((k >> (3 * b + 2)) & 1ull) << b;
@@ -202,8 +243,8 @@ __global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __res
   int la = level[v.x], lb = level[v.y];
   int lf = la > lb ? la : lb;
   long long ia[3], ib[3];
-  cell_ijk(ckey[v.x], ia);
-  cell_ijk(ckey[v.y], ib);
+  cell_ijk(ckey[v.x], la, ia);
+  cell_ijk(ckey[v.y], lb, ib);
   int o[3] = {v.z / 9 - 1, (v.z / 3) % 3 - 1, v.z % 3 - 1};
   long long t[3];
   bool ok = true;
@@ -346,6 +387,38 @@ __global__ void k_tile_ranges(const int* __restrict__ st_tile, int ns, int2* __r
   if (s == ns - 1 || st_tile[s + 1] != t) tr[t].y = s + 1;
 }
 
+// Per-problem constants of a batch, with the arithmetic of the one-problem
+// path: MAC slack and near-field class margin 2e-6 (largest |coordinate| of
+// the cube + side), k_sigma sigma_max, image shift = side (periodic only).
+__global__ void k_seg_tables(int nseg, const double* __restrict__ box, const unsigned int* __restrict__ smax_bits,
+                             const float* __restrict__ sig, double ksig, int periodic, SegMac* __restrict__ mac,
+                             SegP2P* __restrict__ pp) {
+  const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sg >= nseg) return;
+  const double* b = box + 4 * sg;
+  double cmax = 0.0;
+  for (int q = 0; q < 3; ++q) cmax = fmax(cmax, fmax(fabs(b[q]), fabs(__dadd_rn(b[q], b[3]))));
+  const double margin = __dmul_rn(2e-6, __dadd_rn(cmax, b[3]));
+  const double smax = (double)__uint_as_float(smax_bits[sg]);
+  const double blen = periodic ? b[3] : 0.0;
+  SegMac m;
+  m.blen = blen;
+  m.smax = smax;
+  m.blenf = (float)blen;
+  m.ksf = (float)__dmul_rn(ksig, smax);
+  m.slack0 = (float)margin;
+  m.pad = 0.f;
+  mac[sg] = m;
+  SegP2P q;
+  q.sigma = sig ? sig[sg] : 1.f;
+  q.smax = (float)smax;
+  q.blen = (float)blen;
+  q.margin = (float)margin;
+  q.dip[0] = q.dip[1] = q.dip[2] = 0.f;
+  q.pad = 0.f;
+  pp[sg] = q;
+}
+
 int bits_for(int64_t v) {
   int b = 1;
   while (b < 63 && (1ll << b) <= v) ++b;
@@ -353,6 +426,16 @@ int bits_for(int64_t v) {
 }
 
 }  // namespace
+
+int segment_tables(fmm_plan p, int per_particle_sigma, cudaStream_t s) {
+  const int S = p->nseg;
+  ++g_launches;
+  k_seg_tables<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(
+      S, p->seg_box.as<double>(), p->seg_smax.as<unsigned int>(), per_particle_sigma ? nullptr : p->seg_sig.as<float>(),
+      (double)p->prm.sigma_sep, p->prm.periodic, p->seg_mac.as<SegMac>(), p->seg_p2p.as<SegP2P>());
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
 
 int traverse(fmm_plan p, double smax, cudaStream_t s) {
   const int T = 256;
@@ -363,17 +446,23 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   ta.cf = p->c_cf.as<float4>();
   ta.nchild = p->c_nchild.as<int>();
   ta.child = p->c_child.as<int>();
+  ta.cseg = nullptr;
+  ta.sm = nullptr;
   ta.theta = (double)p->prm.theta;
   ta.ksig = (double)p->prm.sigma_sep;
   ta.smax = smax;
   ta.blen = p->prm.periodic ? p->prm.box_len : 0.0;
-  {
+  ta.thetaf = (float)ta.theta;
+  if (p->batched) {
+    ta.cseg = p->c_seg.as<int>();
+    ta.sm = p->seg_mac.as<SegMac>();
+    ta.ksf = ta.blenf = ta.slack0 = 0.f;
+  } else {
     double hbox[4];
     FMM_CUDA_TRY(cudaMemcpyAsync(hbox, p->scal.as<double>() + kScalBox, sizeof(hbox), cudaMemcpyDeviceToHost, s));
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     double cmax = 0.0;
     for (int q = 0; q < 3; ++q) cmax = std::max(cmax, std::max(std::fabs(hbox[q]), std::fabs(hbox[q] + hbox[3])));
-    ta.thetaf = (float)ta.theta;
     ta.ksf = (float)(ta.ksig * ta.smax);
     ta.blenf = (float)ta.blen;
     ta.slack0 = (float)(2e-6 * (cmax + hbox[3]));
@@ -392,7 +481,8 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int4), s));
   FMM_TRY(p->p2p_raw.grow_copy(cap_p * sizeof(int4), s));
   ++g_launches;
-  k_trav_init<<<1, 1, 0, s>>>(ta, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(), p->p2p_raw.as<int4>(), dcnt);
+  k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(),
+                                 p->p2p_raw.as<int4>(), dcnt);
   FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));
   int64_t nm = hc[0], np = hc[1], nf = hc[2];

@@ -9,6 +9,8 @@
 // from the centre to a particle of the cell.  Every FP64 expression uses
 // explicitly rounded operations (no contraction) in a fixed order, so the MAC
 // decisions built on them are reproducible.
+#include <cstring>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -47,6 +49,15 @@ __global__ void k_bbox_partial(const float* __restrict__ pos, int64_t n, double*
 
 // Free-space cube: centre of the bounding box, half side = longest extent/2
 // times (1 + 2^-10) (0.5 if all points coincide).
+__device__ inline void cube_from_bounds(const double lo[3], const double hi[3], double* box) {
+  double ext = 0.0;
+  for (int a = 0; a < 3; ++a) ext = fmax(ext, __dsub_rn(hi[a], lo[a]));
+  double half = __dmul_rn(__dmul_rn(ext, 0.5), 1.0 + 0.0009765625);
+  if (half == 0.0) half = 0.5;
+  for (int a = 0; a < 3; ++a) box[a] = __dsub_rn(__dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5), half);
+  box[3] = __dmul_rn(half, 2.0);
+}
+
 __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ box) {
   if (threadIdx.x != 0) return;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -55,12 +66,72 @@ __global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __
       lo[a] = fmin(lo[a], part[b * 6 + a]);
       hi[a] = fmax(hi[a], part[b * 6 + 3 + a]);
     }
-  double ext = 0.0;
-  for (int a = 0; a < 3; ++a) ext = fmax(ext, __dsub_rn(hi[a], lo[a]));
-  double half = __dmul_rn(__dmul_rn(ext, 0.5), 1.0 + 0.0009765625);
-  if (half == 0.0) half = 0.5;
-  for (int a = 0; a < 3; ++a) box[a] = __dsub_rn(__dmul_rn(__dadd_rn(lo[a], hi[a]), 0.5), half);
-  box[3] = __dmul_rn(half, 2.0);
+  cube_from_bounds(lo, hi, box);
+}
+
+// One CTA per problem of a batch: its cube (same arithmetic as above; min and
+// max are exact, so the cube equals the one of the problem on its own).
+__global__ void __launch_bounds__(256) k_bbox_seg(const float* __restrict__ pos, const int* __restrict__ off,
+                                                  double* __restrict__ box) {
+  const int sg = blockIdx.x;
+  const int b = off[sg], e = off[sg + 1];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = (double)pos[3 * (int64_t)i + a];
+      lo[a] = fmin(lo[a], v);
+      hi[a] = fmax(hi[a], v);
+    }
+  }
+  __shared__ double sh[6][256];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    sh[a][threadIdx.x] = lo[a];
+    sh[3 + a][threadIdx.x] = hi[a];
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sh[a][threadIdx.x] = fmin(sh[a][threadIdx.x], sh[a][threadIdx.x + o]);
+        sh[3 + a][threadIdx.x] = fmax(sh[3 + a][threadIdx.x], sh[3 + a][threadIdx.x + o]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double l[3] = {sh[0][0], sh[1][0], sh[2][0]}, h[3] = {sh[3][0], sh[4][0], sh[5][0]};
+    cube_from_bounds(l, h, box + 4 * sg);
+  }
+}
+
+// Largest sigma of each problem (float bits; sigma > 0 orders like its bits).
+__global__ void __launch_bounds__(256) k_sigma_max_seg(const float* __restrict__ sig, const int* __restrict__ off,
+                                                       unsigned int* __restrict__ out) {
+  const int sg = blockIdx.x;
+  float m = 0.f;
+  for (int i = off[sg] + threadIdx.x; i < off[sg + 1]; i += blockDim.x) m = fmaxf(m, sig[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+    out[sg] = __float_as_uint(fmaxf(m, sh[0]));
+  }
+}
+
+// Problem of particle i: the largest s with off[s] <= i.
+__device__ inline int seg_of(const int* __restrict__ off, int nseg, int64_t i) {
+  int lo = 0, hi = nseg;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
 __global__ void k_set_box(double x, double y, double z, double len, double* box) {
@@ -90,33 +161,39 @@ __device__ inline uint32_t compact3(uint64_t x) {
   return (uint32_t)x;
 }
 
-__device__ inline uint64_t quantize_axis(float x, double bmin, double blen) {
+__device__ inline uint64_t quantize_axis(float x, double bmin, double blen, double scale) {
   double u = __ddiv_rn(__dsub_rn((double)x, bmin), blen);
-  double k = floor(__dmul_rn(u, 2097152.0));
+  double k = floor(__dmul_rn(u, scale));
   if (!(k >= 0.0)) k = 0.0;
-  if (k > 2097151.0) k = 2097151.0;
+  if (k > scale - 1.0) k = scale - 1.0;
   return (uint64_t)k;
 }
 
+// kbits Morton bits per axis; a batch puts the problem index above them.
 __global__ void k_keys(const float* __restrict__ pos, int64_t n, const double* __restrict__ box,
-                       uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+                       const int* __restrict__ off, int nseg, int kbits, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ idx) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double blen = box[3];
-  uint64_t kx = quantize_axis(pos[3 * i + 0], box[0], blen);
-  uint64_t ky = quantize_axis(pos[3 * i + 1], box[1], blen);
-  uint64_t kz = quantize_axis(pos[3 * i + 2], box[2], blen);
-  keys[i] = (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
+  const int sg = off ? seg_of(off, nseg, i) : 0;
+  const double* b = box + 4 * sg;
+  const double blen = b[3], scale = ldexp(1.0, kbits);
+  uint64_t kx = quantize_axis(pos[3 * i + 0], b[0], blen, scale);
+  uint64_t ky = quantize_axis(pos[3 * i + 1], b[1], blen, scale);
+  uint64_t kz = quantize_axis(pos[3 * i + 2], b[2], blen, scale);
+  keys[i] = ((uint64_t)sg << (3 * kbits)) | (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
   idx[i] = (uint32_t)i;
 }
 
+// Sorted position i of a batch lies in its problem's input range.
 __global__ void k_permute(const float* __restrict__ pos, const float* __restrict__ gam,
-                          const float* __restrict__ sig, float sig_u, const uint32_t* __restrict__ idx,
+                          const float* __restrict__ sig, float sig_u, const float* __restrict__ seg_sig,
+                          const int* __restrict__ off, int nseg, const uint32_t* __restrict__ idx,
                           int64_t n, float4* __restrict__ A, float4* __restrict__ B) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t j = idx[i];
-  float s = sig ? sig[j] : sig_u;
+  float s = sig ? sig[j] : (seg_sig ? seg_sig[seg_of(off, nseg, i)] : sig_u);
   A[i] = make_float4(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], s);
   B[i] = make_float4(gam[3 * j], gam[3 * j + 1], gam[3 * j + 2], 0.f);
 }
@@ -129,12 +206,16 @@ __global__ void k_sigma_max(const float* __restrict__ sig, int64_t n, unsigned i
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // sigma > 0: order of bits = order of values
 }
 
-__global__ void k_root(int n, int* begin, int* end, int* level, int* parent, uint64_t* key) {
-  begin[0] = 0;
-  end[0] = n;
-  level[0] = 0;
-  parent[0] = -1;
-  key[0] = 0;
+// Root cells at level 0: one per problem (key = problem index).
+__global__ void k_roots(int nroot, const int* __restrict__ off, int n, int* begin, int* end, int* level, int* parent,
+                        uint64_t* key) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nroot) return;
+  begin[r] = off ? off[r] : 0;
+  end[r] = off ? off[r + 1] : n;
+  level[r] = 0;
+  parent[r] = -1;
+  key[r] = (uint64_t)r;
 }
 
 __device__ inline int lower_bound_u64(const uint64_t* a, int lo, int hi, uint64_t v) {
@@ -147,8 +228,8 @@ __device__ inline int lower_bound_u64(const uint64_t* a, int lo, int hi, uint64_
 }
 
 // Child boundaries of cell c at level l (8 digits -> 9 bounds).
-__device__ inline void child_bounds(const uint64_t* skeys, int b, int e, uint64_t prefix, int l, int* bd) {
-  const int shift = 3 * (kMaxLevel - 1 - l);
+__device__ inline void child_bounds(const uint64_t* skeys, int b, int e, uint64_t prefix, int l, int kbits, int* bd) {
+  const int shift = 3 * (kbits - 1 - l);
   bd[0] = b;
   bd[8] = e;
   for (int d = 1; d < 8; ++d) bd[d] = lower_bound_u64(skeys, b, e, ((prefix << 3) | (uint64_t)d) << shift);
@@ -156,14 +237,14 @@ __device__ inline void child_bounds(const uint64_t* skeys, int b, int e, uint64_
 
 __global__ void k_split_count(const uint64_t* __restrict__ skeys, const int* __restrict__ begin,
                               const int* __restrict__ end, const uint64_t* __restrict__ key, int lb, int le,
-                              int l, int ncrit, uint32_t* __restrict__ cnt) {
+                              int l, int kbits, int ncrit, uint32_t* __restrict__ cnt) {
   int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= le) return;
   int b = begin[c], e = end[c];
   uint32_t k = 0;
-  if (e - b > ncrit && l < kMaxLevel) {
+  if (e - b > ncrit && l < kbits) {
     int bd[9];
-    child_bounds(skeys, b, e, key[c], l, bd);
+    child_bounds(skeys, b, e, key[c], l, kbits, bd);
     for (int d = 0; d < 8; ++d) k += bd[d + 1] > bd[d] ? 1u : 0u;
   }
   cnt[c - lb] = k;
@@ -172,7 +253,7 @@ __global__ void k_split_count(const uint64_t* __restrict__ skeys, const int* __r
 __global__ void k_split_write(const uint64_t* __restrict__ skeys, int* __restrict__ begin, int* __restrict__ end,
                               int* __restrict__ level, int* __restrict__ parent, int* __restrict__ child,
                               int* __restrict__ nchild, uint64_t* __restrict__ key, int lb, int le, int l,
-                              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off) {
+                              int kbits, const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off) {
   int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= le) return;
   uint32_t k = cnt[c - lb];
@@ -184,7 +265,7 @@ __global__ void k_split_write(const uint64_t* __restrict__ skeys, int* __restric
   int first = le + (int)off[c - lb];
   child[c] = first;
   int bd[9];
-  child_bounds(skeys, begin[c], end[c], key[c], l, bd);
+  child_bounds(skeys, begin[c], end[c], key[c], l, kbits, bd);
   int o = first;
   for (int d = 0; d < 8; ++d) {
     if (bd[d + 1] > bd[d]) {
@@ -199,18 +280,23 @@ __global__ void k_split_write(const uint64_t* __restrict__ skeys, int* __restric
 }
 
 
+// Cell key = problem index above the 3l level-local Morton bits.
 __global__ void k_centers(const int* __restrict__ level, const uint64_t* __restrict__ key, int nc,
                           const double* __restrict__ box, double* __restrict__ center,
-                          unsigned long long* __restrict__ r2bits) {
+                          unsigned long long* __restrict__ r2bits, int* __restrict__ cseg) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   int l = level[c];
-  uint64_t k = key[c];
-  double a = __dmul_rn(box[3], ldexp(1.0, -l));
+  const uint64_t kf = key[c];
+  const int sg = (int)(kf >> (3 * l));
+  const uint64_t k = kf & ((1ull << (3 * l)) - 1ull);
+  const double* b = box + 4 * sg;
+  double a = __dmul_rn(b[3], ldexp(1.0, -l));
   uint32_t ijk[3] = {compact3(k >> 2), compact3(k >> 1), compact3(k)};
 #pragma unroll
-  for (int q = 0; q < 3; ++q) center[3 * c + q] = __dadd_rn(box[q], __dmul_rn((double)ijk[q] + 0.5, a));
+  for (int q = 0; q < 3; ++q) center[3 * c + q] = __dadd_rn(b[q], __dmul_rn((double)ijk[q] + 0.5, a));
   r2bits[c] = 0ull;
+  if (cseg) cseg[c] = sg;
 }
 
 __global__ void k_leaf_flags(const int* __restrict__ nchild, int nc, uint32_t* __restrict__ f) {
@@ -289,54 +375,19 @@ int grow_cells(fmm_plan p, int64_t need, cudaStream_t s) {
   return FMM_OK;
 }
 
-// Keys, sort, permutation into sorted SoA, octree, centres, radii.
-int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u,
-               cudaStream_t s) {
+// Octree over the sorted keys (one root per problem), centres, leaves, radii.
+static int tree_from_sorted(fmm_plan p, int64_t n, int nroot, const int* off, const double* box, int kbits,
+                            bool with_seg, cudaStream_t s) {
   const int T = 256;
   unsigned nb = (unsigned)((n + T - 1) / T);
-  double* box = p->scal.as<double>();
-  if (p->prm.periodic) {
-    ++g_launches;
-    k_set_box<<<1, 1, 0, s>>>(p->prm.box_min[0], p->prm.box_min[1], p->prm.box_min[2], p->prm.box_len, box);
-  } else {
-    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
-    FMM_TRY(p->scan_tmp.ensure((size_t)parts * 6 * sizeof(double)));
-    ++g_launches;
-    k_bbox_partial<<<parts, 256, 0, s>>>(pos, n, p->scan_tmp.as<double>());
-    ++g_launches;
-    k_bbox_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, box);
-  }
-  // sigma max (uniform: the value itself)
-  unsigned int* smax = reinterpret_cast<unsigned int*>(box + 8);
-  if (sig) {
-    FMM_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(unsigned int), s));
-    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
-    ++g_launches;
-    k_sigma_max<<<parts, 256, 0, s>>>(sig, n, smax);
-  }
-  uint64_t* k0 = p->keys0.as<uint64_t>();
-  uint64_t* k1 = p->keys1.as<uint64_t>();
-  uint32_t* v0 = p->vals0.as<uint32_t>();
-  uint32_t* v1 = p->vals1.as<uint32_t>();
-  ++g_launches;
-  k_keys<<<nb, T, 0, s>>>(pos, n, box, k0, v0);
-  FMM_CUDA_TRY(cudaGetLastError());
-  int second = 0;
-  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 63, &second, p->sort_hist, p->scan_tmp, s));
-  p->skeys = second ? k1 : k0;
-  p->sidx = second ? v1 : v0;
-  ++g_launches;
-  k_permute<<<nb, T, 0, s>>>(pos, gam, sig, sig_u, p->sidx, n, p->sortA.as<float4>(), p->sortB.as<float4>());
-  FMM_CUDA_TRY(cudaGetLastError());
-
-  // ---- octree, level by level
-  int64_t cap = std::max<int64_t>(64, 4 * n / std::max(1, p->prm.ncrit) + 64);
+  int64_t cap = std::max<int64_t>(64, 4 * n / std::max(1, p->prm.ncrit) + 64 + 2 * (int64_t)nroot);
   if ((int64_t)(p->c_begin.bytes / sizeof(int)) < cap) FMM_TRY(grow_cells(p, cap, s));
   ++g_launches;
-  k_root<<<1, 1, 0, s>>>((int)n, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
-                         p->c_parent.as<int>(), p->c_key.as<uint64_t>());
+  k_roots<<<(unsigned)((nroot + T - 1) / T), T, 0, s>>>(nroot, off, (int)n, p->c_begin.as<int>(), p->c_end.as<int>(),
+                                                         p->c_level.as<int>(), p->c_parent.as<int>(),
+                                                         p->c_key.as<uint64_t>());
   p->level_begin.assign(1, 0);
-  int lb = 0, le = 1;
+  int lb = 0, le = nroot;
   uint32_t* hcount = reinterpret_cast<uint32_t*>(p->pinned);
   for (int l = 0;; ++l) {
     p->level_begin.push_back(le);
@@ -346,7 +397,7 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
     unsigned g = (unsigned)((ncl + T - 1) / T);
     ++g_launches;
     k_split_count<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_key.as<uint64_t>(),
-                                  lb, le, l, p->prm.ncrit, p->tcount.as<uint32_t>());
+                                  lb, le, l, kbits, p->prm.ncrit, p->tcount.as<uint32_t>());
     FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ncl,
                                p->tscan0.as<uint32_t>() + ncl, p->scan_tmp, s));
     FMM_CUDA_TRY(cudaMemcpyAsync(hcount, p->tscan0.as<uint32_t>() + ncl, sizeof(uint32_t),
@@ -357,7 +408,7 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
     ++g_launches;
     k_split_write<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
                                   p->c_parent.as<int>(), p->c_child.as<int>(), p->c_nchild.as<int>(),
-                                  p->c_key.as<uint64_t>(), lb, le, l, p->tcount.as<uint32_t>(),
+                                  p->c_key.as<uint64_t>(), lb, le, l, kbits, p->tcount.as<uint32_t>(),
                                   p->tscan0.as<uint32_t>());
     FMM_CUDA_TRY(cudaGetLastError());
     if (nnew == 0) break;
@@ -376,10 +427,15 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   FMM_TRY(p->leaves.ensure((size_t)(nc + 1) * sizeof(int)));
   FMM_TRY(p->tcount.ensure((size_t)(nc + 1) * sizeof(uint32_t)));
   FMM_TRY(p->tscan0.ensure((size_t)(nc + 1) * sizeof(uint32_t)));
+  int* cseg = nullptr;
+  if (with_seg) {
+    FMM_TRY(p->c_seg.ensure((size_t)nc * sizeof(int)));
+    cseg = p->c_seg.as<int>();
+  }
   unsigned gc = (unsigned)((nc + T - 1) / T);
   ++g_launches;
   k_centers<<<gc, T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc, box, p->c_center.as<double>(),
-                             p->c_radius2.as<unsigned long long>());
+                             p->c_radius2.as<unsigned long long>(), cseg);
   ++g_launches;
   k_leaf_flags<<<gc, T, 0, s>>>(p->c_nchild.as<int>(), nc, p->tcount.as<uint32_t>());
   FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), nc, p->tscan0.as<uint32_t>() + nc,
@@ -404,6 +460,132 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   return FMM_OK;
 }
 
+// Keys, sort, permutation into sorted SoA, octree, centres, radii.
+int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u,
+               cudaStream_t s) {
+  const int T = 256;
+  unsigned nb = (unsigned)((n + T - 1) / T);
+  double* box = p->scal.as<double>();
+  p->batched = 0;
+  p->nseg = 1;
+  p->kbits = kMaxLevel;
+  if (p->prm.periodic) {
+    ++g_launches;
+    k_set_box<<<1, 1, 0, s>>>(p->prm.box_min[0], p->prm.box_min[1], p->prm.box_min[2], p->prm.box_len, box);
+  } else {
+    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    FMM_TRY(p->scan_tmp.ensure((size_t)parts * 6 * sizeof(double)));
+    ++g_launches;
+    k_bbox_partial<<<parts, 256, 0, s>>>(pos, n, p->scan_tmp.as<double>());
+    ++g_launches;
+    k_bbox_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, box);
+  }
+  // sigma max (uniform: the value itself)
+  unsigned int* smax = reinterpret_cast<unsigned int*>(box + 8);
+  if (sig) {
+    FMM_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(unsigned int), s));
+    int parts = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    ++g_launches;
+    k_sigma_max<<<parts, 256, 0, s>>>(sig, n, smax);
+  }
+  uint64_t* k0 = p->keys0.as<uint64_t>();
+  uint64_t* k1 = p->keys1.as<uint64_t>();
+  uint32_t* v0 = p->vals0.as<uint32_t>();
+  uint32_t* v1 = p->vals1.as<uint32_t>();
+  ++g_launches;
+  k_keys<<<nb, T, 0, s>>>(pos, n, box, nullptr, 1, kMaxLevel, k0, v0);
+  FMM_CUDA_TRY(cudaGetLastError());
+  int second = 0;
+  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 63, &second, p->sort_hist, p->scan_tmp, s));
+  p->skeys = second ? k1 : k0;
+  p->sidx = second ? v1 : v0;
+  ++g_launches;
+  k_permute<<<nb, T, 0, s>>>(pos, gam, sig, sig_u, nullptr, nullptr, 1, p->sidx, n, p->sortA.as<float4>(),
+                             p->sortB.as<float4>());
+  FMM_CUDA_TRY(cudaGetLastError());
+  return tree_from_sorted(p, n, 1, nullptr, box, kMaxLevel, false, s);
+}
+
+// Problem tables of a batch to the device (ranges, sigma, periodic cubes).
+int upload_segments(fmm_plan p, const SegSpec& sg, cudaStream_t s) {
+  const int S = sg.nseg;
+  const size_t b_off = (size_t)(S + 1) * sizeof(int), b_sig = (size_t)S * sizeof(float),
+               b_box = (size_t)S * 4 * sizeof(double);
+  const size_t need = b_box + b_off + 2 * b_sig + 64;
+  if (p->seg_pinned_bytes < need) {
+    if (p->seg_pinned) cudaFreeHost(p->seg_pinned);
+    p->seg_pinned = nullptr;
+    p->seg_pinned_bytes = 0;
+    if (cudaMallocHost(&p->seg_pinned, need) != cudaSuccess) return FMM_E_NOMEM;
+    p->seg_pinned_bytes = need;
+  }
+  char* h = reinterpret_cast<char*>(p->seg_pinned);
+  double* hbox = reinterpret_cast<double*>(h);
+  int* hoff = reinterpret_cast<int*>(h + b_box);
+  float* hsig = reinterpret_cast<float*>(h + b_box + b_off);
+  unsigned int* hsm = reinterpret_cast<unsigned int*>(h + b_box + b_off + b_sig);
+  memcpy(hoff, sg.h_off, b_off);
+  FMM_TRY(p->seg_off.ensure(b_off));
+  FMM_TRY(p->seg_box.ensure(b_box));
+  FMM_TRY(p->seg_smax.ensure((size_t)S * sizeof(unsigned int)));
+  FMM_TRY(p->seg_mac.ensure((size_t)S * sizeof(SegMac)));
+  FMM_TRY(p->seg_p2p.ensure((size_t)S * sizeof(SegP2P)));
+  FMM_CUDA_TRY(cudaMemcpyAsync(p->seg_off.ptr, hoff, b_off, cudaMemcpyHostToDevice, s));
+  if (sg.h_box) {
+    memcpy(hbox, sg.h_box, b_box);
+    FMM_CUDA_TRY(cudaMemcpyAsync(p->seg_box.ptr, hbox, b_box, cudaMemcpyHostToDevice, s));
+  }
+  if (sg.h_sigma) {
+    memcpy(hsig, sg.h_sigma, b_sig);
+    memcpy(hsm, sg.h_sigma, b_sig);  // sigma > 0: its bits are the max of one value
+    FMM_TRY(p->seg_sig.ensure(b_sig));
+    FMM_CUDA_TRY(cudaMemcpyAsync(p->seg_sig.ptr, hsig, b_sig, cudaMemcpyHostToDevice, s));
+    FMM_CUDA_TRY(cudaMemcpyAsync(p->seg_smax.ptr, hsm, b_sig, cudaMemcpyHostToDevice, s));
+  }
+  return FMM_OK;
+}
+
+// A forest of independent problems: problem index above kBatchBits Morton
+// bits per axis, one root per problem, each problem its own cube and sigma.
+int build_forest(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, const SegSpec& sg,
+                 cudaStream_t s) {
+  const int T = 256;
+  const int S = sg.nseg;
+  unsigned nb = (unsigned)((n + T - 1) / T);
+  p->batched = 1;
+  p->nseg = S;
+  p->kbits = kBatchBits;
+  FMM_TRY(upload_segments(p, sg, s));
+  const int* off = p->seg_off.as<int>();
+  double* box = p->seg_box.as<double>();
+  if (!sg.h_box) {
+    ++g_launches;
+    k_bbox_seg<<<S, 256, 0, s>>>(pos, off, box);
+  }
+  if (sig) {
+    ++g_launches;
+    k_sigma_max_seg<<<S, 256, 0, s>>>(sig, off, p->seg_smax.as<unsigned int>());
+  }
+  uint64_t* k0 = p->keys0.as<uint64_t>();
+  uint64_t* k1 = p->keys1.as<uint64_t>();
+  uint32_t* v0 = p->vals0.as<uint32_t>();
+  uint32_t* v1 = p->vals1.as<uint32_t>();
+  ++g_launches;
+  k_keys<<<nb, T, 0, s>>>(pos, n, box, off, S, kBatchBits, k0, v0);
+  FMM_CUDA_TRY(cudaGetLastError());
+  int sbits = 0;
+  while ((1 << sbits) < S) ++sbits;
+  int second = 0;
+  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 3 * kBatchBits + sbits, &second, p->sort_hist, p->scan_tmp, s));
+  p->skeys = second ? k1 : k0;
+  p->sidx = second ? v1 : v0;
+  ++g_launches;
+  k_permute<<<nb, T, 0, s>>>(pos, gam, sig, 0.f, sig ? nullptr : p->seg_sig.as<float>(), off, S, p->sidx, n,
+                             p->sortA.as<float4>(), p->sortB.as<float4>());
+  FMM_CUDA_TRY(cudaGetLastError());
+  return tree_from_sorted(p, n, S, off, box, kBatchBits, true, s);
+}
+
 }  // namespace fmm
 
 namespace fmm {
@@ -423,7 +605,7 @@ int morton_keys_raw(int64_t n, const float* pos, int periodic, const double* box
     k_bbox_final<<<1, 32, 0, s>>>(partials, parts, box);
   }
   ++g_launches;
-  k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, box, keys, idx);
+  k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, box, nullptr, 1, kMaxLevel, keys, idx);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -16,6 +16,7 @@ constexpr int kP2MChunk = 32;
 __global__ void __launch_bounds__(128) k_p2m(const int* __restrict__ leaves, const int* __restrict__ begin,
                                              const int* __restrict__ end, const int* __restrict__ level,
                                              const double* __restrict__ center, const double* __restrict__ box,
+                                             const int* __restrict__ cseg,
                                              const float4* __restrict__ A, const float4* __restrict__ B, int p,
                                              float* __restrict__ M) {
   extern __shared__ float sm[];
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(128) k_p2m(const int* __restrict__ leaves, con
   float* sIm = sRe + kP2MChunk * NC;    // [32][NC]
   const int leaf = leaves[blockIdx.x];
   const int b = begin[leaf], e = end[leaf];
-  const double a = box[3] * ldexp(1.0, -level[leaf]);
+  const double a = box[4 * (cseg ? cseg[leaf] : 0) + 3] * ldexp(1.0, -level[leaf]);
   const float inv_a = (float)(1.0 / a);
   const double cx = center[3 * leaf], cy = center[3 * leaf + 1], cz = center[3 * leaf + 2];
   float acc[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -142,7 +143,9 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
   if (sh > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   ++g_launches;
   k_p2m<<<(unsigned)p->nleaves, 128, sh, s>>>(p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(),
-                                              p->c_level.as<int>(), p->c_center.as<double>(), p->scal.as<double>(),
+                                              p->c_level.as<int>(), p->c_center.as<double>(),
+                                              p->batched ? p->seg_box.as<double>() : p->scal.as<double>(),
+                                              p->batched ? p->c_seg.as<int>() : nullptr,
                                               p->sortA.as<float4>(), p->sortB.as<float4>(), pp, p->M.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   for (int l = p->nlevels - 2; l >= 0; --l) {

@@ -46,3 +46,7 @@ def test_params_and_errors_without_gpu(lib):
         qq = binding.Params.default(**bad)
         assert lib.fmm_plan_create(ctypes.byref(qq), 100, ctypes.byref(h)) == -1
     assert lib.fmm_plan_create(ctypes.byref(q), -1, ctypes.byref(h)) == -1
+    # batched entry point: argument checks before any CUDA call
+    off = (ctypes.c_int64 * 3)(0, 10, 20)
+    assert lib.fmm_eval_batch(None, 2, off, None, None, None, None, None, None, None, None) == -1
+    assert lib.fmm_plan_device_bytes(None) == 0

@@ -142,6 +142,53 @@ def plummer(n, a=0.1, seed=BASE_SEED + 5):
                 sigma=np.float32(sigma), periodic=False, name="plummer-%d" % n)
 
 
+def batch_specs(nprob=512, nmin=1e3, nmax=1e6, orders=(4, 8, 12), seed=BASE_SEED + 4):
+    """Independent free-space problems for a batched evaluation: N log-uniform
+    in [nmin, nmax], positions uniform in the unit ball or Plummer-clustered
+    (a = 0.1) with equal odds, Gaussian strengths, sigma = 1.5 (V_ball/N)^(1/3),
+    expansion order drawn from `orders`.  Returns specs; make_problem builds one."""
+    g = rng(seed)
+    N = np.exp(g.uniform(math.log(nmin), math.log(nmax), nprob)).astype(np.int64)
+    kind = g.integers(0, 2, nprob)
+    p = g.choice(np.asarray(orders), nprob)
+    seeds = g.integers(0, 2 ** 31, nprob)
+    return [dict(n=int(N[k]), kind=("ball", "plummer")[int(kind[k])], p=int(p[k]), seed=int(seeds[k]),
+                 periodic=False) for k in range(nprob)]
+
+
+def request_specs(rate=200.0, horizon_s=60.0, nmin=1e4, nmax=4e6, orders=(4, 8, 12), periodic_frac=0.3,
+                  seed=BASE_SEED + 5):
+    """A Poisson request stream: arrival times with mean rate `rate` per second
+    over `horizon_s`, N log-uniform in [nmin, nmax], order from `orders`;
+    `periodic_frac` of the requests are random-spectrum blobs on a ceil(N^(1/3))^3
+    lattice in the periodic cube [0, 2 pi)^3, the rest Plummer-clustered free-space
+    problems.  Returns specs sorted by arrival time."""
+    g = rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += g.exponential(1.0 / rate)
+        if t >= horizon_s:
+            break
+        n = int(math.exp(g.uniform(math.log(nmin), math.log(nmax))))
+        per = bool(g.random() < periodic_frac)
+        if per:
+            m = int(math.ceil(n ** (1.0 / 3.0)))
+            n = m ** 3
+        out.append(dict(t=t, n=n, kind="spectrum" if per else "plummer", p=int(g.choice(np.asarray(orders))),
+                        seed=int(g.integers(0, 2 ** 31)), periodic=per))
+    return out
+
+
+def make_problem(spec):
+    """Particles of one batch_specs / request_specs entry."""
+    if spec["kind"] == "ball":
+        return uniform_ball(spec["n"], seed=spec["seed"])
+    if spec["kind"] == "plummer":
+        return plummer(spec["n"], seed=spec["seed"])
+    m = int(round(spec["n"] ** (1.0 / 3.0)))
+    return random_spectrum(m, seed=spec["seed"])
+
+
 def random_cloud(n, seed=BASE_SEED + 6, box=1.0, zero_net=False):
     g = rng(seed)
     pos = g.random((n, 3)) * box
