@@ -47,6 +47,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-targets", type=int, default=48)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer runs (profiling)")
+    ap.add_argument("--workload", default="taylor-green", choices=["taylor-green", "batched", "serving"],
+                    help="taylor-green: the 128^3 periodic evaluation (default); batched: 512 independent "
+                         "free-space problems; serving: a Poisson request stream")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default line")
+    ap.add_argument("--serving-seconds", type=float, default=1.0, help="arrival horizon of the serving run")
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="mean arrivals per second")
     return ap.parse_args()
 
 
@@ -183,8 +189,188 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+SERVING_ORDERS = (4, 8, 12)
+
+
+def serving_inputs(specs):
+    """Host arrays (page-locked) of a request stream: Plummer requests take the
+    first N particles of one Plummer sample (independent draws, so every prefix
+    is a Plummer sample of its size), spectrum requests the random-spectrum
+    lattice of their size (one per size)."""
+    import numpy as np
+    import torch
+    import workloads
+    nmax = max([r["n"] for r in specs if not r["periodic"]] + [1])
+    pool = workloads.plummer(nmax, seed=workloads.BASE_SEED + 50)
+    ppos = torch.from_numpy(pool["pos"]).pin_memory().numpy()
+    pgam = torch.from_numpy(pool["gamma"]).pin_memory().numpy()
+    spec = {}
+    out = []
+    for r in specs:
+        n = r["n"]
+        if r["periodic"]:
+            m = int(round(n ** (1.0 / 3.0)))
+            if m not in spec:
+                w = workloads.random_spectrum(m, seed=r["seed"])
+                spec[m] = (torch.from_numpy(w["pos"]).pin_memory().numpy(),
+                           torch.from_numpy(w["gamma"]).pin_memory().numpy(), float(w["sigma"]))
+            pos, gam, sig = spec[m]
+            out.append(dict(pos=pos, gamma=gam, sigma=sig, box=(0.0, 0.0, 0.0, 2 * math.pi)))
+        else:
+            out.append(dict(pos=ppos[:n], gamma=pgam[:n], sigma=workloads.plummer_sigma(n), box=None))
+    return out
+
+
+def serve_stream(specs, inputs, workers, batching, budget):
+    """Submit every request at its arrival time; per-request latency = completion - arrival."""
+    import numpy as np
+    from paper_1106_5273_gb300 import Server
+    srv = Server(workers=workers, batching=batching, theta=0.5, ncrit=64, hbm_budget_bytes=budget,
+                 max_batch_particles=16 << 20)
+    # warm-up (untimed): one request of every class creates the plans and operator caches
+    seen = {}
+    for r, x in zip(specs, inputs):
+        seen.setdefault((r["p"], r["periodic"]), (r, x))
+    for r, x in seen.values():
+        t = srv.submit(x["pos"], x["gamma"], r["p"], x["sigma"], periodic=r["periodic"], box=x["box"])
+        srv.wait(t, 600.0)
+    c0 = srv.counters()
+    t0 = srv.clock()
+    tickets = []
+    for r, x in zip(specs, inputs):
+        while True:
+            dt = t0 + r["t"] - srv.clock()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.001))
+        tickets.append(srv.submit(x["pos"], x["gamma"], r["p"], x["sigma"], periodic=r["periodic"], box=x["box"]))
+    lat, done, bsz, status = [], [], [], []
+    for r, t in zip(specs, tickets):
+        res, _, _ = srv.wait(t, 3600.0)
+        lat.append(res["t_done"] - (t0 + r["t"]))
+        done.append(res["t_done"])
+        bsz.append(res["batch_problems"])
+        status.append(res["status"])
+    c1 = srv.counters()
+    srv.close()
+    parts = sum(r["n"] for r in specs)
+    span = max(done) - t0
+    lat = np.array(lat) * 1e3
+    return {"particles_per_s": parts / span, "makespan_s": span, "latency_ms": {
+                "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "max": float(lat.max())},
+            "requests": len(specs), "particles": parts, "failed": int(sum(1 for s_ in status if s_ != 0)),
+            "batches": c1["batches"] - c0["batches"], "mean_batch_problems": float(np.mean(bsz)),
+            "peak_device_bytes": c1["peak_bytes"], "memory_waits": c1["memory_waits"] - c0["memory_waits"],
+            "workers": workers, "batching": bool(batching)}
+
+
+def run_serving(args, horizon=None):
+    """Poisson request stream (N log-uniform in [1e4, 4e6], p in {4, 8, 12}, 30% periodic
+    random-spectrum lattices, 70% Plummer clusters, theta 0.5, ncrit 64): continuous batching
+    with two workers against one request per call on one worker."""
+    import workloads
+    horizon = args.serving_seconds if horizon is None else horizon
+    specs = workloads.request_specs(rate=args.serving_rate, horizon_s=horizon, orders=SERVING_ORDERS)
+    inputs = serving_inputs(specs)
+    budget = 200 << 30
+    served = serve_stream(specs, inputs, 2, 1, budget)
+    plain = serve_stream(specs, inputs, 1, 0, budget)
+    return {"stream": "Poisson %.0f req/s for %.1f s (%d requests, %d particles), N log-uniform [1e4, 4e6], "
+                      "p in {4,8,12}, 30%% periodic spectrum / 70%% Plummer, host arrays in and out"
+                      % (args.serving_rate, horizon, len(specs), served["particles"]),
+            "continuous_batching": served, "one_request_per_call": plain,
+            "speedup_particles_per_s": served["particles_per_s"] / plain["particles_per_s"],
+            "p99_ratio": plain["latency_ms"]["p99"] / served["latency_ms"]["p99"]}
+
+
+def run_batched(args):
+    """512 independent free-space problems (N log-uniform [1e3, 1e6], ball or Plummer, p in
+    {4, 8, 12}, theta 0.5, ncrit 64): one fmm_eval_batch per order against one
+    fmm_eval_velocity_stretching per problem; inputs resident in HBM."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1106_5273_gb300 import Params, Plan, kernel_launch_count
+    specs = workloads.batch_specs()
+    groups = {}
+    for sp in specs:
+        groups.setdefault(sp["p"], []).append(sp)
+    dev = {}
+    for p, lst in sorted(groups.items()):
+        probs = [workloads.make_problem(sp) for sp in lst]
+        off = np.zeros(len(probs) + 1, np.int64)
+        for k, w in enumerate(probs):
+            off[k + 1] = off[k] + w["pos"].shape[0]
+        pos = torch.from_numpy(np.concatenate([w["pos"] for w in probs])).cuda()
+        gam = torch.from_numpy(np.concatenate([w["gamma"] for w in probs])).cuda()
+        sig = np.array([w["sigma"] for w in probs], np.float32)
+        dev[p] = dict(off=off, pos=pos, gam=gam, sig=sig, n=int(off[-1]),
+                      vel=torch.empty_like(pos), dg=torch.empty_like(pos),
+                      plan=Plan(int(off[-1]), Params.default(p=p, theta=0.5, ncrit=64)),
+                      one=Plan(int(max(np.diff(off))), Params.default(p=p, theta=0.5, ncrit=64)))
+    ntot = sum(d["n"] for d in dev.values())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step_batched():
+        for d in dev.values():
+            d["plan"].eval_batch(d["off"], d["pos"], d["gam"], sigma_prob=d["sig"], vel=d["vel"], dgamma=d["dg"])
+
+    def step_plain():
+        for d in dev.values():
+            o = d["off"]
+            for k in range(len(o) - 1):
+                a, b = int(o[k]), int(o[k + 1])
+                d["one"].eval(d["pos"][a:b], d["gam"][a:b], sigma_uniform=float(d["sig"][k]),
+                              vel=d["vel"][a:b], dgamma=d["dg"][a:b])
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        l0 = kernel_launch_count()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms), (kernel_launch_count() - l0) // steps
+
+    steps, warm = max(1, min(args.steps, 5)), max(3, args.warmup)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_b, l_b = timed(step_batched, steps, warm)
+    t_p, l_p = timed(step_plain, max(1, steps // 2), 1)
+    clk = clocks.stop()
+    return {"metric": "FMM batched evaluation particles/s (512 independent problems)", "value": ntot / (t_b * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": t_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched-512-free-space", "problems": len(specs), "n_total": ntot,
+                       "n_range": [1000, 1000000], "orders": {str(p): len(g) for p, g in sorted(groups.items())},
+                       "theta": 0.5, "ncrit": 64, "l2": "flushed (512 MB write) before every timed step"},
+            "gpu_launches": l_b,
+            "one_problem_per_call": {"value": ntot / (t_p * 1e-3), "ms_per_step": t_p, "gpu_launches": l_p},
+            "speedup": t_p / t_b, "clocks": clk}
+
+
 def main():
     args = parse()
+    if args.workload in ("batched", "serving") and args.impl == "fmm":
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if int(os.environ.get("RANK", "0")) == 0:
+            out = run_batched(args) if args.workload == "batched" else dict(
+                metric="FMM serving particles/s (Poisson request stream)", **run_serving(args))
+            print(json.dumps(out), flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -307,6 +493,9 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if not args.no_serving and world == 1:
+            plan.close()
+            line["serving"] = run_serving(args)
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:

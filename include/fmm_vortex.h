@@ -184,6 +184,97 @@ int fmm_eval_batch(fmm_plan plan, int32_t nprob, const int64_t* offsets, const f
  * largest evaluation seen and is kept for the next one). */
 int64_t fmm_plan_device_bytes(fmm_plan plan);
 
+/*
+ * Serving loop: a request queue in front of fmm_eval_batch (continuous
+ * batching; the paper evaluates one problem per call).  Worker threads, each
+ * with its own CUDA stream and device-resident plans (one per expansion order
+ * and boundary type, kept between requests with their operator caches), take
+ * requests as they arrive: a free worker forms a batch from the oldest queued
+ * request and the later queued requests of the same (p, periodic) class, in
+ * arrival order, up to max_batch_particles / max_batch_problems, and only as
+ * far as the device-memory budget admits (see below).  Batches of different
+ * workers run concurrently on the device.  Requests that arrive while batches
+ * run wait in the queue and join the next batch of their class.
+ *
+ * Memory admission: the server accounts every device byte it holds (plans and
+ * staging buffers).  A batch is admitted when the bytes held by all workers,
+ * with this worker's plan grown to the batch's estimated need, stay within
+ * hbm_budget_bytes.  The need of a class (p, periodic) is learned from its
+ * evaluations as fixed + per-particle bytes (upper envelope of what the plans
+ * grew to); the first batch of a class runs alone, so its footprint is
+ * measured before anything is admitted next to it.  When a batch does not fit
+ * the worker first frees idle plans, then takes fewer requests, then waits
+ * for other workers (which free their idle plans while anyone waits).  A
+ * request that does not fit the budget on its own completes with FMM_E_NOMEM.
+ *
+ * batching = 0 gives the one-problem-per-call path for comparison: every
+ * request is evaluated alone through fmm_eval_velocity_stretching.
+ * In batching mode each result is bit-identical to the request evaluated alone
+ * through fmm_eval_batch with a plan of the server's parameters.
+ */
+typedef struct fmm_server_s* fmm_server;
+
+typedef struct {
+  int32_t workers;              /* concurrent batches (threads + streams), 1..16 */
+  int32_t batching;             /* 1 continuous batching, 0 one request per evaluation */
+  int64_t hbm_budget_bytes;     /* device bytes the server may hold (> 0) */
+  int64_t max_batch_particles;  /* particles per batch (a larger single request runs alone) */
+  int32_t max_batch_problems;   /* requests per batch, 1..FMM_BATCH_MAX */
+  float theta;                  /* as fmm_params; shared by every request */
+  int32_t ncrit;
+  float sigma_sep;
+  int32_t images;
+  int32_t m2l_mode;
+} fmm_server_params;
+
+/* One request.  Host arrays; the caller keeps them valid (and does not read
+ * the outputs) until fmm_server_wait reports the ticket done.  Page-locked
+ * memory gives the fastest copies. */
+typedef struct {
+  int64_t n;             /* particles, >= 0 */
+  int32_t p;             /* expansion order 1..16 */
+  int32_t periodic;      /* 0 free space, 1 periodic cube `box` */
+  double box[4];         /* box_min xyz, side (periodic only) */
+  float sigma;           /* core width of every particle, > 0 */
+  const float* pos;      /* [n][3] */
+  const float* gamma;    /* [n][3] */
+  float* vel;            /* [n][3] output or NULL */
+  float* dgamma;         /* [n][3] output or NULL */
+} fmm_request;
+
+typedef struct {
+  int32_t status;        /* FMM_OK or the FMM_E_* code of its evaluation */
+  int32_t batch_problems;/* requests in the batch that carried it */
+  int32_t worker;        /* worker that ran it */
+  int32_t pad;
+  int64_t batch_particles;
+  double t_submit;       /* seconds on the server's steady clock (0 = creation) */
+  double t_start;        /* batch formed */
+  double t_done;         /* outputs copied back */
+} fmm_request_result;
+
+/* Server counters: batches run, requests done, particles done, the largest
+ * number of device bytes held at once, and the batches that waited for memory. */
+typedef struct {
+  int64_t batches, requests, particles, peak_bytes, memory_waits;
+} fmm_server_counters;
+
+void fmm_server_params_default(fmm_server_params* prm); /* 2 workers, batching, 64 GiB, 16M particles,
+                                                           4096 problems, theta 0.5, ncrit 64,
+                                                           sigma_sep 5, images 3, AUTO */
+int fmm_server_create(const fmm_server_params* prm, fmm_server* out);  /* current CUDA device */
+/* Queue a request; *ticket identifies it.  FMM_E_INVAL for a bad request. */
+int fmm_server_submit(fmm_server srv, const fmm_request* req, int64_t* ticket);
+/* Wait up to timeout_s seconds (< 0: no limit) for a ticket; FMM_OK and *out
+ * filled once done (the ticket is then forgotten), FMM_E_TIMEOUT if not done
+ * yet, FMM_E_INVAL for an unknown ticket.  The request's own status is out->status. */
+int fmm_server_wait(fmm_server srv, int64_t ticket, double timeout_s, fmm_request_result* out);
+/* Seconds on the server's clock (for arrival schedules). */
+double fmm_server_clock(fmm_server srv);
+int fmm_server_get_counters(fmm_server srv, fmm_server_counters* out);
+/* Finish queued work, stop the workers, free everything.  NULL is ok. */
+void fmm_server_destroy(fmm_server srv);
+
 /* Release every resource of the plan (synchronizes the device). NULL is ok. */
 void fmm_plan_destroy(fmm_plan plan);
 
@@ -229,6 +320,17 @@ int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gam
 int fmm_morton_order_noalloc(int64_t n, const float* pos, int periodic, const double* box_min,
                              double box_len, uint64_t* keys_out, uint32_t* order_out,
                              void* cuda_stream);
+
+/*
+ * Self-test of the bounded device wait that guards every mbarrier wait of the
+ * tensor-core M2L kernel (a wait that gives up records FMM_E_TIMEOUT instead of
+ * hanging, and the kernel returns).  One thread of one CTA waits on a shared
+ * memory barrier with at most `spins` polls (1 .. 2^24): arrive = 1 completes
+ * the barrier first (returns FMM_OK), arrive = 0 leaves it incomplete so the
+ * wait runs out (returns FMM_E_TIMEOUT).  Synchronous; FMM_E_INVAL for bad
+ * arguments.  The CUDA context stays usable afterwards.
+ */
+int fmm_selftest_bounded_wait(int64_t spins, int arrive, void* cuda_stream);
 
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all plans and entry points; for launch accounting in benchmarks). */

@@ -11,7 +11,7 @@ The binding is loaded on first use, so `python -m paper_1106_5273_gb300.build`
 works before the library exists; using the binding without the library
 raises ImportError (there is no fallback).
 """
-__all__ = ["Params", "Plan", "Stats", "FmmError", "direct", "lib", "library_path", "kernel_launch_count", "morton_order_noalloc", "NOALLOC_MAX_N", "BATCH_MAX", "BATCH_DEPTH",
+__all__ = ["Params", "Plan", "Stats", "FmmError", "direct", "lib", "library_path", "kernel_launch_count", "morton_order_noalloc", "NOALLOC_MAX_N", "BATCH_MAX", "BATCH_DEPTH", "Server", "ServerParams",
            "FMM_M2L_AUTO", "FMM_M2L_SIMT", "FMM_M2L_TENSOR"]
 
 

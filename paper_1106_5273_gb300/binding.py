@@ -78,6 +78,7 @@ for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+lib.fmm_selftest_bounded_wait.argtypes = [_i64, ctypes.c_int, _vp]
 lib.fmm_eval_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 lib.fmm_plan_device_bytes.argtypes = [_vp]
 lib.fmm_plan_device_bytes.restype = _i64
@@ -249,6 +250,11 @@ def morton_order_noalloc(pos, keys_out, order_out, periodic=False, box_min=None,
     return keys_out, order_out
 
 
+def selftest_bounded_wait(spins, arrive, stream=None):
+    """fmm_selftest_bounded_wait: FMM_OK (0) or FMM_E_TIMEOUT (-4)."""
+    return int(lib.fmm_selftest_bounded_wait(int(spins), int(arrive), _stream_ptr(stream)))
+
+
 def kernel_launch_count():
     """Kernels launched by the CUDA library since it was loaded."""
     return int(lib.fmm_kernel_launch_count())
@@ -267,3 +273,116 @@ def direct(pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, str
                                               _dptr(vel, name="vel"), _dptr(dgamma, name="dgamma"),
                                               _stream_ptr(stream)), "fmm_direct_velocity_stretching")
     return vel, dgamma
+
+
+# ---------------------------------------------------------------- serving loop
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("batching", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("max_batch_particles", ctypes.c_int64), ("max_batch_problems", ctypes.c_int32),
+                ("theta", ctypes.c_float), ("ncrit", ctypes.c_int32), ("sigma_sep", ctypes.c_float),
+                ("images", ctypes.c_int32), ("m2l_mode", ctypes.c_int32)]
+
+    @classmethod
+    def default(cls, **kw):
+        q = cls()
+        lib.fmm_server_params_default(ctypes.byref(q))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return q
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_int32), ("periodic", ctypes.c_int32),
+                ("box", ctypes.c_double * 4), ("sigma", ctypes.c_float), ("pos", ctypes.c_void_p),
+                ("gamma", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("dgamma", ctypes.c_void_p)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_problems", ctypes.c_int32), ("worker", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("batch_particles", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("requests", ctypes.c_int64), ("particles", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("memory_waits", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+lib.fmm_server_params_default.argtypes = [ctypes.POINTER(ServerParams)]
+lib.fmm_server_params_default.restype = None
+lib.fmm_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(_vp)]
+lib.fmm_server_submit.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(_i64)]
+lib.fmm_server_wait.argtypes = [_vp, _i64, ctypes.c_double, ctypes.POINTER(RequestResult)]
+lib.fmm_server_clock.argtypes = [_vp]
+lib.fmm_server_clock.restype = ctypes.c_double
+lib.fmm_server_get_counters.argtypes = [_vp, ctypes.POINTER(ServerCounters)]
+lib.fmm_server_destroy.argtypes = [_vp]
+lib.fmm_server_destroy.restype = None
+
+
+class Server:
+    """fmm_server_*: queue of host-array requests, continuous batching on the device."""
+
+    def __init__(self, params=None, **kw):
+        self.params = params if params is not None else ServerParams.default(**kw)
+        h = _vp()
+        _check(lib.fmm_server_create(ctypes.byref(self.params), ctypes.byref(h)), "fmm_server_create")
+        self._h = h
+        self._live = {}
+
+    def submit(self, pos, gamma, p, sigma, periodic=False, box=None, vel=None, dgamma=None):
+        """Queue one request (numpy float32 [n,3] arrays, kept alive until wait); returns a ticket."""
+        import numpy as np
+        for a in (pos, gamma):
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+        n = pos.shape[0]
+        if vel is None:
+            vel = np.empty((n, 3), np.float32)
+        if dgamma is None:
+            dgamma = np.empty((n, 3), np.float32)
+        r = Request()
+        r.n, r.p, r.periodic, r.sigma = n, int(p), 1 if periodic else 0, float(sigma)
+        if box is not None:
+            for k in range(4):
+                r.box[k] = float(box[k])
+        r.pos, r.gamma = pos.ctypes.data, gamma.ctypes.data
+        r.vel = vel.ctypes.data if vel is not False else None
+        r.dgamma = dgamma.ctypes.data if dgamma is not False else None
+        t = _i64()
+        _check(lib.fmm_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "fmm_server_submit")
+        self._live[t.value] = (pos, gamma, vel, dgamma)
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        """(result dict, vel, dgamma) of a ticket; raises FmmError on timeout."""
+        res = RequestResult()
+        _check(lib.fmm_server_wait(self._h, int(ticket), float(timeout), ctypes.byref(res)), "fmm_server_wait")
+        _, _, vel, dg = self._live.pop(int(ticket))
+        return res.as_dict(), vel, dg
+
+    def clock(self):
+        return float(lib.fmm_server_clock(self._h))
+
+    def counters(self):
+        c = ServerCounters()
+        _check(lib.fmm_server_get_counters(self._h, ctypes.byref(c)), "fmm_server_get_counters")
+        return c.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fmm_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -177,6 +177,9 @@ __host__ __device__ inline void m2l_key_decode(uint64_t key, int* delta, double 
   tau[2] = (double)key_field(key, 0) * f;
 }
 
+// K chunks of 64 coefficients (4 MMA K-steps of 16) covering P inputs.
+__host__ __device__ inline int m2l_kchunks(int P) { return ((P + 15) / 16 + 3) / 4; }
+
 // Level / tile layout of the current tree, passed to kernels by value.
 struct LevelInfo {
   int nlevels;

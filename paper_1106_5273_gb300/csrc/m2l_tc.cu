@@ -62,8 +62,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: false when the limit is reached (the caller aborts).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  for (long long i = 0; i < kSpin; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                          long long limit = kSpin) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 1023) == 1023 && *abort) return false;
   }
@@ -197,8 +198,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(empty(stage), ph ^ 1u, abort)) return false;
       const int st = rg.x + it / nkc, kc = it % nkc;
       const size_t key = (size_t)st_slot[st];
-      const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * 2 + kc) * (128 * 64);
-      const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * 2 + kc) * (128 * 64);
+      const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * nkc + kc) * (128 * 64);
+      const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * nkc + kc) * (128 * 64);
       const uint32_t a0 = sbase + stage * kStageBytes;
       mbar_arrive_tx(fullA(stage), 2 * kABytes);
       bulk_g2s(a0, hi, kABytes, fullA(stage));
@@ -282,6 +283,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Self-test of the bounded wait above: one thread waits on a barrier that
+// either completes (arrive = 1: it arrives first) or that nothing completes
+// (arrive = 0), polling at most `spins` times; FMM_OK or FMM_E_TIMEOUT.
+__global__ void k_wait_selftest(long long spins, int arrive, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    const uint32_t b = smem_u32(&bar);
+    abort_flag = 0;
+    mbar_init(b, 1);
+    if (arrive) mbar_arrive(b);
+    *status = mbar_wait(b, 0u, &abort_flag, spins) ? FMM_OK : FMM_E_TIMEOUT;
+  }
+}
+
 }  // namespace
 
 int m2l_tensor(fmm_plan p, cudaStream_t s) {
@@ -294,14 +310,10 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
     li.tile_begin[l] = p->tile_begin[l];
   }
   const int ksteps = (p->P + 15) / 16;
-  const int nkc = (ksteps + 3) / 4;
+  const int nkc = m2l_kchunks(p->P);
   const int last = ksteps - 4 * (nkc - 1);
   const size_t sh = (size_t)kBarOff + 128 + 1024;
-  static bool attr = false;
-  if (!attr) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    attr = true;
-  }
+  FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   ++g_launches;
   k_m2l_tc<<<(unsigned)p->ntiles, kThreads, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
                                                       p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
@@ -312,3 +324,20 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
 }
 
 }  // namespace fmm
+
+extern "C" int fmm_selftest_bounded_wait(int64_t spins, int arrive, void* stream) {
+  if (spins < 1 || spins > fmm::kSpin || (arrive != 0 && arrive != 1)) return FMM_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d = nullptr;
+  int h = FMM_E_CUDA;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return FMM_E_NOMEM;
+  ++fmm::g_launches;
+  fmm::k_wait_selftest<<<1, 32, 0, s>>>((long long)spins, arrive, d);
+  if (cudaGetLastError() == cudaSuccess && cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess) {
+  } else {
+    h = FMM_E_CUDA;
+  }
+  cudaFree(d);
+  return h;
+}

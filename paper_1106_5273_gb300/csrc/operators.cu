@@ -138,7 +138,7 @@ Mat lattice_matrix(int p, int images) {
 // ---- device: M2L operator per translation key
 
 __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __restrict__ slots, int nkeys, int p,
-                            float* __restrict__ T32, __nv_bfloat16* __restrict__ Tbf, int tc) {
+                            float* __restrict__ T32, __nv_bfloat16* __restrict__ Tbf, int nkc) {
   __shared__ cd I[(2 * kPMax - 1) * (2 * kPMax) / 2];
   __shared__ double nu[kNCoefMax];
   __shared__ double rp[kPMax];
@@ -162,9 +162,9 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
     nu[r] = nu_d(n, m);
   }
   if (threadIdx.x < (unsigned)p) rp[threadIdx.x] = ldexp(1.0, delta * (int)threadIdx.x);
-  if (tc) {  // zero this slot's BF16 tiles (padding rows and columns stay zero)
-    uint4* z = reinterpret_cast<uint4*>(Tbf + (size_t)key_id * 2 * 128 * 128);
-    for (int i = threadIdx.x; i < 2 * 128 * 128 / 8; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (nkc) {  // zero this slot's BF16 tiles (padding rows and columns stay zero)
+    uint4* z = reinterpret_cast<uint4*>(Tbf + (size_t)key_id * 2 * nkc * 128 * 64);
+    for (int i = threadIdx.x; i < 2 * nkc * 128 * 64 / 8; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
@@ -183,15 +183,15 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
     if (pi == 0) v = po == 0 ? s * (A.re + B.re) : s * (A.im + B.im);
     else v = po == 0 ? -s * (B.im - A.im) : s * (B.re - A.re);
     T32[(size_t)key_id * P * P + e] = (float)v;
-    if (tc) {
-      // [key][hi/lo][K chunk of 64][128 rows][64], 16-byte groups of a row
+    if (nkc) {
+      // [key][hi/lo][nkc K chunks of 64][128 rows][64], 16-byte groups of a row
       // stored in the 128-byte swizzle order (group j at j ^ (row & 7))
       __nv_bfloat16 hi = __double2bfloat16(v);
       __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
       const int kc = c >> 6, j = (c & 63) >> 3, el = c & 7;
       const size_t within = (size_t)r * 64 + (size_t)(((j ^ (r & 7)) << 3) + el);
-      Tbf[(((size_t)key_id * 2 + 0) * 2 + kc) * (128 * 64) + within] = hi;
-      Tbf[(((size_t)key_id * 2 + 1) * 2 + kc) * (128 * 64) + within] = lo;
+      Tbf[(((size_t)key_id * 2 + 0) * nkc + kc) * (128 * 64) + within] = hi;
+      Tbf[(((size_t)key_id * 2 + 1) * nkc + kc) * (128 * 64) + within] = lo;
     }
   }
 }
@@ -264,6 +264,8 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
   p->h_keys.resize(nk);
   FMM_CUDA_TRY(cudaMemcpyAsync(p->h_keys.data(), p->ukeys.ptr, nk * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  // BF16 tiles only for the tensor-core path (P <= 128 output rows; the
+  // plan's M2L mode does not change between evaluations)
   const int tc = p->last_tc;
   // bound the cache: start over when it would exceed 1 << 16 operators
   if ((int64_t)p->tcache.size() + nk > (1 << 16)) p->tcache.clear();
@@ -286,7 +288,7 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
   if (need > p->tcache_cap) {
     int64_t cap = std::max<int64_t>(need, p->tcache_cap * 2);
     FMM_TRY(p->T32.grow_copy((size_t)cap * P * P * sizeof(float), s));
-    FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * 128 * 128 * sizeof(__nv_bfloat16), s));
+    if (tc) FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * m2l_kchunks(P) * 128 * 64 * sizeof(__nv_bfloat16), s));
     p->tcache_cap = cap;
   }
   if (!miss_keys.empty()) {
@@ -297,11 +299,11 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
     FMM_CUDA_TRY(cudaMemcpyAsync(p->tmiss_slots.ptr, miss_slots.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
     ++g_launches;
     k_build_m2l<<<(unsigned)nm, 256, 0, s>>>(p->tmiss_keys.as<uint64_t>(), p->tmiss_slots.as<int>(), (int)nm,
-                                             p->prm.p, p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(), 1);
+                                             p->prm.p, p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(),
+                                             tc ? m2l_kchunks(P) : 0);
     FMM_CUDA_TRY(cudaGetLastError());
     p->n_built = nm;
   }
-  (void)tc;
   FMM_TRY(p->tslot_map.ensure(nk * sizeof(int)));
   FMM_CUDA_TRY(cudaMemcpyAsync(p->tslot_map.ptr, p->h_map.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s));
   ++g_launches;

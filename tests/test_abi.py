@@ -50,3 +50,31 @@ def test_params_and_errors_without_gpu(lib):
     off = (ctypes.c_int64 * 3)(0, 10, 20)
     assert lib.fmm_eval_batch(None, 2, off, None, None, None, None, None, None, None, None) == -1
     assert lib.fmm_plan_device_bytes(None) == 0
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """ctypes mirrors of the header's structs have the C sizes (gcc on this host)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "fmm_vortex.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu",'
+                   'sizeof(fmm_params), sizeof(fmm_stats), sizeof(fmm_server_params), sizeof(fmm_request),'
+                   'sizeof(fmm_request_result), sizeof(fmm_server_counters));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sizes = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    from paper_1106_5273_gb300 import binding as b
+    assert sizes == [ctypes.sizeof(t) for t in (b.Params, b.Stats, b.ServerParams, b.Request, b.RequestResult,
+                                                 b.ServerCounters)]
+
+
+def test_server_params_validated_without_gpu(lib):
+    from paper_1106_5273_gb300 import binding as b
+    h = ctypes.c_void_p()
+    for bad in (dict(workers=0), dict(workers=17), dict(batching=2), dict(hbm_budget_bytes=0),
+                dict(max_batch_problems=0), dict(theta=1.0), dict(ncrit=0), dict(images=0)):
+        q = b.ServerParams.default(**bad)
+        assert lib.fmm_server_create(ctypes.byref(q), ctypes.byref(h)) == -1
+    assert lib.fmm_server_submit(None, None, None) == -1

@@ -241,3 +241,18 @@ def test_full_size_taylor_green_128(m2l_mode):
     assert rel_l2(s, st_) < 1e-3
     stt = plan.stats()
     assert stt.nleaves == 32768 and stt.m2l_tensor == (1 if m2l_mode == 2 else 0)
+
+
+@pytest.mark.parametrize("m2l_mode", [0, 1])
+def test_high_order_p12_converges(m2l_mode):
+    """p = 12 (144 coefficients: the SIMT M2L; no BF16 operator tiles) on a
+    Plummer cloud: against the FP64 direct sum, more accurate than p = 8."""
+    from oracle import direct as od
+    w = workloads.plummer(4000, seed=12, sigma_rule="halfmass")
+    ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], float(w["sigma"]), skip_self=True)
+    plan, u12, s12 = run_fmm(w, 12, 0.5, 32, m2l_mode=m2l_mode)
+    _, u8, s8 = run_fmm(w, 8, 0.5, 32, m2l_mode=m2l_mode)
+    assert plan.stats().m2l_pairs > 0 and plan.stats().m2l_tensor == 0
+    e12, e8 = rel_l2(u12, ud), rel_l2(u8, ud)
+    assert e12 < 0.5 * e8 and e12 < 1e-4, (e12, e8)
+    assert rel_l2(s12, sd) < rel_l2(s8, sd)

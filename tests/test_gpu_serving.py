@@ -1,0 +1,149 @@
+"""Serving loop (fmm_server_*): continuous batching of host-array requests.
+Each result is bit-identical to the request evaluated alone through
+fmm_eval_batch, requests of two workers overlap on the device, and the
+device-memory budget admits batches (or refuses a request that cannot fit)."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_common import rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+THETA, NCRIT = 0.5, 32
+
+
+def _requests():
+    out = []
+    for k, (kind, n, p) in enumerate([("ball", 3000, 4), ("plummer", 5000, 8), ("ball", 800, 4),
+                                       ("plummer", 12000, 4), ("ball", 2500, 8), ("plummer", 40, 4)]):
+        w = (workloads.uniform_ball if kind == "ball" else workloads.plummer)(n, seed=500 + k)
+        out.append(dict(w=w, p=p, periodic=False, box=None))
+    L = 2 * math.pi
+    for k, m in enumerate([8, 12]):
+        w = workloads.random_spectrum(m, seed=600 + k, kmax=3)
+        out.append(dict(w=w, p=6, periodic=True, box=(0.0, 0.0, 0.0, L)))
+    tg = workloads.taylor_green(10)
+    out.append(dict(w=tg, p=6, periodic=True, box=(0.0, 0.0, 0.0, L)))
+    return out
+
+
+def _alone(r):
+    """The request through fmm_eval_batch as a batch of one, plan parameters of the server."""
+    import torch
+    from paper_1106_5273_gb300 import Plan, Params
+    w = r["w"]
+    n = w["pos"].shape[0]
+    kw = dict(p=r["p"], theta=THETA, ncrit=NCRIT)
+    if r["periodic"]:
+        kw.update(periodic=1, box_min=np.array(r["box"][:3]), box_len=r["box"][3], images=3)
+    plan = Plan(n, Params.default(**kw))
+    u, s = plan.eval_batch(np.array([0, n]), to_dev(w["pos"]), to_dev(w["gamma"]),
+                           sigma_prob=np.array([w["sigma"]], np.float32),
+                           boxes=np.array([r["box"]]) if r["periodic"] else None)
+    torch.cuda.synchronize()
+    return u.cpu().numpy(), s.cpu().numpy()
+
+
+def _submit_all(srv, reqs):
+    return [srv.submit(np.ascontiguousarray(r["w"]["pos"], np.float32),
+                       np.ascontiguousarray(r["w"]["gamma"], np.float32), r["p"], float(r["w"]["sigma"]),
+                       periodic=r["periodic"], box=r["box"]) for r in reqs]
+
+
+def test_serving_results_identical_alone_and_in_mix():
+    from oracle import direct as od
+    from paper_1106_5273_gb300 import Server
+    reqs = _requests()
+    srv = Server(workers=2, batching=1, theta=THETA, ncrit=NCRIT, max_batch_problems=64)
+    tickets = _submit_all(srv, reqs)
+    results = [srv.wait(t, 120.0) for t in tickets]
+    assert all(res["status"] == 0 for res, _, _ in results)
+    assert max(res["batch_problems"] for res, _, _ in results) > 1  # requests did share batches
+    for r, (res, u, s) in zip(reqs, results):
+        ua, sa = _alone(r)
+        assert np.array_equal(u, ua) and np.array_equal(s, sa), (r["p"], r["w"]["pos"].shape)
+    # accuracy of a free-space request against the FP64 direct sum, within the
+    # method error of the CPU oracle FMM at the same p, theta, ncrit
+    from oracle import fmm as ofmm
+    r, (res, u, s) = reqs[0], results[0]
+    w = r["w"]
+    ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], float(w["sigma"]), skip_self=True)
+    ref = ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), r["p"], THETA, NCRIT)
+    assert rel_l2(u, ud) < 1.5 * rel_l2(ref.u, ud) + 2e-5
+    assert rel_l2(s, sd) < 1.5 * rel_l2(ref.s, sd) + 5e-5
+    c = srv.counters()
+    assert c["requests"] == len(reqs) and c["particles"] == sum(r["w"]["pos"].shape[0] for r in reqs)
+    assert c["batches"] < len(reqs)
+    srv.close()
+
+
+def test_serving_one_request_per_call_mode():
+    from paper_1106_5273_gb300 import Server
+    reqs = _requests()
+    srv = Server(workers=1, batching=0, theta=THETA, ncrit=NCRIT)
+    tickets = _submit_all(srv, reqs)
+    results = [srv.wait(t, 120.0) for t in tickets]
+    assert all(res["status"] == 0 and res["batch_problems"] == 1 for res, _, _ in results)
+    for r, (res, u, s) in zip(reqs, results):
+        ua, sa = _alone(r)  # 21-bit keys there, 16 here: same trees at these sizes, rounding-level differences
+        assert rel_l2(u, ua) < 1e-5 and rel_l2(s, sa) < 1e-5
+    assert srv.counters()["batches"] == len(reqs)
+    srv.close()
+
+
+def test_serving_requests_arriving_while_busy_overlap_and_batch():
+    from paper_1106_5273_gb300 import Server
+    srv = Server(workers=2, batching=1, theta=THETA, ncrit=NCRIT)
+    # steady state: both classes have run once (a class's first batch runs alone)
+    for p_, w in ((8, workloads.plummer(5000, seed=70)), (4, workloads.uniform_ball(5000, seed=71))):
+        srv.wait(srv.submit(w["pos"], w["gamma"], p_, float(w["sigma"])), 120.0)
+    big = workloads.plummer(400000, seed=77)
+    t_big = srv.submit(big["pos"], big["gamma"], 8, float(big["sigma"]))
+    time.sleep(0.002)
+    small = [workloads.uniform_ball(20000, seed=80 + k) for k in range(6)]
+    ts = [srv.submit(w["pos"], w["gamma"], 4, float(w["sigma"])) for w in small]
+    rb, _, _ = srv.wait(t_big, 300.0)
+    rs = [srv.wait(t, 300.0)[0] for t in ts]
+    assert rb["status"] == 0 and all(r["status"] == 0 for r in rs)
+    # the small requests ran on the other worker while the big one was on the device
+    assert any(r["worker"] != rb["worker"] and r["t_start"] < rb["t_done"] for r in rs)
+    # and shared batches
+    assert max(r["batch_problems"] for r in rs) > 1
+    srv.close()
+
+
+def test_serving_memory_budget():
+    """2 GiB budget: 50k-particle requests are admitted a few at a time; a
+    2M-particle request cannot fit the budget on its own and is refused."""
+    from paper_1106_5273_gb300 import Server
+    budget = 2 << 30
+    srv = Server(workers=2, batching=1, theta=THETA, ncrit=NCRIT, hbm_budget_bytes=budget,
+                 max_batch_particles=100000)
+    ws = [workloads.uniform_ball(50000, seed=90 + k) for k in range(6)]
+    ts = [srv.submit(w["pos"], w["gamma"], 4, float(w["sigma"])) for w in ws]
+    huge = workloads.uniform_ball(2000000, seed=99)
+    th = srv.submit(huge["pos"], huge["gamma"], 4, float(huge["sigma"]))
+    rs = [srv.wait(t, 300.0)[0] for t in ts]
+    rh = srv.wait(th, 300.0)[0]
+    assert all(r["status"] == 0 for r in rs)
+    assert rh["status"] == -2  # FMM_E_NOMEM
+    c = srv.counters()
+    assert 0 < c["peak_bytes"] <= budget, c
+    srv.close()
+
+
+def test_serving_bad_requests():
+    from paper_1106_5273_gb300 import Server, FmmError
+    srv = Server(workers=1)
+    x = np.zeros((4, 3), np.float32)
+    for kw in (dict(p=0, sigma=0.1), dict(p=4, sigma=0.0), dict(p=17, sigma=0.1),
+               dict(p=4, sigma=0.1, periodic=True, box=(0, 0, 0, 0))):
+        with pytest.raises(FmmError):
+            srv.submit(x, x, **kw)
+    with pytest.raises(FmmError):
+        srv.wait(12345, 0.0)
+    srv.close()

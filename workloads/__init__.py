@@ -125,7 +125,17 @@ def uniform_ball(n, seed=BASE_SEED + 4):
                 sigma=np.float32(sigma), periodic=False, name="ball-%d" % n)
 
 
-def plummer(n, a=0.1, seed=BASE_SEED + 5):
+def plummer_sigma(n, a=0.1):
+    """Core width for a Plummer cloud of n blobs: 1.5 x the mean spacing inside
+    the half-mass radius r_h = a / sqrt(2^(2/3) - 1) (n/2 blobs there), so the
+    near field of the dense core stays a few thousand neighbours as for a
+    uniform cloud (a width from the spacing of the whole unit ball would put
+    most of the core inside 5 sigma of every core blob)."""
+    rh = a / math.sqrt(2.0 ** (2.0 / 3.0) - 1.0)
+    return 1.5 * (4.0 / 3.0 * math.pi * rh ** 3 / max(n / 2.0, 1.0)) ** (1.0 / 3.0)
+
+
+def plummer(n, a=0.1, seed=BASE_SEED + 5, sigma_rule="ball"):
     g = rng(seed)
     X = g.random(2 * n + 16)
     X = X[X < 0.999][:n]
@@ -137,7 +147,10 @@ def plummer(n, a=0.1, seed=BASE_SEED + 5):
     v /= np.linalg.norm(v, axis=1)[:, None]
     pos = v * r[:, None]
     gamma = g.standard_normal((n, 3))
-    sigma = 1.5 * (4.0 / 3.0 * math.pi / n) ** (1.0 / 3.0)
+    if sigma_rule == "halfmass":
+        sigma = plummer_sigma(n, a)
+    else:
+        sigma = 1.5 * (4.0 / 3.0 * math.pi / n) ** (1.0 / 3.0)
     return dict(pos=pos.astype(np.float32), gamma=gamma.astype(np.float32),
                 sigma=np.float32(sigma), periodic=False, name="plummer-%d" % n)
 
@@ -145,8 +158,9 @@ def plummer(n, a=0.1, seed=BASE_SEED + 5):
 def batch_specs(nprob=512, nmin=1e3, nmax=1e6, orders=(4, 8, 12), seed=BASE_SEED + 4):
     """Independent free-space problems for a batched evaluation: N log-uniform
     in [nmin, nmax], positions uniform in the unit ball or Plummer-clustered
-    (a = 0.1) with equal odds, Gaussian strengths, sigma = 1.5 (V_ball/N)^(1/3),
-    expansion order drawn from `orders`.  Returns specs; make_problem builds one."""
+    (a = 0.1) with equal odds, Gaussian strengths, sigma = 1.5 (V_ball/N)^(1/3)
+    for the ball and plummer_sigma(N) for the clusters, expansion order drawn
+    from `orders`.  Returns specs; make_problem builds one."""
     g = rng(seed)
     N = np.exp(g.uniform(math.log(nmin), math.log(nmax), nprob)).astype(np.int64)
     kind = g.integers(0, 2, nprob)
@@ -184,7 +198,7 @@ def make_problem(spec):
     if spec["kind"] == "ball":
         return uniform_ball(spec["n"], seed=spec["seed"])
     if spec["kind"] == "plummer":
-        return plummer(spec["n"], seed=spec["seed"])
+        return plummer(spec["n"], seed=spec["seed"], sigma_rule="halfmass")
     m = int(round(spec["n"] ** (1.0 / 3.0)))
     return random_spectrum(m, seed=spec["seed"])
 
