@@ -45,7 +45,7 @@ enum { FMM_OUT_VELOCITY = 1, FMM_OUT_STRETCHING = 2 };
 
 /* How M2L products are computed. */
 enum {
-  FMM_M2L_AUTO = 0,   /* tensor cores when p^2 <= 128, else SIMT FP32 */
+  FMM_M2L_AUTO = 0,   /* tensor cores (every p) */
   FMM_M2L_SIMT = 1,   /* FP32 CUDA-core GEMM per (target tile, translation) */
   FMM_M2L_TENSOR = 2  /* tcgen05 BF16x3 split products, FP32 accumulation */
 };

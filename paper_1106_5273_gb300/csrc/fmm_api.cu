@@ -181,7 +181,7 @@ int fmm_plan_create(const fmm_params* prm, int64_t n_max, fmm_plan* out) {
   p->n_max = n_max;
   p->P = prm->p * prm->p;
   p->Kpad = 128;
-  p->tc_ok = p->P <= 128 ? 1 : 0;  // tcgen05 M2L needs the P output rows within M = 128
+  p->tc_ok = 1;  // tcgen05 M2L: one CTA per 128 output rows (two for p > 11)
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
     return FMM_E_CUDA;

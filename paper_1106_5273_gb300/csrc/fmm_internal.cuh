@@ -41,7 +41,7 @@ struct fmm_plan_s {
   fmm_params prm;
   int64_t n_max = 0;
   int P = 0;      // p^2 real coefficients per potential
-  int Kpad = 0;   // P rounded up to a multiple of 16 (tensor-core K)
+  int Kpad = 0;   // unused (the BF16 layouts use 64 x m2l_kchunks(P))
   int device = 0;
   int timing = 0;
   int tc_ok = 0;  // tensor-core M2L usable for this p
@@ -80,7 +80,7 @@ struct fmm_plan_s {
   fmm::DBuf tile_cells;                                             // cell of each (tile, slot) position
   fmm::DBuf leaves;                                                 // leaf cell ids
   fmm::DBuf M, L;                                                   // [cells][3][P] FP32
-  fmm::DBuf Mbf;                                                    // [cells][2][3][Kpad] BF16 hi/lo
+  fmm::DBuf Mbf;                                                    // [cells][2][3][64 x K chunks] BF16 hi/lo
   // traversal
   fmm::DBuf fr0, fr1;                                 // frontier int4 (a,b,o,0)
   fmm::DBuf tcount, tmask, tscan0, tscan1, tscan2;    // per-item scratch
@@ -179,6 +179,8 @@ __host__ __device__ inline void m2l_key_decode(uint64_t key, int* delta, double 
 
 // K chunks of 64 coefficients (4 MMA K-steps of 16) covering P inputs.
 __host__ __device__ inline int m2l_kchunks(int P) { return ((P + 15) / 16 + 3) / 4; }
+// Blocks of 128 output rows (one MMA M) covering P outputs.
+__host__ __device__ inline int m2l_rowblocks(int P) { return (P + 127) / 128; }
 
 // Level / tile layout of the current tree, passed to kernels by value.
 struct LevelInfo {

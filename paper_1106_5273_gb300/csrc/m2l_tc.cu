@@ -2,14 +2,16 @@
 // with FP32 accumulation in tensor memory (Sec. 3.1 M2L, batched per
 // translation vector).
 //
-// A step applies one translation operator T (P x P, P = p^2 <= 128) to the
+// A step applies one translation operator T (P x P, P = p^2) to the
 // multipoles of the 64 source cells paired with a tile of 64 target cells:
 //   D[128 x 192] += T[128 x K] . B[K x 192],  B column (comp, slot) = M~ of
 // the slot's source for that potential component (zero if the slot has no
 // source under this translation).  T = T_hi + T_lo and B = B_hi + B_lo in
 // BF16; D accumulates T_hi B_hi + T_hi B_lo + T_lo B_hi (the lo.lo term is
 // below FP32 resolution of the sum).  D lives in TMEM for all steps of the
-// tile; each target local expansion is written once.
+// tile; each target local expansion is written once.  P > 128 output rows
+// take a second CTA per tile (blockIdx.y = block of 128 rows), which gathers
+// the same B and its own rows of T.
 //
 // Per stage (one step, one 64-wide K chunk): A (T hi/lo, pre-swizzled in
 // global memory in the 128B-swizzle K-major layout) arrives by two 1-D bulk
@@ -120,11 +122,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const int2* __restrict__ tile_range, LevelInfo li, const int* __restrict__ st_slot,
              const int* __restrict__ st_src, const __nv_bfloat16* __restrict__ Tbf,
-             const __nv_bfloat16* __restrict__ Mbf, int P, int nkc, int ksteps_last, const int* __restrict__ tcell,
-             float* __restrict__ L, int* __restrict__ flag) {
+             const __nv_bfloat16* __restrict__ Mbf, int P, int nkc, int ksteps_last, int kpad, int nrh,
+             const int* __restrict__ tcell, float* __restrict__ L, int* __restrict__ flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tile = blockIdx.x;
+  const int rh = blockIdx.y;  // block of 128 output rows
   const int2 rg = tile_range[tile];
   if (rg.y <= rg.x) return;  // no M2L for this tile: the whole CTA leaves before any barrier
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int src = st_src[(size_t)st * kTile + slot];
         v[q] = make_uint4(0u, 0u, 0u, 0u);
         if (src >= 0) {
-          const uint4* gp = reinterpret_cast<const uint4*>(Mbf + (((size_t)src * 2 + h) * 3 + comp) * 128 + kc * 64) + j;
+          const uint4* gp = reinterpret_cast<const uint4*>(Mbf + (((size_t)src * 2 + h) * 3 + comp) * kpad + kc * 64) + j;
           v[q] = __ldg(gp);
         }
         dst[q] = (int)(stage * kStageBytes + 2 * kABytes + h * kBBytes + n * 128 + ((j ^ (n & 7)) << 4));
@@ -198,8 +201,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(empty(stage), ph ^ 1u, abort)) return false;
       const int st = rg.x + it / nkc, kc = it % nkc;
       const size_t key = (size_t)st_slot[st];
-      const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * nkc + kc) * (128 * 64);
-      const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * nkc + kc) * (128 * 64);
+      const size_t chunk = (size_t)nrh * 128 * 64, row0 = (size_t)rh * 128 * 64;
+      const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * nkc + kc) * chunk + row0;
+      const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * nkc + kc) * chunk + row0;
       const uint32_t a0 = sbase + stage * kStageBytes;
       mbar_arrive_tx(fullA(stage), 2 * kABytes);
       bulk_g2s(a0, hi, kABytes, fullA(stage));
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (l + 1 < li.nlevels && li.tile_begin[l + 1] <= tile) ++l;
       const int first = li.level_begin[l] + (tile - li.tile_begin[l]) * kTile;
       const int ncell = min(kTile, li.level_begin[l + 1] - first);
-      const int r = warp * 32 + lane;
+      const int r = rh * 128 + warp * 32 + lane;  // output coefficient of this TMEM lane
 #pragma unroll 1
       for (int cb = 0; cb < kN / 16; ++cb) {
         float v[16];
@@ -302,7 +306,6 @@ __global__ void k_wait_selftest(long long spins, int arrive, int* status) {
 
 int m2l_tensor(fmm_plan p, cudaStream_t s) {
   if (p->n_steps == 0) return FMM_OK;
-  if (p->P > 128) return FMM_E_INVAL;
   LevelInfo li;
   li.nlevels = p->nlevels;
   for (int l = 0; l <= p->nlevels; ++l) {
@@ -314,11 +317,12 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   const int last = ksteps - 4 * (nkc - 1);
   const size_t sh = (size_t)kBarOff + 128 + 1024;
   FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  const int nrh = m2l_rowblocks(p->P);
   ++g_launches;
-  k_m2l_tc<<<(unsigned)p->ntiles, kThreads, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
-                                                      p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
-                                                      p->Mbf.as<__nv_bfloat16>(), p->P, nkc, last,
-                                                      p->tile_cells.as<int>(), p->L.as<float>(), p->flags.as<int>());
+  k_m2l_tc<<<dim3((unsigned)p->ntiles, (unsigned)nrh), kThreads, sh, s>>>(
+      p->tile_range.as<int2>(), li, p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
+      p->Mbf.as<__nv_bfloat16>(), p->P, nkc, last, 64 * nkc, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
+      p->flags.as<int>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -162,9 +162,10 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
     nu[r] = nu_d(n, m);
   }
   if (threadIdx.x < (unsigned)p) rp[threadIdx.x] = ldexp(1.0, delta * (int)threadIdx.x);
+  const int rows = 128 * m2l_rowblocks(P);  // output rows of the BF16 tiles
   if (nkc) {  // zero this slot's BF16 tiles (padding rows and columns stay zero)
-    uint4* z = reinterpret_cast<uint4*>(Tbf + (size_t)key_id * 2 * nkc * 128 * 64);
-    for (int i = threadIdx.x; i < 2 * nkc * 128 * 64 / 8; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    uint4* z = reinterpret_cast<uint4*>(Tbf + (size_t)key_id * 2 * nkc * rows * 64);
+    for (int i = threadIdx.x; i < 2 * nkc * rows * 64 / 8; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
@@ -182,16 +183,16 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
     double v;
     if (pi == 0) v = po == 0 ? s * (A.re + B.re) : s * (A.im + B.im);
     else v = po == 0 ? -s * (B.im - A.im) : s * (B.re - A.re);
-    T32[(size_t)key_id * P * P + e] = (float)v;
+    if (!nkc) T32[(size_t)key_id * P * P + e] = (float)v;  // FP32 copy for the SIMT path only
     if (nkc) {
-      // [key][hi/lo][nkc K chunks of 64][128 rows][64], 16-byte groups of a row
+      // [key][hi/lo][nkc K chunks of 64][rows][64], 16-byte groups of a row
       // stored in the 128-byte swizzle order (group j at j ^ (row & 7))
       __nv_bfloat16 hi = __double2bfloat16(v);
       __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
       const int kc = c >> 6, j = (c & 63) >> 3, el = c & 7;
       const size_t within = (size_t)r * 64 + (size_t)(((j ^ (r & 7)) << 3) + el);
-      Tbf[(((size_t)key_id * 2 + 0) * nkc + kc) * (128 * 64) + within] = hi;
-      Tbf[(((size_t)key_id * 2 + 1) * nkc + kc) * (128 * 64) + within] = lo;
+      Tbf[(((size_t)key_id * 2 + 0) * nkc + kc) * ((size_t)rows * 64) + within] = hi;
+      Tbf[(((size_t)key_id * 2 + 1) * nkc + kc) * ((size_t)rows * 64) + within] = lo;
     }
   }
 }
@@ -264,11 +265,16 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
   p->h_keys.resize(nk);
   FMM_CUDA_TRY(cudaMemcpyAsync(p->h_keys.data(), p->ukeys.ptr, nk * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   FMM_CUDA_TRY(cudaStreamSynchronize(s));
-  // BF16 tiles only for the tensor-core path (P <= 128 output rows; the
-  // plan's M2L mode does not change between evaluations)
+  // BF16 tiles only for the tensor-core path (the plan's M2L mode does not
+  // change between evaluations)
   const int tc = p->last_tc;
-  // bound the cache: start over when it would exceed 1 << 16 operators
-  if ((int64_t)p->tcache.size() + nk > (1 << 16)) p->tcache.clear();
+  // bound the cache: start over when this evaluation's new operators would
+  // take it past 1 << 16 (a cleared cache then holds exactly this evaluation's)
+  {
+    int64_t misses = 0;
+    for (int64_t i = 0; i < nk; ++i) misses += p->tcache.count(p->h_keys[i]) ? 0 : 1;
+    if ((int64_t)p->tcache.size() + misses > (1 << 16)) p->tcache.clear();
+  }
   p->h_map.resize(nk);
   std::vector<uint64_t> miss_keys;
   std::vector<int> miss_slots;
@@ -287,8 +293,10 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
   const int64_t need = (int64_t)p->tcache.size();
   if (need > p->tcache_cap) {
     int64_t cap = std::max<int64_t>(need, p->tcache_cap * 2);
-    FMM_TRY(p->T32.grow_copy((size_t)cap * P * P * sizeof(float), s));
-    if (tc) FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * m2l_kchunks(P) * 128 * 64 * sizeof(__nv_bfloat16), s));
+    if (!tc) FMM_TRY(p->T32.grow_copy((size_t)cap * P * P * sizeof(float), s));
+    if (tc)
+      FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * m2l_kchunks(P) * 128 * m2l_rowblocks(P) * 64 * sizeof(__nv_bfloat16),
+                               s));
     p->tcache_cap = cap;
   }
   if (!miss_keys.empty()) {

@@ -116,19 +116,20 @@ __global__ void __launch_bounds__(128) k_m2m(int lb, const int* __restrict__ chi
   }
 }
 
-// Mbf[cell][hi/lo][comp][128], zero beyond P.
-__global__ void k_split_bf16(const float* __restrict__ M, int64_t ncell, int P, __nv_bfloat16* __restrict__ Mbf) {
-  int64_t total = ncell * 3 * 128;
+// Mbf[cell][hi/lo][comp][kpad], zero beyond P (kpad = 64 x K chunks).
+__global__ void k_split_bf16(const float* __restrict__ M, int64_t ncell, int P, int kpad,
+                             __nv_bfloat16* __restrict__ Mbf) {
+  int64_t total = ncell * 3 * kpad;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int k = (int)(i % 128);
-    int64_t cc = i / 128;  // cell*3 + comp
+    int k = (int)(i % kpad);
+    int64_t cc = i / kpad;  // cell*3 + comp
     int64_t cell = cc / 3;
     int comp = (int)(cc % 3);
     float v = k < P ? M[cc * P + k] : 0.f;
     __nv_bfloat16 hi = __float2bfloat16(v);
     __nv_bfloat16 lo = __float2bfloat16(v - __bfloat162float(hi));
-    Mbf[((cell * 2 + 0) * 3 + comp) * 128 + k] = hi;
-    Mbf[((cell * 2 + 1) * 3 + comp) * 128 + k] = lo;
+    Mbf[((cell * 2 + 0) * 3 + comp) * kpad + k] = hi;
+    Mbf[((cell * 2 + 1) * 3 + comp) * kpad + k] = lo;
   }
 }
 
@@ -157,9 +158,10 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
   }
   FMM_CUDA_TRY(cudaGetLastError());
   if (p->last_tc) {
-    FMM_TRY(p->Mbf.ensure((size_t)nc * 2 * 3 * 128 * sizeof(__nv_bfloat16)));
+    const int kpad = 64 * m2l_kchunks(P);
+    FMM_TRY(p->Mbf.ensure((size_t)nc * 2 * 3 * kpad * sizeof(__nv_bfloat16)));
     ++g_launches;
-    k_split_bf16<<<2048, 256, 0, s>>>(p->M.as<float>(), nc, P, p->Mbf.as<__nv_bfloat16>());
+    k_split_bf16<<<2048, 256, 0, s>>>(p->M.as<float>(), nc, P, kpad, p->Mbf.as<__nv_bfloat16>());
     FMM_CUDA_TRY(cudaGetLastError());
   }
   return FMM_OK;
