@@ -411,6 +411,279 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
   }
 }
 
+// ---- Packed form: the two targets of a lane as float2 lanes of the FP32x2
+// instructions (fma/mul/add .f32x2).  The FMA pipe does the same work per
+// clock either way; the packed form halves the issue slots per pair, which
+// is what bounds the scalar kernel.  Every element sees the same operations in
+// the same order as pair_acc_rel (subtractions as additions of staged
+// negated values, 1 - qF as an FMA with the negated fit), so each element is
+// rounded exactly as in the scalar form.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// SigK with every constant duplicated into both lanes.
+struct SigK2 {
+  float2 kq, kxc_n, ky, kc, ku, is3, is5;  // kxc_n = -sqrt(2/pi)/sigma
+};
+
+__device__ __forceinline__ SigK2 make_sigk2(const SigK& K) {
+  SigK2 k;
+  k.kq = dup2(K.kq);
+  k.kxc_n = dup2(-K.kxc);
+  k.ky = dup2(K.ky);
+  k.kc = dup2(K.kc);
+  k.ku = dup2(K.ku);
+  k.is3 = dup2(K.is3);
+  k.is5 = dup2(K.is5);
+  return k;
+}
+
+struct AccR2 {
+  float2 ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz;
+};
+
+// S and T of two pairs (see pair_ST).
+template <int MODE>
+__device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, float2& T) {
+  const float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+  const float2 rinv2 = mul2(rinv, rinv);
+  if (MODE == kFar) {
+    S = mul2(rinv2, rinv);
+    T = mul2(mul2(dup2(-3.f), S), rinv2);
+    return;
+  }
+  const float2 qa = mul2(r2, K.kq);
+  const float2 q = make_float2(ex2_approx(qa.x), ex2_approx(qa.y));
+  const float2 r = mul2(r2, rinv);
+  const float2 y = mul2(rinv, K.ky);
+  // Fn = -(fit(y) + r kxc); g = 1 + q Fn
+  float2 Fn = fma2(fma2(fma2(dup2(-kE3), y, dup2(-kE2)), y, dup2(-kE1)), y, dup2(-kE0));
+  Fn = fma2(r, K.kxc_n, Fn);
+  const float2 g = fma2(q, Fn, dup2(1.f));
+  S = mul2(mul2(g, rinv2), rinv);
+  T = mul2(fma2(K.kc, q, mul2(dup2(-3.f), S)), rinv2);
+  if (MODE == kNear) {
+    const float2 u = mul2(r2, K.ku);
+    if (u.x < 2.f || u.y < 2.f) {
+      float2 sS = dup2(cSer[kSerTerms - 1]), sT = dup2((float)(kSerTerms - 1) * cSer[kSerTerms - 1]);
+#pragma unroll
+      for (int k = kSerTerms - 2; k >= 0; --k) {
+        sS = fma2(sS, u, dup2(cSer[k]));
+        if (k >= 1) sT = fma2(sT, u, dup2((float)k * cSer[k]));
+      }
+      const float2 Ss = mul2(sS, K.is3), Ts = mul2(sT, K.is5);
+      if (u.x < 2.f) {
+        S.x = Ss.x;
+        T.x = Ts.x;
+      }
+      if (u.y < 2.f) {
+        S.y = Ss.y;
+        T.y = Ts.y;
+      }
+    }
+  }
+}
+
+template <int MODE, bool SELF>
+__device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
+                                             const float2* s4, int cnt, float2 tx, float2 ty, float2 tz,
+                                             float2 gix, float2 giy, float2 giz, int self_lo, int self_hi,
+                                             const SigK2& K, AccR2& a) {
+#pragma unroll 4
+  for (int j = 0; j < cnt; ++j) {
+    const float4 v0 = s0[j], v1 = s1[j], v2 = s2[j], v3 = s3[j];
+    const float2 v4 = s4[j];
+    const float2 dx = add2(tx, make_float2(v0.x, v0.y));
+    const float2 dy = add2(ty, make_float2(v0.z, v0.w));
+    const float2 dz = add2(tz, make_float2(v1.x, v1.y));
+    const float2 gjx = make_float2(v1.z, v1.w), gjy = make_float2(v2.x, v2.y), gjz = make_float2(v2.z, v2.w);
+    const float2 kjx = make_float2(v3.x, v3.y), kjy = make_float2(v3.z, v3.w), kjz = v4;
+    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    float2 S, T;
+    pair_ST2<MODE>(r2, K, S, T);
+    float2 td = mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz))));
+    if (SELF) {
+      if (j == self_lo) {
+        S.x = 0.f;
+        td.x = 0.f;
+      }
+      if (j == self_hi) {
+        S.y = 0.f;
+        td.y = 0.f;
+      }
+    }
+    a.ax = fma2(S, gjx, a.ax);
+    a.ay = fma2(S, gjy, a.ay);
+    a.az = fma2(S, gjz, a.az);
+    a.bx = fma2(S, kjx, a.bx);
+    a.by = fma2(S, kjy, a.by);
+    a.bz = fma2(S, kjz, a.bz);
+    a.cx = fma2(td, gjx, a.cx);
+    a.cy = fma2(td, gjy, a.cy);
+    a.cz = fma2(td, gjz, a.cz);
+    a.dx = fma2(td, kjx, a.dx);
+    a.dy = fma2(td, kjy, a.dy);
+    a.dz = fma2(td, kjz, a.dz);
+  }
+}
+
+// k_p2p for a uniform core width and two targets per lane, in the packed
+// form.  Same lists, classes, staging order and output as k_p2p<false, 2, SEG>;
+// the staged source holds its negated coordinates and every value twice.
+template <bool SEG>
+__global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, const int2* __restrict__ off,
+                                               const int2* __restrict__ list, const int* __restrict__ begin,
+                                               const int* __restrict__ end, const float4* __restrict__ cf,
+                                               const float4* __restrict__ A, const float4* __restrict__ B,
+                                               const float* __restrict__ far_u, const float* __restrict__ far_s,
+                                               const uint32_t* __restrict__ sidx, float blen, float smax,
+                                               float margin0, SigK K0, const double* __restrict__ dip,
+                                               const int* __restrict__ cseg, const SegP2P* __restrict__ sp,
+                                               float* __restrict__ vel, float* __restrict__ dg) {
+  constexpr int CH = 64;
+  __shared__ float4 s0[2][CH], s1[2][CH], s2[2][CH], s3[2][CH];
+  __shared__ float2 s4[2][CH];
+  const int lane = threadIdx.x;
+  const int leaf = leaves[blockIdx.x];
+  const int tb = begin[leaf], te = end[leaf];
+  const int2 rg = off[blockIdx.x];
+  const float4 lc = cf[leaf];
+  float dux = dip ? (float)dip[0] : 0.f, duy = dip ? (float)dip[1] : 0.f, duz = dip ? (float)dip[2] : 0.f;
+  if (SEG) {
+    const SegP2P q = sp[cseg[leaf]];
+    K0 = make_sigk(q.sigma);
+    blen = q.blen;
+    smax = q.smax;
+    margin0 = q.margin;
+    dux = q.dip[0];
+    duy = q.dip[1];
+    duz = q.dip[2];
+  }
+  const SigK2 K = make_sigk2(K0);
+  float4 ra[2], rb[2];
+  auto stage = [&](int bb, int cnt, int img) {
+    const float shx = -(float)(img / 9 - 1) * blen, shy = -(float)((img / 3) % 3 - 1) * blen,
+                shz = -(float)(img % 3 - 1) * blen;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int j = lane + 32 * q;
+      if (j < cnt) {
+        const float X = (ra[q].x - lc.x) - shx, Y = (ra[q].y - lc.y) - shy, Z = (ra[q].z - lc.z) - shz;
+        const float4 g = rb[q];
+        const float kx = g.y * Z - g.z * Y, ky = g.z * X - g.x * Z, kz = g.x * Y - g.y * X;
+        s0[bb][j] = make_float4(-X, -X, -Y, -Y);
+        s1[bb][j] = make_float4(-Z, -Z, g.x, g.x);
+        s2[bb][j] = make_float4(g.y, g.y, g.z, g.z);
+        s3[bb][j] = make_float4(kx, kx, ky, ky);
+        s4[bb][j] = make_float2(kz, kz);
+      }
+    }
+  };
+  for (int t0 = tb; t0 < te; t0 += CH) {
+    float xs[2], ys[2], zs[2], gxs[2], gys[2], gzs[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = t0 + lane + 32 * q;
+      const float4 xi = i < te ? A[i] : lc;
+      const float4 gi = i < te ? B[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      xs[q] = xi.x - lc.x;
+      ys[q] = xi.y - lc.y;
+      zs[q] = xi.z - lc.z;
+      gxs[q] = gi.x;
+      gys[q] = gi.y;
+      gzs[q] = gi.z;
+    }
+    const float2 tx = make_float2(xs[0], xs[1]), ty = make_float2(ys[0], ys[1]), tz = make_float2(zs[0], zs[1]);
+    const float2 gix = make_float2(gxs[0], gxs[1]), giy = make_float2(gys[0], gys[1]),
+                 giz = make_float2(gzs[0], gzs[1]);
+    AccR2 a;
+    a.ax = a.ay = a.az = a.bx = a.by = a.bz = a.cx = a.cy = a.cz = a.dx = a.dy = a.dz = dup2(0.f);
+    int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0;
+    int buf = 0;
+    if (cur_e < rg.y) {
+      cur_cnt = min(CH, end[list[cur_e].x] - cur_c0);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int j = lane + 32 * q;
+        if (j < cur_cnt) {
+          ra[q] = A[cur_c0 + j];
+          rb[q] = B[cur_c0 + j];
+        }
+      }
+      stage(0, cur_cnt, list[cur_e].y);
+    }
+    __syncwarp();
+    while (cur_e < rg.y) {
+      int ne = cur_e, nc0 = cur_c0 + CH;
+      if (nc0 >= end[list[ne].x]) {
+        ++ne;
+        nc0 = ne < rg.y ? begin[list[ne].x] : 0;
+      }
+      int ncnt = 0;
+      if (ne < rg.y) {
+        ncnt = min(CH, end[list[ne].x] - nc0);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int j = lane + 32 * q;
+          if (j < ncnt) {
+            ra[q] = A[nc0 + j];
+            rb[q] = B[nc0 + j];
+          }
+        }
+      }
+      const int2 ent = list[cur_e];
+      const bool self = (ent.x == leaf) && ent.y == kImageZero;
+      const int mode = entry_mode_f(cf, leaf, ent.x, ent.y, blen, smax, margin0);
+      const float4* c0 = s0[buf];
+      const float4* c1 = s1[buf];
+      const float4* c2 = s2[buf];
+      const float4* c3 = s3[buf];
+      const float2* c4 = s4[buf];
+      if (self) {
+        const int slo = (t0 + lane) - cur_c0, shi = (t0 + lane + 32) - cur_c0;
+        run_chunk_x2<kNear, true>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, slo, shi, K, a);
+      } else if (mode == kFar) {
+        run_chunk_x2<kFar, false>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+      } else if (mode == kMid) {
+        run_chunk_x2<kMid, false>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+      } else {
+        run_chunk_x2<kNear, false>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+      }
+      __syncwarp();
+      buf ^= 1;
+      if (ne < rg.y) stage(buf, ncnt, list[ne].y);
+      __syncwarp();
+      cur_e = ne;
+      cur_c0 = nc0;
+      cur_cnt = ncnt;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = t0 + lane + 32 * q;
+      if (i >= te) continue;
+      const float ax = q ? a.ax.y : a.ax.x, ay = q ? a.ay.y : a.ay.x, az = q ? a.az.y : a.az.x;
+      const float bx = q ? a.bx.y : a.bx.x, by = q ? a.by.y : a.by.x, bz = q ? a.bz.y : a.bz.x;
+      const float cx = q ? a.cx.y : a.cx.x, cy = q ? a.cy.y : a.cy.x, cz = q ? a.cz.y : a.cz.x;
+      const float ex = q ? a.dx.y : a.dx.x, ey = q ? a.dy.y : a.dy.x, ez = q ? a.dz.y : a.dz.x;
+      const float X = xs[q], Y = ys[q], Z = zs[q];
+      const uint32_t o = sidx[i];
+      if (vel) {  // u = A x X_i - B
+        vel[3 * o] = far_u[3 * i] + kInv4Pi * ((ay * Z - az * Y) - bx) + dux;
+        vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * ((az * X - ax * Z) - by) + duy;
+        vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * ((ax * Y - ay * X) - bz) + duz;
+      }
+      if (dg) {  // s = A x gamma_i + C x X_i - D
+        const float gx = gxs[q], gy = gys[q], gz = gzs[q];
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((ay * gz - az * gy) + (cy * Z - cz * Y) - ex);
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((az * gx - ax * gz) + (cz * X - cx * Z) - ey);
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((ax * gy - ay * gx) + (cx * Y - cy * X) - ez);
+      }
+    }
+  }
+}
+
 // All pairs of one array, free space, self pair skipped (near class throughout).
 template <bool PS>
 __global__ void __launch_bounds__(kMaxBlock) k_direct(int64_t n, const float* __restrict__ pos,
@@ -597,10 +870,22 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
 #define FMM_P2P_LAUNCH(PS_, TPT_, SEG_)                                                                         \
   k_p2p<PS_, TPT_, SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, \
                                           margin0, K0, dip, cseg, sp, vel, dg)
+  // the packed kernel stages 9 KB per warp: ask for the largest shared-memory carveout
+  static bool carveout_set = false;
+  if (!carveout_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute((const void*)k_p2p_x2<false>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    FMM_CUDA_TRY(cudaFuncSetAttribute((const void*)k_p2p_x2<true>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    carveout_set = true;
+  }
+#define FMM_P2P_X2_LAUNCH(SEG_)                                                                                \
+  k_p2p_x2<SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, \
+                                  K0, dip, cseg, sp, vel, dg)
   if (cseg) {
     if (two) {
       if (ps) FMM_P2P_LAUNCH(true, 2, true);
-      else FMM_P2P_LAUNCH(false, 2, true);
+      else FMM_P2P_X2_LAUNCH(true);
     } else {
       if (ps) FMM_P2P_LAUNCH(true, 1, true);
       else FMM_P2P_LAUNCH(false, 1, true);
@@ -608,13 +893,14 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   } else {
     if (two) {
       if (ps) FMM_P2P_LAUNCH(true, 2, false);
-      else FMM_P2P_LAUNCH(false, 2, false);
+      else FMM_P2P_X2_LAUNCH(false);
     } else {
       if (ps) FMM_P2P_LAUNCH(true, 1, false);
       else FMM_P2P_LAUNCH(false, 1, false);
     }
   }
 #undef FMM_P2P_LAUNCH
+#undef FMM_P2P_X2_LAUNCH
   FMM_CUDA_TRY(cudaGetLastError());
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));

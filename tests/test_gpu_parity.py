@@ -165,6 +165,29 @@ def test_fmm_per_particle_sigma_and_plummer():
     assert rel_l2(u, ud) < 2e-4 and rel_l2(s, sd) < 1e-3
 
 
+@pytest.mark.parametrize("case", ["taylor-green-16", "plummer-free"])
+def test_packed_p2p_bitwise_equals_scalar_kernel(case):
+    """Two targets per lane (ncrit > 32) with one core width run the packed
+    FP32x2 pair kernel; the same problem with a per-particle sigma array of
+    equal values runs the scalar kernel.  Each packed element takes the scalar
+    form's operations in the same order, so the outputs must agree bit for
+    bit (near, mid and far classes, the series branch and the self pair)."""
+    if case == "taylor-green-16":
+        w = workloads.taylor_green(16)
+        p, theta, ncrit = 8, 0.4, 64
+    else:
+        w = workloads.plummer(5000)
+        w["sigma"] = np.float32(workloads.plummer_sigma(5000))
+        p, theta, ncrit = 8, 0.5, 48
+    n = w["pos"].shape[0]
+    sig = np.full(n, np.float32(w["sigma"]), np.float32)
+    plan1, u1, s1 = run_fmm(w, p, theta, ncrit, m2l_mode=1)
+    plan2, u2, s2 = run_fmm(w, p, theta, ncrit, m2l_mode=1, sigma_arr=sig)
+    st = plan1.stats()
+    assert st.p2p_pairs_near > 0 and st.p2p_pairs_mid + st.p2p_pairs_far > 0
+    assert np.array_equal(u1, u2) and np.array_equal(s1, s2)
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 257])
 def test_edge_sizes(n):
     from oracle import direct as od
