@@ -29,11 +29,16 @@ METRIC = "FMM Biot-Savart+stretching particles/s at rel-L2<=1e-4"
 UNIT = "particles/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# FP32 flops per P2P pair counted from the CUDA source of pair_acc (FMA = 2),
-# per pair class: difference 3, r^2 5, S and T (near 21 / mid 20 / far 4),
-# gamma_j x d 9, u 6, sum S gamma_j 6, T (gamma_i . d) 6, s 6; plus MUFU ops
-# (rsqrt and ex2; far pairs rsqrt only).
-P2P_FLOPS = {"near": 62, "mid": 61, "far": 45}
+# FP32 flops per P2P pair counted from the CUDA source of the packed pair
+# kernel (per element; FMA = 2): difference 3, r^2 5, S and T (near 21 / mid
+# 20 / far 4: 1/r^2, 1/r^3, ex2 argument, degree-4 Horner in 1/r, S, T; near
+# adds the series test), T (gamma_i . d) 6, the four accumulated sums 24; plus
+# MUFU ops (rsqrt and ex2; far pairs rsqrt only).  The near-class series
+# branch (rho^2 < 2) is not counted.
+P2P_FLOPS = {"near": 57, "mid": 56, "far": 42}
+# FP32-pipe instructions per pair (FMA, MUL and ADD alike), for the pipe-slot
+# utilisation reported beside the flop rate.
+P2P_SLOTS = {"near": 35, "mid": 34, "far": 26}
 
 
 def parse():
@@ -465,6 +470,8 @@ def main():
     flops = (P2P_FLOPS["near"] * st.p2p_pairs_near + P2P_FLOPS["mid"] * st.p2p_pairs_mid
              + P2P_FLOPS["far"] * st.p2p_pairs_far)
     achieved = flops / p2p_t / 1e12
+    slots = (P2P_SLOTS["near"] * st.p2p_pairs_near + P2P_SLOTS["mid"] * st.p2p_pairs_mid
+             + P2P_SLOTS["far"] * st.p2p_pairs_far)
     clk_mhz = 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
     traffic = None
@@ -496,6 +503,7 @@ def main():
                          "pairs_by_class": {"near": st.p2p_pairs_near, "mid": st.p2p_pairs_mid,
                                             "far": st.p2p_pairs_far},
                          "ms_per_launch": p2p_t * 1e3,
+                         "fp32_pipe_slot_frac": slots / p2p_t / (SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6),
                          "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
             "paper_convention_tflops": 174 * pairs / p2p_t / 1e12,
             "phases_ms": {k: getattr(st, k) for k in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",

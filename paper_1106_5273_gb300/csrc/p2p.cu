@@ -3,10 +3,13 @@
 //
 // Per pair (d = x_i - x_j, r = |d|, rho = r/sigma_j, x = rho/sqrt2, c = sqrt(2/pi)):
 //   q = exp(-x^2)                       (one ex2)
-//   g = 1 - q (erfcx(x) + 2x/sqrt(pi))  (Eq. 2; erfcx by a degree-5 fit in 1/x,
-//                                         gen_cutoff_fit.py; rho^2 < 2 uses the
-//                                         Taylor series of g/rho^3 instead)
-//   S = g / r^3,  T = (c q / sigma^3 - 3 S) / r^2 = S'(r)/r
+//   g = 1 - q (erfcx(x) + 2x/sqrt(pi))  (Eq. 2; erfcx by a degree-3 fit in
+//                                         y = 1/x = sqrt2 sigma / r, gen_cutoff_fit.py;
+//                                         rho^2 < 2 uses the Taylor series of g/rho^3)
+//   S = g / r^3 = 1/r^3 - q H / r^2 with H = (erfcx fit + 2x/sqrt(pi)) / r, i.e.
+//       H = sqrt(2/pi)/sigma + e_0/r + e_1/r^2 + e_2/r^3 + e_3/r^4,  e_k = c_k (sqrt2 sigma)^k
+//       (one Horner polynomial in 1/r: 2x/sqrt(pi) / r is the constant term)
+//   T = (c q / sigma^3 - 3 S) / r^2 = S'(r)/r
 //   u_i += S (gamma_j x d)                                            (Eq. 1)
 //   s_i += S (gamma_j x gamma_i) + T (gamma_i . d)(gamma_j x d)       (Eq. 3)
 // The gamma_j x gamma_i part is summed as (sum_j S gamma_j) x gamma_i.  The
@@ -60,29 +63,31 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
-// Constants of one core width sigma.
+// Constants of one core width sigma.  The polynomial H is stored negated
+// (hn = -H) so that S = 1/r^3 + q (hn / r^2) is one FMA.
 struct SigK {
   float kq;   // -log2(e) / (2 sigma^2)
-  float kxc;  // sqrt(2/pi) / sigma   (2x/sqrt(pi) = r kxc)
-  float ky;   // sqrt2 sigma          (1/x = ky / r)
   float kc;   // sqrt(2/pi) / sigma^3
   float ku;   // 1 / sigma^2
   float is3;  // 1 / sigma^3
   float is5;  // 2 / sigma^5
-  float pad;
+  float hn0;  // -sqrt(2/pi) / sigma          (constant term of -H)
+  float hn1, hn2, hn3, hn4;  // -e_0 .. -e_3,  e_k = c_k (sqrt2 sigma)^k
 };
 
 __host__ __device__ inline SigK make_sigk(float sigma) {
   SigK k;
-  double s = (double)sigma;
+  const double s = (double)sigma, ky = 1.4142135623730951 * s;
   k.kq = (float)(-1.4426950408889634 / (2.0 * s * s));
-  k.kxc = (float)(0.79788456080286535588 / s);
-  k.ky = (float)(1.4142135623730951 * s);
   k.kc = (float)(0.79788456080286535588 / (s * s * s));
   k.ku = (float)(1.0 / (s * s));
   k.is3 = (float)(1.0 / (s * s * s));
   k.is5 = (float)(2.0 / (s * s * s * s * s));
-  k.pad = 0.f;
+  k.hn0 = (float)(-0.79788456080286535588 / s);
+  k.hn1 = (float)(-(double)kE0);
+  k.hn2 = (float)(-(double)kE1 * ky);
+  k.hn3 = (float)(-(double)kE2 * ky * ky);
+  k.hn4 = (float)(-(double)kE3 * ky * ky * ky);
   return k;
 }
 
@@ -96,15 +101,12 @@ __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float
     T = -3.f * S * rinv2;
     return;
   }
+  const float rinv3 = rinv2 * rinv;
   const float q = ex2_approx(r2 * K.kq);
-  const float r = r2 * rinv;
-  // y = 1/x; beyond the fit range (x > 4.6) exp(-x^2) < 8e-10 multiplies a
-  // bounded cubic, so g = 1 to FP32 precision without clamping y
-  const float y = rinv * K.ky;
-  float F = fmaf(fmaf(fmaf(kE3, y, kE2), y, kE1), y, kE0);
-  F = fmaf(r, K.kxc, F);
-  const float g = fmaf(-q, F, 1.f);
-  S = g * rinv2 * rinv;
+  // beyond the fit range (x > 4.6) exp(-x^2) < 8e-10 multiplies a bounded
+  // polynomial, so g = 1 to FP32 precision without clamping
+  const float hn = fmaf(fmaf(fmaf(fmaf(K.hn4, rinv, K.hn3), rinv, K.hn2), rinv, K.hn1), rinv, K.hn0);
+  S = fmaf(q, rinv2 * hn, rinv3);
   T = fmaf(K.kc, q, -3.f * S) * rinv2;
   if (MODE == kNear) {
     const float u = r2 * K.ku;
@@ -416,8 +418,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
 // clock either way; the packed form halves the issue slots per pair, which
 // is what bounds the scalar kernel.  Every element sees the same operations in
 // the same order as pair_acc_rel (subtractions as additions of staged
-// negated values, 1 - qF as an FMA with the negated fit), so each element is
-// rounded exactly as in the scalar form.
+// negated values), so each element is rounded exactly as in the scalar form.
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -425,18 +426,21 @@ __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 // SigK with every constant duplicated into both lanes.
 struct SigK2 {
-  float2 kq, kxc_n, ky, kc, ku, is3, is5;  // kxc_n = -sqrt(2/pi)/sigma
+  float2 kq, kc, ku, is3, is5, hn0, hn1, hn2, hn3, hn4;
 };
 
 __device__ __forceinline__ SigK2 make_sigk2(const SigK& K) {
   SigK2 k;
   k.kq = dup2(K.kq);
-  k.kxc_n = dup2(-K.kxc);
-  k.ky = dup2(K.ky);
   k.kc = dup2(K.kc);
   k.ku = dup2(K.ku);
   k.is3 = dup2(K.is3);
   k.is5 = dup2(K.is5);
+  k.hn0 = dup2(K.hn0);
+  k.hn1 = dup2(K.hn1);
+  k.hn2 = dup2(K.hn2);
+  k.hn3 = dup2(K.hn3);
+  k.hn4 = dup2(K.hn4);
   return k;
 }
 
@@ -454,15 +458,11 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
     T = mul2(mul2(dup2(-3.f), S), rinv2);
     return;
   }
+  const float2 rinv3 = mul2(rinv2, rinv);
   const float2 qa = mul2(r2, K.kq);
   const float2 q = make_float2(ex2_approx(qa.x), ex2_approx(qa.y));
-  const float2 r = mul2(r2, rinv);
-  const float2 y = mul2(rinv, K.ky);
-  // Fn = -(fit(y) + r kxc); g = 1 + q Fn
-  float2 Fn = fma2(fma2(fma2(dup2(-kE3), y, dup2(-kE2)), y, dup2(-kE1)), y, dup2(-kE0));
-  Fn = fma2(r, K.kxc_n, Fn);
-  const float2 g = fma2(q, Fn, dup2(1.f));
-  S = mul2(mul2(g, rinv2), rinv);
+  const float2 hn = fma2(fma2(fma2(fma2(K.hn4, rinv, K.hn3), rinv, K.hn2), rinv, K.hn1), rinv, K.hn0);
+  S = fma2(q, mul2(rinv2, hn), rinv3);
   T = mul2(fma2(K.kc, q, mul2(dup2(-3.f), S)), rinv2);
   if (MODE == kNear) {
     const float2 u = mul2(r2, K.ku);
