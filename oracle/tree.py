@@ -17,8 +17,10 @@ Readings taken where the paper is silent or ambiguous:
     the singular kernel, |X_A - X_B| - (R_A + R_B) >= k_sigma sigma_max.  The
     MAC is tested before the leaf test; two leaves that fail it do P2P; any
     other pair is pushed.
-  * Algorithm 1 splits the cell with the larger radius (B on a tie); when that
-    cell is a leaf the other one is split.
+  * Algorithm 1 splits the larger cell, read as the larger cube (the coarser
+    level; the target A when both cubes are equal); when that cell is a leaf
+    the other one is split.  (Comparing tight radii instead would let the
+    rounding of the inputs decide between cells of equal cubes.)
   * Periodic: the traversal starts from (root, root + o L) for the 27 shifts
     o in {-1,0,1}^3 (targets stay in the original cube).
 All FP64 expressions are written in a fixed order with no fused operations so
@@ -170,6 +172,7 @@ def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False):
     sigma_max = float(sigma_max)
     C = tree.center
     R = tree.radius
+    lev = tree.level
     leaf = tree.nchild == 0
     p2p, m2l, stack = [], [], []
     if len(tree.begin) == 0:
@@ -191,7 +194,7 @@ def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False):
         interact(0, 0, o)
     while stack:
         a, b, o = stack.pop()
-        split_a = R[a] > R[b]
+        split_a = lev[a] <= lev[b]
         if split_a and leaf[a]:
             split_a = False
         elif (not split_a) and leaf[b]:

@@ -1,7 +1,8 @@
 // Dual-tree traversal (Sec. 3.3, Algorithms 1-2) and list grouping.
 //
-// Algorithm 1 pops a pair (A, B), splits the cell with the larger radius
-// (B on a tie; the other one when that cell is a leaf) and calls Algorithm 2
+// Algorithm 1 pops a pair (A, B), splits the larger cell -- the larger cube,
+// i.e. the coarser level (the target A when both are equal; the other one when
+// that cell is a leaf) -- and calls Algorithm 2
 // on every child pair: M2L if the FMM MAC holds (R_A + R_B < theta |X_A-X_B|)
 // and the pair is at least k_sigma sigma_max apart (the far field uses the
 // singular kernel), else P2P if both are leaves, else push.  Here the stack
@@ -27,6 +28,7 @@ struct TravArgs {
   const float4* cf;  // FP32 copies of centre and radius
   const int* nchild;
   const int* child;
+  const int* level;
   const int* cseg;    // batch: problem of each cell (nullptr: one problem, the scalars below)
   const SegMac* sm;   // batch: per-problem shift and MAC constants
   double theta, ksig, smax, blen;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int n
 }
 
 __device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, int& c0, int& nc) {
-  split_a = t.radius[a] > t.radius[b];
+  split_a = t.level[a] <= t.level[b];
   if (split_a && t.nchild[a] == 0) split_a = false;
   else if (!split_a && t.nchild[b] == 0) split_a = true;
   int s = split_a ? a : b;
@@ -446,6 +448,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   ta.cf = p->c_cf.as<float4>();
   ta.nchild = p->c_nchild.as<int>();
   ta.child = p->c_child.as<int>();
+  ta.level = p->c_level.as<int>();
   ta.cseg = nullptr;
   ta.sm = nullptr;
   ta.theta = (double)p->prm.theta;
