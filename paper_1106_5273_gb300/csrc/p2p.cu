@@ -18,10 +18,11 @@
 //
 // One warp per target leaf, two target particles per lane (one when ncrit <=
 // 32); the source leaves of the leaf's list are staged through shared memory
-// in double-buffered chunks.  Each (source leaf, image) entry is classified by
-// a lower bound on its pair distances: the singular kernel where g = 1 to FP32
-// precision (rho >= 6.5), the cutoff without the series test (rho^2 >= 2), or
-// the full form.
+// in double-buffered chunks.  Each staged source is classified by a lower
+// bound on its distance to every target of the leaf: the singular kernel where
+// g = 1 to FP32 precision (rho >= 6.5), the cutoff without the series test
+// (rho^2 >= 2), or the full form; a chunk is staged grouped by class, so each
+// group runs its own branch-free loop.
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -187,9 +188,9 @@ struct TgtR {
 
 template <bool PS, int MODE, bool SELF, int TPT>
 __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
-                                              int cnt, TgtR<TPT>& t, const SigK& K0) {
+                                              int jb, int je, TgtR<TPT>& t, const SigK& K0) {
 #pragma unroll 4
-  for (int j = 0; j < cnt; ++j) {
+  for (int j = jb; j < je; ++j) {
     const float4 xj = sA[j];
     const float4 gj = sB[j];
     const float4 kj = sC[j];
@@ -202,30 +203,77 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
   }
 }
 
+// The groups of a staged chunk: sources [0, nf) far, [nf, nf + nm) mid, the
+// rest near; the self entry (not grouped) runs the near form with the self
+// pair skipped.
 template <bool PS, int TPT>
-__device__ __forceinline__ void dispatch_rel(int mode, bool self, const float4* sA, const float4* sB, const float4* sC,
-                                             const SigK* sK, int cnt, TgtR<TPT>& t, const SigK& K0) {
-  if (self) run_chunk_rel<PS, kNear, true, TPT>(sA, sB, sC, sK, cnt, t, K0);
-  else if (mode == kFar) run_chunk_rel<PS, kFar, false, TPT>(sA, sB, sC, sK, cnt, t, K0);
-  else if (mode == kMid) run_chunk_rel<PS, kMid, false, TPT>(sA, sB, sC, sK, cnt, t, K0);
-  else run_chunk_rel<PS, kNear, false, TPT>(sA, sB, sC, sK, cnt, t, K0);
+__device__ __forceinline__ void dispatch_rel(bool self, int nf, int nm, const float4* sA, const float4* sB,
+                                             const float4* sC, const SigK* sK, int cnt, TgtR<TPT>& t,
+                                             const SigK& K0) {
+  if (self) {
+    run_chunk_rel<PS, kNear, true, TPT>(sA, sB, sC, sK, 0, cnt, t, K0);
+    return;
+  }
+  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT>(sA, sB, sC, sK, 0, nf, t, K0);
+  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT>(sA, sB, sC, sK, nf, nf + nm, t, K0);
+  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT>(sA, sB, sC, sK, nf + nm, cnt, t, K0);
 }
 
-// Class of a (target leaf, source leaf, image) entry.  d_min bounds every pair
-// distance from below (centre distance minus both radii); it is computed
-// from the FP32 copies and lowered by a margin covering their rounding, so
-// the class is never more optimistic than the FP64 value would give.
-__device__ __forceinline__ int entry_mode_f(const float4* cf, int a, int b, int img, float blen, float smax,
-                                            float margin0) {
-  const float4 A = cf[a], B = cf[b];
-  const float dx = A.x - (B.x + (float)(img / 9 - 1) * blen);
-  const float dy = A.y - (B.y + (float)((img / 3) % 3 - 1) * blen);
-  const float dz = A.z - (B.z + (float)(img % 3 - 1) * blen);
-  const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-  const float dmin = d - A.w - B.w - (margin0 + 1e-6f * (d + A.w + B.w));
+// Class of a staged source at X (relative to the target leaf centre, image
+// shift included) for a target leaf of radius Rt: its distance to the centre
+// minus Rt bounds its distance to every target from below; the bound is
+// lowered by a margin covering the FP32 rounding of the coordinates, so the
+// class is never more optimistic than exact arithmetic would give.
+__device__ __forceinline__ int source_class(float X, float Y, float Z, float Rt, float smax, float margin0) {
+  const float d = sqrtf(X * X + Y * Y + Z * Z);
+  const float dmin = d - Rt - (margin0 + 1e-6f * (d + Rt));
   if (dmin >= (float)kFarRho * smax) return kFar;
   if (dmin >= (float)kMidRho * smax) return kMid;
   return kNear;
+}
+
+// Staging slots of this lane's sources j = lane + 32 q (class cls[q], -1 if
+// j >= cnt): far sources first, then mid, then near, each group in source
+// order.  nf and nm (the far and mid counts) come out equal in every lane.
+// When every source is near the slot of source j is j.
+template <int TPT>
+__device__ __forceinline__ void group_slots(const int* cls, int lane, int* slot, int& nf, int& nm) {
+  unsigned bf[TPT], bm[TPT], bn[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    bf[q] = __ballot_sync(0xffffffffu, cls[q] == kFar);
+    bm[q] = __ballot_sync(0xffffffffu, cls[q] == kMid);
+    bn[q] = __ballot_sync(0xffffffffu, cls[q] == kNear);
+  }
+  nf = 0;
+  nm = 0;
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    nf += __popc(bf[q]);
+    nm += __popc(bm[q]);
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  int ef = 0, em = 0, en = 0;  // members of each class among the earlier q
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    if (cls[q] == kFar) slot[q] = ef + __popc(bf[q] & lt);
+    else if (cls[q] == kMid) slot[q] = nf + em + __popc(bm[q] & lt);
+    else if (cls[q] == kNear) slot[q] = nf + nm + en + __popc(bn[q] & lt);
+    else slot[q] = -1;
+    ef += __popc(bf[q]);
+    em += __popc(bm[q]);
+    en += __popc(bn[q]);
+  }
+}
+
+// Pair counts by class of one warp, added to the evaluation's counters.
+__device__ __forceinline__ void add_class_counts(unsigned long long* cnt, unsigned long long c_near,
+                                                 unsigned long long c_mid, unsigned long long c_far) {
+  if (threadIdx.x == 0) {
+    if (c_near) atomicAdd(&cnt[0], c_near);
+    if (c_mid) atomicAdd(&cnt[1], c_mid);
+    if (c_far) atomicAdd(&cnt[2], c_far);
+  }
 }
 
 // Targets held by one thread.
@@ -257,23 +305,6 @@ __device__ __forceinline__ void run_chunk(const float4* sA, const float4* sB, co
   }
 }
 
-template <bool PS, int TPT>
-__device__ __forceinline__ void dispatch_chunk(int mode, bool shift, bool self, const float4* sA, const float4* sB,
-                                               const SigK* sK, int cnt, Tgt<TPT>& t, float shx, float shy, float shz,
-                                               const SigK& K0) {
-  if (self) {
-    run_chunk<PS, kNear, false, true, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
-  } else if (mode == kFar) {
-    if (shift) run_chunk<PS, kFar, true, false, TPT>(sA, sB, sK, cnt, t, shx, shy, shz, K0);
-    else run_chunk<PS, kFar, false, false, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
-  } else if (mode == kMid) {
-    if (shift) run_chunk<PS, kMid, true, false, TPT>(sA, sB, sK, cnt, t, shx, shy, shz, K0);
-    else run_chunk<PS, kMid, false, false, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
-  } else {
-    if (shift) run_chunk<PS, kNear, true, false, TPT>(sA, sB, sK, cnt, t, shx, shy, shz, K0);
-    else run_chunk<PS, kNear, false, false, TPT>(sA, sB, sK, cnt, t, 0.f, 0.f, 0.f, K0);
-  }
-}
 
 
 // One warp per target leaf, TPT targets per lane; source chunks of 32*TPT
@@ -291,7 +322,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
                                             const uint32_t* __restrict__ sidx, float blen, float smax, float margin0,
                                             SigK K0, const double* __restrict__ dip, const int* __restrict__ cseg,
                                             const SegP2P* __restrict__ sp, float* __restrict__ vel,
-                                            float* __restrict__ dg) {
+                                            float* __restrict__ dg, unsigned long long* __restrict__ ccount) {
   constexpr int CH = 32 * TPT;
   __shared__ float4 sA[2][CH], sB[2][CH], sC[2][CH];
   __shared__ SigK sK[2][PS ? CH : 1];
@@ -312,20 +343,32 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
     duz = q.dip[2];
   }
   float4 ra[TPT], rb[TPT];
-  // source j of entry e, staged as X_j = (x_j - c) - shift, gamma_j, k_j = gamma_j x X_j
-  auto stage = [&](int bb, int cnt, int img) {
+  unsigned long long c_near = 0, c_mid = 0, c_far = 0;
+  // source j of entry e, staged as X_j = (x_j - c) - shift, gamma_j, k_j = gamma_j x X_j,
+  // grouped by class (the self entry in source order)
+  auto stage = [&](int bb, int cnt, int img, bool self_entry, int& nf, int& nm) {
     const float shx = -(float)(img / 9 - 1) * blen, shy = -(float)((img / 3) % 3 - 1) * blen,
                 shz = -(float)(img % 3 - 1) * blen;
+    float X[TPT], Y[TPT], Z[TPT];
+    int cls[TPT], slot[TPT];
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       const int j = lane + 32 * q;
-      if (j < cnt) {
-        const float X = (ra[q].x - lc.x) - shx, Y = (ra[q].y - lc.y) - shy, Z = (ra[q].z - lc.z) - shz;
+      X[q] = (ra[q].x - lc.x) - shx;
+      Y[q] = (ra[q].y - lc.y) - shy;
+      Z[q] = (ra[q].z - lc.z) - shz;
+      cls[q] = j >= cnt ? -1 : self_entry ? kNear : source_class(X[q], Y[q], Z[q], lc.w, smax, margin0);
+    }
+    group_slots<TPT>(cls, lane, slot, nf, nm);
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int k = slot[q];
+      if (k >= 0) {
         const float4 g = rb[q];
-        sA[bb][j] = make_float4(X, Y, Z, ra[q].w);
-        sB[bb][j] = g;
-        sC[bb][j] = make_float4(g.y * Z - g.z * Y, g.z * X - g.x * Z, g.x * Y - g.y * X, 0.f);
-        if (PS) sK[bb][j] = make_sigk(ra[q].w);
+        sA[bb][k] = make_float4(X[q], Y[q], Z[q], ra[q].w);
+        sB[bb][k] = g;
+        sC[bb][k] = make_float4(g.y * Z[q] - g.z * Y[q], g.z * X[q] - g.x * Z[q], g.x * Y[q] - g.y * X[q], 0.f);
+        if (PS) sK[bb][k] = make_sigk(ra[q].w);
       }
     }
   };
@@ -344,7 +387,8 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       t.gz[q] = gi.z;
       t.a[q] = AccR{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     }
-    int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0;
+    const unsigned long long nt = (unsigned long long)min(CH, te - t0);
+    int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0, cur_nf = 0, cur_nm = 0;
     int buf = 0;
     if (cur_e < rg.y) {
       cur_cnt = min(CH, end[list[cur_e].x] - cur_c0);
@@ -356,7 +400,8 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
           rb[q] = B[cur_c0 + j];
         }
       }
-      stage(0, cur_cnt, list[cur_e].y);
+      const int2 e0 = list[cur_e];
+      stage(0, cur_cnt, e0.y, e0.x == leaf && e0.y == kImageZero, cur_nf, cur_nm);
     }
     __syncwarp();
     while (cur_e < rg.y) {
@@ -379,17 +424,25 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       }
       const int2 ent = list[cur_e];
       const bool self = (ent.x == leaf) && ent.y == kImageZero;
-      const int mode = entry_mode_f(cf, leaf, ent.x, ent.y, blen, smax, margin0);
 #pragma unroll
       for (int q = 0; q < TPT; ++q) t.self[q] = self ? (t0 + lane + 32 * q) - cur_c0 : -1;
-      dispatch_rel<PS, TPT>(mode, self, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0);
+      dispatch_rel<PS, TPT>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0);
+      c_far += nt * (unsigned long long)cur_nf;
+      c_mid += nt * (unsigned long long)cur_nm;
+      c_near += nt * (unsigned long long)(cur_cnt - cur_nf - cur_nm);
       __syncwarp();
       buf ^= 1;
-      if (ne < rg.y) stage(buf, ncnt, list[ne].y);
+      int nnf = 0, nnm = 0;
+      if (ne < rg.y) {
+        const int2 en = list[ne];
+        stage(buf, ncnt, en.y, en.x == leaf && en.y == kImageZero, nnf, nnm);
+      }
       __syncwarp();
       cur_e = ne;
       cur_c0 = nc0;
       cur_cnt = ncnt;
+      cur_nf = nnf;
+      cur_nm = nnm;
     }
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
@@ -411,6 +464,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       }
     }
   }
+  add_class_counts(ccount, c_near, c_mid, c_far);
 }
 
 // ---- Packed form: the two targets of a lane as float2 lanes of the FP32x2
@@ -488,11 +542,11 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
 
 template <int MODE, bool SELF>
 __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
-                                             const float2* s4, int cnt, float2 tx, float2 ty, float2 tz,
+                                             const float2* s4, int jb, int je, float2 tx, float2 ty, float2 tz,
                                              float2 gix, float2 giy, float2 giz, int self_lo, int self_hi,
                                              const SigK2& K, AccR2& a) {
 #pragma unroll 4
-  for (int j = 0; j < cnt; ++j) {
+  for (int j = jb; j < je; ++j) {
     const float4 v0 = s0[j], v1 = s1[j], v2 = s2[j], v3 = s3[j];
     const float2 v4 = s4[j];
     const float2 dx = add2(tx, make_float2(v0.x, v0.y));
@@ -541,7 +595,8 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
                                                const uint32_t* __restrict__ sidx, float blen, float smax,
                                                float margin0, SigK K0, const double* __restrict__ dip,
                                                const int* __restrict__ cseg, const SegP2P* __restrict__ sp,
-                                               float* __restrict__ vel, float* __restrict__ dg) {
+                                               float* __restrict__ vel, float* __restrict__ dg,
+                                               unsigned long long* __restrict__ ccount) {
   constexpr int CH = 64;
   __shared__ float4 s0[2][CH], s1[2][CH], s2[2][CH], s3[2][CH];
   __shared__ float2 s4[2][CH];
@@ -563,21 +618,32 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
   }
   const SigK2 K = make_sigk2(K0);
   float4 ra[2], rb[2];
-  auto stage = [&](int bb, int cnt, int img) {
+  unsigned long long c_near = 0, c_mid = 0, c_far = 0;
+  auto stage = [&](int bb, int cnt, int img, bool self_entry, int& nf, int& nm) {
     const float shx = -(float)(img / 9 - 1) * blen, shy = -(float)((img / 3) % 3 - 1) * blen,
                 shz = -(float)(img % 3 - 1) * blen;
+    float X[2], Y[2], Z[2];
+    int cls[2], slot[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int j = lane + 32 * q;
-      if (j < cnt) {
-        const float X = (ra[q].x - lc.x) - shx, Y = (ra[q].y - lc.y) - shy, Z = (ra[q].z - lc.z) - shz;
+      X[q] = (ra[q].x - lc.x) - shx;
+      Y[q] = (ra[q].y - lc.y) - shy;
+      Z[q] = (ra[q].z - lc.z) - shz;
+      cls[q] = j >= cnt ? -1 : self_entry ? kNear : source_class(X[q], Y[q], Z[q], lc.w, smax, margin0);
+    }
+    group_slots<2>(cls, lane, slot, nf, nm);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int k = slot[q];
+      if (k >= 0) {
         const float4 g = rb[q];
-        const float kx = g.y * Z - g.z * Y, ky = g.z * X - g.x * Z, kz = g.x * Y - g.y * X;
-        s0[bb][j] = make_float4(-X, -X, -Y, -Y);
-        s1[bb][j] = make_float4(-Z, -Z, g.x, g.x);
-        s2[bb][j] = make_float4(g.y, g.y, g.z, g.z);
-        s3[bb][j] = make_float4(kx, kx, ky, ky);
-        s4[bb][j] = make_float2(kz, kz);
+        const float kx = g.y * Z[q] - g.z * Y[q], ky = g.z * X[q] - g.x * Z[q], kz = g.x * Y[q] - g.y * X[q];
+        s0[bb][k] = make_float4(-X[q], -X[q], -Y[q], -Y[q]);
+        s1[bb][k] = make_float4(-Z[q], -Z[q], g.x, g.x);
+        s2[bb][k] = make_float4(g.y, g.y, g.z, g.z);
+        s3[bb][k] = make_float4(kx, kx, ky, ky);
+        s4[bb][k] = make_float2(kz, kz);
       }
     }
   };
@@ -600,7 +666,8 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
                  giz = make_float2(gzs[0], gzs[1]);
     AccR2 a;
     a.ax = a.ay = a.az = a.bx = a.by = a.bz = a.cx = a.cy = a.cz = a.dx = a.dy = a.dz = dup2(0.f);
-    int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0;
+    const unsigned long long nt = (unsigned long long)min(CH, te - t0);
+    int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0, cur_nf = 0, cur_nm = 0;
     int buf = 0;
     if (cur_e < rg.y) {
       cur_cnt = min(CH, end[list[cur_e].x] - cur_c0);
@@ -612,7 +679,8 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
           rb[q] = B[cur_c0 + j];
         }
       }
-      stage(0, cur_cnt, list[cur_e].y);
+      const int2 e0 = list[cur_e];
+      stage(0, cur_cnt, e0.y, e0.x == leaf && e0.y == kImageZero, cur_nf, cur_nm);
     }
     __syncwarp();
     while (cur_e < rg.y) {
@@ -635,7 +703,6 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       }
       const int2 ent = list[cur_e];
       const bool self = (ent.x == leaf) && ent.y == kImageZero;
-      const int mode = entry_mode_f(cf, leaf, ent.x, ent.y, blen, smax, margin0);
       const float4* c0 = s0[buf];
       const float4* c1 = s1[buf];
       const float4* c2 = s2[buf];
@@ -643,21 +710,32 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       const float2* c4 = s4[buf];
       if (self) {
         const int slo = (t0 + lane) - cur_c0, shi = (t0 + lane + 32) - cur_c0;
-        run_chunk_x2<kNear, true>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, slo, shi, K, a);
-      } else if (mode == kFar) {
-        run_chunk_x2<kFar, false>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
-      } else if (mode == kMid) {
-        run_chunk_x2<kMid, false>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+        run_chunk_x2<kNear, true>(c0, c1, c2, c3, c4, 0, cur_cnt, tx, ty, tz, gix, giy, giz, slo, shi, K, a);
       } else {
-        run_chunk_x2<kNear, false>(c0, c1, c2, c3, c4, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+        const int nfm = cur_nf + cur_nm;
+        if (cur_nf > 0)
+          run_chunk_x2<kFar, false>(c0, c1, c2, c3, c4, 0, cur_nf, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+        if (cur_nm > 0)
+          run_chunk_x2<kMid, false>(c0, c1, c2, c3, c4, cur_nf, nfm, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+        if (nfm < cur_cnt)
+          run_chunk_x2<kNear, false>(c0, c1, c2, c3, c4, nfm, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
       }
+      c_far += nt * (unsigned long long)cur_nf;
+      c_mid += nt * (unsigned long long)cur_nm;
+      c_near += nt * (unsigned long long)(cur_cnt - cur_nf - cur_nm);
       __syncwarp();
       buf ^= 1;
-      if (ne < rg.y) stage(buf, ncnt, list[ne].y);
+      int nnf = 0, nnm = 0;
+      if (ne < rg.y) {
+        const int2 en = list[ne];
+        stage(buf, ncnt, en.y, en.x == leaf && en.y == kImageZero, nnf, nnm);
+      }
       __syncwarp();
       cur_e = ne;
       cur_c0 = nc0;
       cur_cnt = ncnt;
+      cur_nf = nnf;
+      cur_nm = nnm;
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -682,6 +760,7 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       }
     }
   }
+  add_class_counts(ccount, c_near, c_mid, c_far);
 }
 
 // All pairs of one array, free space, self pair skipped (near class throughout).
@@ -800,35 +879,6 @@ __global__ void __launch_bounds__(256) k_dipole_seg(const float4* __restrict__ A
   if (threadIdx.x < 3) sp[sg].dip[threadIdx.x] = (float)(-sh[threadIdx.x][0] / (3.0 * L * L * L));
 }
 
-// Pair counts per class (near, mid, far) for the work statistics.
-__global__ void k_p2p_classes(const int* __restrict__ leaves, const int2* __restrict__ off,
-                              const int2* __restrict__ list, const int* __restrict__ begin,
-                              const int* __restrict__ end, const float4* __restrict__ cf, float blen, float smax,
-                              float margin0, const int* __restrict__ cseg, const SegP2P* __restrict__ sp,
-                              unsigned long long* __restrict__ counts) {
-  const int leaf = leaves[blockIdx.x];
-  if (cseg) {
-    const SegP2P q = sp[cseg[leaf]];
-    blen = q.blen;
-    smax = q.smax;
-    margin0 = q.margin;
-  }
-  const int2 rg = off[blockIdx.x];
-  const unsigned long long nt = (unsigned long long)(end[leaf] - begin[leaf]);
-  unsigned long long c[3] = {0ull, 0ull, 0ull};
-  for (int e = rg.x + (int)threadIdx.x; e < rg.y; e += 32) {
-    const int2 ent = list[e];
-    const int m = (ent.x == leaf && ent.y == kImageZero) ? kNear
-                                                         : entry_mode_f(cf, leaf, ent.x, ent.y, blen, smax, margin0);
-    c[m] += nt * (unsigned long long)(end[ent.x] - begin[ent.x]);
-  }
-  for (int q = 0; q < 3; ++q) {
-    unsigned long long v = c[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0 && v) atomicAdd(&counts[q], v);
-  }
-}
-
 }  // namespace
 
 int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel, float* dg, cudaStream_t s) {
@@ -866,10 +916,12 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   const float smaxf = (float)smax;
   const float margin0 = (float)p->cf_margin;
   const bool two = p->prm.ncrit > 32;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
+  FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
   ++g_launches;
 #define FMM_P2P_LAUNCH(PS_, TPT_, SEG_)                                                                         \
   k_p2p<PS_, TPT_, SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, \
-                                          margin0, K0, dip, cseg, sp, vel, dg)
+                                          margin0, K0, dip, cseg, sp, vel, dg, cnt)
   // the packed kernel stages 9 KB per warp: ask for the largest shared-memory carveout
   static bool carveout_set = false;
   if (!carveout_set) {
@@ -881,7 +933,7 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   }
 #define FMM_P2P_X2_LAUNCH(SEG_)                                                                                \
   k_p2p_x2<SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, \
-                                  K0, dip, cseg, sp, vel, dg)
+                                  K0, dip, cseg, sp, vel, dg, cnt)
   if (cseg) {
     if (two) {
       if (ps) FMM_P2P_LAUNCH(true, 2, true);
@@ -901,11 +953,6 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   }
 #undef FMM_P2P_LAUNCH
 #undef FMM_P2P_X2_LAUNCH
-  FMM_CUDA_TRY(cudaGetLastError());
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
-  FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
-  ++g_launches;
-  k_p2p_classes<<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, blen, smaxf, margin0, cseg, sp, cnt);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
