@@ -78,6 +78,8 @@ struct fmm_plan_s {
   fmm::DBuf c_cf;                                                   // float4 (centre, radius) rounded to FP32
   fmm::DBuf c_tile;                                                 // int32 tile*64+slot of each cell
   fmm::DBuf tile_cells;                                             // cell of each (tile, slot) position
+  fmm::DBuf tile_first;  // int32 [ntiles+1]: tile t = tile_cells[tile_first[t] .. tile_first[t+1])
+  fmm::DBuf tile_groups; // int32 (level, octant) cell counts, then cell and tile offsets of the groups
   fmm::DBuf leaves;                                                 // leaf cell ids
   fmm::DBuf M, L;                                                   // [cells][3][P] FP32
   fmm::DBuf Mbf;                                                    // [cells][2][3][64 x K chunks] BF16 hi/lo
@@ -105,7 +107,6 @@ struct fmm_plan_s {
   void* pinned = nullptr;  // host pinned scratch (counts)
   // host mirror of the last tree / lists
   std::vector<int> level_begin;  // cells of level l: [level_begin[l], level_begin[l+1])
-  std::vector<int> tile_begin;   // tiles of level l: [tile_begin[l], tile_begin[l+1])
   int64_t ncells = 0, nleaves = 0, ntiles = 0;
   int nlevels = 0;
   double cf_margin = 0.0;  // rounding margin of the FP32 cell copies (2e-6 x largest coordinate)
@@ -183,9 +184,4 @@ __host__ __device__ inline int m2l_kchunks(int P) { return ((P + 15) / 16 + 3) /
 __host__ __device__ inline int m2l_rowblocks(int P) { return (P + 127) / 128; }
 
 // Level / tile layout of the current tree, passed to kernels by value.
-struct LevelInfo {
-  int nlevels;
-  int level_begin[kMaxLevel + 2];
-  int tile_begin[kMaxLevel + 2];
-};
 }  // namespace fmm

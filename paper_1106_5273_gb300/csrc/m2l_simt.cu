@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kRC = 32;  // output rows per pass
 
-__global__ void __launch_bounds__(192) k_m2l_simt(const int2* __restrict__ tile_range, LevelInfo li,
+__global__ void __launch_bounds__(192) k_m2l_simt(const int2* __restrict__ tile_range, const int* __restrict__ tfirst,
                                                   const int* __restrict__ st_slot, const int* __restrict__ st_src,
                                                   const float* __restrict__ T32, const float* __restrict__ M, int P,
                                                   const int* __restrict__ tcell, float* __restrict__ L) {
@@ -20,10 +20,8 @@ __global__ void __launch_bounds__(192) k_m2l_simt(const int2* __restrict__ tile_
   const int tile = blockIdx.x;
   const int2 rg = tile_range[tile];
   if (rg.y <= rg.x) return;
-  int l = 0;
-  while (l + 1 < li.nlevels && li.tile_begin[l + 1] <= tile) ++l;
-  const int first = li.level_begin[l] + (tile - li.tile_begin[l]) * kTile;
-  const int ncell = min(kTile, li.level_begin[l + 1] - first);
+  const int first = tfirst[tile];
+  const int ncell = tfirst[tile + 1] - first;
   const int comp = threadIdx.x / kTile, slot = threadIdx.x % kTile;
   for (int r0 = 0; r0 < P; r0 += kRC) {
     const int nr = min(kRC, P - r0);
@@ -56,16 +54,11 @@ __global__ void __launch_bounds__(192) k_m2l_simt(const int2* __restrict__ tile_
 
 int m2l_simt(fmm_plan p, cudaStream_t s) {
   if (p->n_steps == 0) return FMM_OK;
-  LevelInfo li;
-  li.nlevels = p->nlevels;
-  for (int l = 0; l <= p->nlevels; ++l) {
-    li.level_begin[l] = p->level_begin[l];
-    li.tile_begin[l] = p->tile_begin[l];
-  }
   size_t sh = (size_t)kRC * p->P * sizeof(float);
   if (sh > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   ++g_launches;
-  k_m2l_simt<<<(unsigned)p->ntiles, 3 * kTile, sh, s>>>(p->tile_range.as<int2>(), li, p->st_slot.as<int>(),
+  k_m2l_simt<<<(unsigned)p->ntiles, 3 * kTile, sh, s>>>(p->tile_range.as<int2>(), p->tile_first.as<int>(),
+                                                         p->st_slot.as<int>(),
                                                          p->st_src.as<int>(), p->T32.as<float>(), p->M.as<float>(),
                                                          p->P, p->tile_cells.as<int>(), p->L.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());

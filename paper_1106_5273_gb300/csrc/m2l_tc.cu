@@ -120,7 +120,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_m2l_tc(const int2* __restrict__ tile_range, LevelInfo li, const int* __restrict__ st_slot,
+    k_m2l_tc(const int2* __restrict__ tile_range, const int* __restrict__ tfirst, const int* __restrict__ st_slot,
              const int* __restrict__ st_src, const __nv_bfloat16* __restrict__ Tbf,
              const __nv_bfloat16* __restrict__ Mbf, int P, int nkc, int ksteps_last, int kpad, int nrh,
              const int* __restrict__ tcell, float* __restrict__ L, int* __restrict__ flag) {
@@ -193,7 +193,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(fullB(stage));
     }
   } else if (lane == 0) {
-    // ---- control thread: operator copies and MMAs
+    // ---- control thread: operator copies and MMAs.  Only the operator rows
+    // below P are copied (whole 8-row swizzle groups): the rows above feed only
+    // output rows that the epilogue never stores.
+    const uint32_t arows = (uint32_t)min(128, ((P - rh * 128) + 7) & ~7);
+    const uint32_t abytes = arows * 128u;
     int issued = 0;  // A copies issued for iterations [0, issued)
     auto issue_A = [&](int it) -> bool {
       const int stage = it & 1;
@@ -205,9 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * nkc + kc) * chunk + row0;
       const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * nkc + kc) * chunk + row0;
       const uint32_t a0 = sbase + stage * kStageBytes;
-      mbar_arrive_tx(fullA(stage), 2 * kABytes);
-      bulk_g2s(a0, hi, kABytes, fullA(stage));
-      bulk_g2s(a0 + kABytes, lo, kABytes, fullA(stage));
+      mbar_arrive_tx(fullA(stage), 2 * abytes);
+      bulk_g2s(a0, hi, abytes, fullA(stage));
+      bulk_g2s(a0 + kABytes, lo, abytes, fullA(stage));
       issued = it + 1;
       return true;
     };
@@ -259,10 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp < 4) {
     if (mbar_wait(done, 0u, abort)) {
       tc_fence_after();
-      int l = 0;
-      while (l + 1 < li.nlevels && li.tile_begin[l + 1] <= tile) ++l;
-      const int first = li.level_begin[l] + (tile - li.tile_begin[l]) * kTile;
-      const int ncell = min(kTile, li.level_begin[l + 1] - first);
+      const int first = tfirst[tile];
+      const int ncell = tfirst[tile + 1] - first;
       const int r = rh * 128 + warp * 32 + lane;  // output coefficient of this TMEM lane
 #pragma unroll 1
       for (int cb = 0; cb < kN / 16; ++cb) {
@@ -306,12 +308,6 @@ __global__ void k_wait_selftest(long long spins, int arrive, int* status) {
 
 int m2l_tensor(fmm_plan p, cudaStream_t s) {
   if (p->n_steps == 0) return FMM_OK;
-  LevelInfo li;
-  li.nlevels = p->nlevels;
-  for (int l = 0; l <= p->nlevels; ++l) {
-    li.level_begin[l] = p->level_begin[l];
-    li.tile_begin[l] = p->tile_begin[l];
-  }
   const int ksteps = (p->P + 15) / 16;
   const int nkc = m2l_kchunks(p->P);
   const int last = ksteps - 4 * (nkc - 1);
@@ -320,7 +316,7 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   const int nrh = m2l_rowblocks(p->P);
   ++g_launches;
   k_m2l_tc<<<dim3((unsigned)p->ntiles, (unsigned)nrh), kThreads, sh, s>>>(
-      p->tile_range.as<int2>(), li, p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
+      p->tile_range.as<int2>(), p->tile_first.as<int>(), p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
       p->Mbf.as<__nv_bfloat16>(), p->P, nkc, last, 64 * nkc, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
       p->flags.as<int>());
   FMM_CUDA_TRY(cudaGetLastError());

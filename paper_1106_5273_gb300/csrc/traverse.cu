@@ -353,27 +353,38 @@ __global__ void k_unique_flags(const uint64_t* __restrict__ k, int n, uint32_t* 
   if (i < n) f[i] = (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
 }
 
-// Tiles group the cells of one level by child octant (then Morton order):
-// cells at the same octant position have the same relative interaction
-// lists in a uniform region, so a tile's steps are nearly full.
+// Tiles group the cells of one level and one child octant (in Morton order),
+// at most 64 per tile: cells at the same octant position have the same
+// relative interaction lists in a uniform region, so a tile's steps are
+// nearly full; a tile never mixes octants, so a coarse level is split into
+// its octants instead of one long tile.
 __global__ void k_tile_order_keys(const int* __restrict__ level, const uint64_t* __restrict__ ckey, int nc,
-                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                  int* __restrict__ gcount) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
-  keys[c] = ((uint64_t)level[c] << 40) | ((ckey[c] & 7ull) << 32) | (uint64_t)c;
+  const int oct = (int)(ckey[c] & 7ull);
+  keys[c] = ((uint64_t)level[c] << 40) | ((uint64_t)oct << 32) | (uint64_t)c;
   vals[c] = (uint32_t)c;
+  atomicAdd(&gcount[level[c] * 8 + oct], 1);
 }
 
-__global__ void k_cell_tiles(LevelInfo li, int nc, const uint32_t* __restrict__ order, int* __restrict__ ctile,
-                             int* __restrict__ tcell) {
+// gofs[g] = first sorted position of (level, octant) group g, gtile[g] = its
+// first tile.
+__global__ void k_cell_tiles(int nc, int ntiles, const uint32_t* __restrict__ order, const int* __restrict__ level,
+                             const uint64_t* __restrict__ ckey, const int* __restrict__ gofs,
+                             const int* __restrict__ gtile, int* __restrict__ ctile, int* __restrict__ tcell,
+                             int* __restrict__ tfirst) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nc) return;
-  int l = 0;
-  while (l + 1 < li.nlevels && li.level_begin[l + 1] <= q) ++l;
-  int r = q - li.level_begin[l];
-  int c = (int)order[q];
-  ctile[c] = (li.tile_begin[l] + r / kTile) * kTile + r % kTile;
+  const int c = (int)order[q];
+  const int g = level[c] * 8 + (int)(ckey[c] & 7ull);
+  const int r = q - gofs[g];
+  const int t = gtile[g] + r / kTile;
+  ctile[c] = t * kTile + r % kTile;
   tcell[q] = c;
+  if (r % kTile == 0) tfirst[t] = q;
+  if (q == 0) tfirst[ntiles] = nc;
 }
 
 __global__ void k_step_flags(const uint64_t* __restrict__ k, int n, uint32_t* __restrict__ f) {
@@ -557,36 +568,46 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   // ---- M2L: keys, unique operators, steps per (tile, key)
   {
     const int n = (int)nm;
-    // tiles of 64 consecutive cells per level
-    LevelInfo li;
-    li.nlevels = p->nlevels;
-    p->tile_begin.assign(p->nlevels + 1, 0);
-    for (int l = 0; l < p->nlevels; ++l) {
-      li.level_begin[l] = p->level_begin[l];
-      li.tile_begin[l] = p->tile_begin[l];
-      int cnt = p->level_begin[l + 1] - p->level_begin[l];
-      p->tile_begin[l + 1] = p->tile_begin[l] + (cnt + kTile - 1) / kTile;
-    }
-    li.level_begin[p->nlevels] = p->level_begin[p->nlevels];
-    li.tile_begin[p->nlevels] = p->tile_begin[p->nlevels];
-    p->ntiles = p->tile_begin[p->nlevels];
+    // tiles: at most 64 cells of one (level, octant) group each
+    constexpr int kGroups = (kMaxLevel + 1) * 8;
     FMM_TRY(p->c_tile.ensure((nc + 1) * sizeof(int)));
     FMM_TRY(p->tile_cells.ensure((nc + 1) * sizeof(int)));
+    FMM_TRY(p->tile_groups.ensure(3 * kGroups * sizeof(int)));
     FMM_TRY(p->lk0.ensure((nc + 1) * sizeof(uint64_t)));
     FMM_TRY(p->lk1.ensure((nc + 1) * sizeof(uint64_t)));
     FMM_TRY(p->lv0.ensure((nc + 1) * sizeof(uint32_t)));
     FMM_TRY(p->lv1.ensure((nc + 1) * sizeof(uint32_t)));
     {
+      int* gcount = p->tile_groups.as<int>();
+      int* gofs = gcount + kGroups;
+      int* gtile = gofs + kGroups;
+      FMM_CUDA_TRY(cudaMemsetAsync(gcount, 0, kGroups * sizeof(int), s));
       unsigned gc = (unsigned)((nc + T - 1) / T);
       ++g_launches;
       k_tile_order_keys<<<gc, T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc, p->lk0.as<uint64_t>(),
-                                         p->lv0.as<uint32_t>());
+                                         p->lv0.as<uint32_t>(), gcount);
       int second = 0;
       FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
                              p->lv1.as<uint32_t>(), nc, 0, 48, &second, p->sort_hist, p->scan_tmp, s));
       uint32_t* ord = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+      int* hg = reinterpret_cast<int*>(reinterpret_cast<char*>(p->pinned) + 1024);  // counts, then offsets
+      FMM_CUDA_TRY(cudaMemcpyAsync(hg, gcount, kGroups * sizeof(int), cudaMemcpyDeviceToHost, s));
+      FMM_CUDA_TRY(cudaStreamSynchronize(s));
+      int* hofs = hg + kGroups;
+      int* htile = hofs + kGroups;
+      int cells = 0, tiles = 0;
+      for (int g = 0; g < kGroups; ++g) {
+        hofs[g] = cells;
+        htile[g] = tiles;
+        cells += hg[g];
+        tiles += (hg[g] + kTile - 1) / kTile;
+      }
+      p->ntiles = tiles;
+      FMM_CUDA_TRY(cudaMemcpyAsync(gofs, hofs, 2 * kGroups * sizeof(int), cudaMemcpyHostToDevice, s));
+      FMM_TRY(p->tile_first.ensure((p->ntiles + 1) * sizeof(int)));
       ++g_launches;
-      k_cell_tiles<<<gc, T, 0, s>>>(li, nc, ord, p->c_tile.as<int>(), p->tile_cells.as<int>());
+      k_cell_tiles<<<gc, T, 0, s>>>(nc, (int)p->ntiles, ord, p->c_level.as<int>(), p->c_key.as<uint64_t>(), gofs,
+                                    gtile, p->c_tile.as<int>(), p->tile_cells.as<int>(), p->tile_first.as<int>());
     }
     FMM_TRY(p->tile_range.ensure((p->ntiles + 1) * sizeof(int2)));
     FMM_CUDA_TRY(cudaMemsetAsync(p->tile_range.ptr, 0, (p->ntiles + 1) * sizeof(int2), s));
