@@ -446,6 +446,22 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     st = plan.stats()
+    # the same evaluation without the stretching output (velocity-only kernels)
+    vo_ms, vo_p2p = [], []
+    for it in range(3 + 3):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval(pos, gam, sigma_uniform=sig, vel=vel, stretching=False)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= 3:
+            vo_ms.append(e0.elapsed_time(e1))
+            vo_p2p.append(plan.stats().ms_p2p)
+    velocity_only = {"ms_per_step": sum(vo_ms) / len(vo_ms), "ms_p2p": sum(vo_p2p) / len(vo_p2p),
+                     "particles_per_s": job_value(n, world, job_time(sum(vo_ms) / len(vo_ms), dist)),
+                     "steps": len(vo_ms), "note": "dgamma = NULL: P2P skips T and the stretching sums"}
     t_step = job_time(sum(ms) / len(ms), dist)
     value = job_value(n, world, t_step)
     # end to end through the host-buffer entry point (pinned memory)
@@ -506,6 +522,7 @@ def main():
                          "fp32_pipe_slot_frac": slots / p2p_t / (SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6),
                          "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
             "paper_convention_tflops": 174 * pairs / p2p_t / 1e12,
+            "velocity_only": velocity_only,
             "phases_ms": {k: getattr(st, k) for k in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
                                                        "ms_downward", "ms_p2p", "ms_total")},
             "work": {k: getattr(st, k) for k in ("ncells", "nleaves", "nlevels", "p2p_cell_pairs", "p2p_pairs",

@@ -138,14 +138,19 @@ class Plan:
         except Exception:
             pass
 
-    def eval(self, pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None):
-        """fmm_eval_velocity_stretching on torch CUDA tensors; returns (vel, dgamma)."""
+    def eval(self, pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None,
+             stretching=True):
+        """fmm_eval_velocity_stretching on torch CUDA tensors; returns (vel, dgamma).
+        stretching=False passes no stretching output (the velocity-only kernels run)
+        and returns (vel, None)."""
         import torch
         n = pos.shape[0]
         if vel is None:
             vel = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
-        if dgamma is None:
+        if dgamma is None and stretching:
             dgamma = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        if not stretching:
+            dgamma = None
         _check(lib.fmm_eval_velocity_stretching(
             self._h, n, _dptr(pos, name="pos"), _dptr(gamma, name="gamma"), _dptr(sigma, name="sigma"),
             float(sigma_uniform), _dptr(vel, name="vel"), _dptr(dgamma, name="dgamma"),

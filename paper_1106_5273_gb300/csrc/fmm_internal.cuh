@@ -78,6 +78,7 @@ struct fmm_plan_s {
   fmm::DBuf c_cf;                                                   // float4 (centre, radius) rounded to FP32
   fmm::DBuf c_tile;                                                 // int32 tile*64+slot of each cell
   fmm::DBuf tile_cells;                                             // cell of each (tile, slot) position
+  fmm::DBuf c_ijk;       // uint64 integer cell coordinates, 21 bits per axis
   fmm::DBuf tile_first;  // int32 [ntiles+1]: tile t = tile_cells[tile_first[t] .. tile_first[t+1])
   fmm::DBuf tile_groups; // int32 (level, octant) cell counts, then cell and tile offsets of the groups
   fmm::DBuf leaves;                                                 // leaf cell ids

@@ -92,14 +92,16 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   return k;
 }
 
-// S = g/r^3 and T = S'(r)/r for one pair (see the file header).
-template <int MODE>
+// S = g/r^3 and T = S'(r)/r for one pair (see the file header); ST = false:
+// S only (velocity without stretching).
+template <int MODE, bool ST = true>
 __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float& T) {
   const float rinv = rsqrt_approx(r2);
   const float rinv2 = rinv * rinv;
+  T = 0.f;
   if (MODE == kFar) {
     S = rinv2 * rinv;
-    T = -3.f * S * rinv2;
+    if (ST) T = -3.f * S * rinv2;
     return;
   }
   const float rinv3 = rinv2 * rinv;
@@ -108,7 +110,7 @@ __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float
   // polynomial, so g = 1 to FP32 precision without clamping
   const float hn = fmaf(fmaf(fmaf(fmaf(K.hn4, rinv, K.hn3), rinv, K.hn2), rinv, K.hn1), rinv, K.hn0);
   S = fmaf(q, rinv2 * hn, rinv3);
-  T = fmaf(K.kc, q, -3.f * S) * rinv2;
+  if (ST) T = fmaf(K.kc, q, -3.f * S) * rinv2;
   if (MODE == kNear) {
     const float u = r2 * K.ku;
     if (u < 2.f) {
@@ -116,10 +118,10 @@ __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float
 #pragma unroll
       for (int k = kSerTerms - 2; k >= 0; --k) {
         sS = fmaf(sS, u, cSer[k]);
-        if (k >= 1) sT = fmaf(sT, u, (float)k * cSer[k]);
+        if (ST && k >= 1) sT = fmaf(sT, u, (float)k * cSer[k]);
       }
       S = sS * K.is3;
-      T = sT * K.is5;
+      if (ST) T = sT * K.is5;
     }
   }
 }
@@ -158,18 +160,19 @@ struct AccR {
   float ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz;
 };
 
-template <int MODE>
+template <int MODE, bool ST>
 __device__ __forceinline__ void pair_acc_rel(float dx, float dy, float dz, const float4& gj, const float4& kj,
                                              float gix, float giy, float giz, const SigK& K, AccR& a) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   float S, T;
-  pair_ST<MODE>(r2, K, S, T);
+  pair_ST<MODE, ST>(r2, K, S, T);
   a.ax = fmaf(S, gj.x, a.ax);
   a.ay = fmaf(S, gj.y, a.ay);
   a.az = fmaf(S, gj.z, a.az);
   a.bx = fmaf(S, kj.x, a.bx);
   a.by = fmaf(S, kj.y, a.by);
   a.bz = fmaf(S, kj.z, a.bz);
+  if (!ST) return;
   const float td = T * fmaf(gix, dx, fmaf(giy, dy, giz * dz));
   a.cx = fmaf(td, gj.x, a.cx);
   a.cy = fmaf(td, gj.y, a.cy);
@@ -186,7 +189,7 @@ struct TgtR {
   AccR a[TPT];
 };
 
-template <bool PS, int MODE, bool SELF, int TPT>
+template <bool PS, int MODE, bool SELF, int TPT, bool ST>
 __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
                                               int jb, int je, TgtR<TPT>& t, const SigK& K0) {
 #pragma unroll 4
@@ -197,7 +200,7 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       if (SELF && j == t.self[q]) continue;
-      pair_acc_rel<MODE>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, gj, kj, t.gx[q], t.gy[q], t.gz[q],
+      pair_acc_rel<MODE, ST>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, gj, kj, t.gx[q], t.gy[q], t.gz[q],
                          PS ? sK[j] : K0, t.a[q]);
     }
   }
@@ -206,17 +209,17 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
 // The groups of a staged chunk: sources [0, nf) far, [nf, nf + nm) mid, the
 // rest near; the self entry (not grouped) runs the near form with the self
 // pair skipped.
-template <bool PS, int TPT>
+template <bool PS, int TPT, bool ST>
 __device__ __forceinline__ void dispatch_rel(bool self, int nf, int nm, const float4* sA, const float4* sB,
                                              const float4* sC, const SigK* sK, int cnt, TgtR<TPT>& t,
                                              const SigK& K0) {
   if (self) {
-    run_chunk_rel<PS, kNear, true, TPT>(sA, sB, sC, sK, 0, cnt, t, K0);
+    run_chunk_rel<PS, kNear, true, TPT, ST>(sA, sB, sC, sK, 0, cnt, t, K0);
     return;
   }
-  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT>(sA, sB, sC, sK, 0, nf, t, K0);
-  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT>(sA, sB, sC, sK, nf, nf + nm, t, K0);
-  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT>(sA, sB, sC, sK, nf + nm, cnt, t, K0);
+  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT, ST>(sA, sB, sC, sK, 0, nf, t, K0);
+  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT, ST>(sA, sB, sC, sK, nf, nf + nm, t, K0);
+  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT, ST>(sA, sB, sC, sK, nf + nm, cnt, t, K0);
 }
 
 // Class of a staged source at X (relative to the target leaf centre, image
@@ -313,7 +316,8 @@ __device__ __forceinline__ void run_chunk(const float4* sA, const float4* sB, co
 // the target leaf centre.
 // SEG: a batch of problems; the leaf's problem supplies sigma, the class
 // bounds, the image shift and the dipole correction instead of the arguments.
-template <bool PS, int TPT, bool SEG>
+// ST = false: velocity only (dg is not written).
+template <bool PS, int TPT, bool SEG, bool ST>
 __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
                                             const int2* __restrict__ list, const int* __restrict__ begin,
                                             const int* __restrict__ end, const float4* __restrict__ cf,
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       const bool self = (ent.x == leaf) && ent.y == kImageZero;
 #pragma unroll
       for (int q = 0; q < TPT; ++q) t.self[q] = self ? (t0 + lane + 32 * q) - cur_c0 : -1;
-      dispatch_rel<PS, TPT>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0);
+      dispatch_rel<PS, TPT, ST>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0);
       c_far += nt * (unsigned long long)cur_nf;
       c_mid += nt * (unsigned long long)cur_nm;
       c_near += nt * (unsigned long long)(cur_cnt - cur_nf - cur_nm);
@@ -456,7 +460,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
         vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * ((a.az * X - a.ax * Z) - a.by) + duy;
         vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * ((a.ax * Y - a.ay * X) - a.bz) + duz;
       }
-      if (dg) {  // s = A x gamma_i + C x X_i - D
+      if (ST && dg) {  // s = A x gamma_i + C x X_i - D
         const float gx = t.gx[q], gy = t.gy[q], gz = t.gz[q];
         dg[3 * o] = far_s[3 * i] + kInv4Pi * ((a.ay * gz - a.az * gy) + (a.cy * Z - a.cz * Y) - a.dx);
         dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((a.az * gx - a.ax * gz) + (a.cz * X - a.cx * Z) - a.dy);
@@ -503,13 +507,14 @@ struct AccR2 {
 };
 
 // S and T of two pairs (see pair_ST).
-template <int MODE>
+template <int MODE, bool ST>
 __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, float2& T) {
   const float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
   const float2 rinv2 = mul2(rinv, rinv);
+  T = dup2(0.f);
   if (MODE == kFar) {
     S = mul2(rinv2, rinv);
-    T = mul2(mul2(dup2(-3.f), S), rinv2);
+    if (ST) T = mul2(mul2(dup2(-3.f), S), rinv2);
     return;
   }
   const float2 rinv3 = mul2(rinv2, rinv);
@@ -517,7 +522,7 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
   const float2 q = make_float2(ex2_approx(qa.x), ex2_approx(qa.y));
   const float2 hn = fma2(fma2(fma2(fma2(K.hn4, rinv, K.hn3), rinv, K.hn2), rinv, K.hn1), rinv, K.hn0);
   S = fma2(q, mul2(rinv2, hn), rinv3);
-  T = mul2(fma2(K.kc, q, mul2(dup2(-3.f), S)), rinv2);
+  if (ST) T = mul2(fma2(K.kc, q, mul2(dup2(-3.f), S)), rinv2);
   if (MODE == kNear) {
     const float2 u = mul2(r2, K.ku);
     if (u.x < 2.f || u.y < 2.f) {
@@ -525,7 +530,7 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
 #pragma unroll
       for (int k = kSerTerms - 2; k >= 0; --k) {
         sS = fma2(sS, u, dup2(cSer[k]));
-        if (k >= 1) sT = fma2(sT, u, dup2((float)k * cSer[k]));
+        if (ST && k >= 1) sT = fma2(sT, u, dup2((float)k * cSer[k]));
       }
       const float2 Ss = mul2(sS, K.is3), Ts = mul2(sT, K.is5);
       if (u.x < 2.f) {
@@ -540,7 +545,7 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
   }
 }
 
-template <int MODE, bool SELF>
+template <int MODE, bool SELF, bool ST>
 __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
                                              const float2* s4, int jb, int je, float2 tx, float2 ty, float2 tz,
                                              float2 gix, float2 giy, float2 giz, int self_lo, int self_hi,
@@ -556,8 +561,8 @@ __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1,
     const float2 kjx = make_float2(v3.x, v3.y), kjy = make_float2(v3.z, v3.w), kjz = v4;
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     float2 S, T;
-    pair_ST2<MODE>(r2, K, S, T);
-    float2 td = mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz))));
+    pair_ST2<MODE, ST>(r2, K, S, T);
+    float2 td = ST ? mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz)))) : dup2(0.f);
     if (SELF) {
       if (j == self_lo) {
         S.x = 0.f;
@@ -574,6 +579,7 @@ __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1,
     a.bx = fma2(S, kjx, a.bx);
     a.by = fma2(S, kjy, a.by);
     a.bz = fma2(S, kjz, a.bz);
+    if (!ST) continue;
     a.cx = fma2(td, gjx, a.cx);
     a.cy = fma2(td, gjy, a.cy);
     a.cz = fma2(td, gjz, a.cz);
@@ -586,7 +592,7 @@ __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1,
 // k_p2p for a uniform core width and two targets per lane, in the packed
 // form.  Same lists, classes, staging order and output as k_p2p<false, 2, SEG>;
 // the staged source holds its negated coordinates and every value twice.
-template <bool SEG>
+template <bool SEG, bool ST>
 __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, const int2* __restrict__ off,
                                                const int2* __restrict__ list, const int* __restrict__ begin,
                                                const int* __restrict__ end, const float4* __restrict__ cf,
@@ -710,15 +716,15 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       const float2* c4 = s4[buf];
       if (self) {
         const int slo = (t0 + lane) - cur_c0, shi = (t0 + lane + 32) - cur_c0;
-        run_chunk_x2<kNear, true>(c0, c1, c2, c3, c4, 0, cur_cnt, tx, ty, tz, gix, giy, giz, slo, shi, K, a);
+        run_chunk_x2<kNear, true, ST>(c0, c1, c2, c3, c4, 0, cur_cnt, tx, ty, tz, gix, giy, giz, slo, shi, K, a);
       } else {
         const int nfm = cur_nf + cur_nm;
         if (cur_nf > 0)
-          run_chunk_x2<kFar, false>(c0, c1, c2, c3, c4, 0, cur_nf, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+          run_chunk_x2<kFar, false, ST>(c0, c1, c2, c3, c4, 0, cur_nf, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
         if (cur_nm > 0)
-          run_chunk_x2<kMid, false>(c0, c1, c2, c3, c4, cur_nf, nfm, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+          run_chunk_x2<kMid, false, ST>(c0, c1, c2, c3, c4, cur_nf, nfm, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
         if (nfm < cur_cnt)
-          run_chunk_x2<kNear, false>(c0, c1, c2, c3, c4, nfm, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+          run_chunk_x2<kNear, false, ST>(c0, c1, c2, c3, c4, nfm, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
       }
       c_far += nt * (unsigned long long)cur_nf;
       c_mid += nt * (unsigned long long)cur_nm;
@@ -752,7 +758,7 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
         vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * ((az * X - ax * Z) - by) + duy;
         vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * ((ax * Y - ay * X) - bz) + duz;
       }
-      if (dg) {  // s = A x gamma_i + C x X_i - D
+      if (ST && dg) {  // s = A x gamma_i + C x X_i - D
         const float gx = gxs[q], gy = gys[q], gz = gzs[q];
         dg[3 * o] = far_s[3 * i] + kInv4Pi * ((ay * gz - az * gy) + (cy * Z - cz * Y) - ex);
         dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((az * gx - ax * gz) + (cz * X - cx * Z) - ey);
@@ -919,38 +925,45 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
   ++g_launches;
-#define FMM_P2P_LAUNCH(PS_, TPT_, SEG_)                                                                         \
-  k_p2p<PS_, TPT_, SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, \
-                                          margin0, K0, dip, cseg, sp, vel, dg, cnt)
   // the packed kernel stages 9 KB per warp: ask for the largest shared-memory carveout
   static bool carveout_set = false;
   if (!carveout_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute((const void*)k_p2p_x2<false>,
-                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    FMM_CUDA_TRY(cudaFuncSetAttribute((const void*)k_p2p_x2<true>,
-                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    const void* kx2[4] = {(const void*)k_p2p_x2<false, false>, (const void*)k_p2p_x2<false, true>,
+                          (const void*)k_p2p_x2<true, false>, (const void*)k_p2p_x2<true, true>};
+    for (const void* k : kx2)
+      FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     carveout_set = true;
   }
-#define FMM_P2P_X2_LAUNCH(SEG_)                                                                                \
-  k_p2p_x2<SEG_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf, margin0, \
-                                  K0, dip, cseg, sp, vel, dg, cnt)
-  if (cseg) {
-    if (two) {
-      if (ps) FMM_P2P_LAUNCH(true, 2, true);
-      else FMM_P2P_X2_LAUNCH(true);
-    } else {
-      if (ps) FMM_P2P_LAUNCH(true, 1, true);
-      else FMM_P2P_LAUNCH(false, 1, true);
-    }
-  } else {
-    if (two) {
-      if (ps) FMM_P2P_LAUNCH(true, 2, false);
-      else FMM_P2P_X2_LAUNCH(false);
-    } else {
-      if (ps) FMM_P2P_LAUNCH(true, 1, false);
-      else FMM_P2P_LAUNCH(false, 1, false);
-    }
-  }
+#define FMM_P2P_LAUNCH(PS_, TPT_, SEG_, ST_)                                                                 \
+  k_p2p<PS_, TPT_, SEG_, ST_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, \
+                                               smaxf, margin0, K0, dip, cseg, sp, vel, dg, cnt)
+#define FMM_P2P_X2_LAUNCH(SEG_, ST_)                                                                          \
+  k_p2p_x2<SEG_, ST_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf,     \
+                                       margin0, K0, dip, cseg, sp, vel, dg, cnt)
+#define FMM_P2P_ALL(ST_)                                       \
+  do {                                                         \
+    if (cseg) {                                                \
+      if (two) {                                               \
+        if (ps) FMM_P2P_LAUNCH(true, 2, true, ST_);            \
+        else FMM_P2P_X2_LAUNCH(true, ST_);                     \
+      } else {                                                 \
+        if (ps) FMM_P2P_LAUNCH(true, 1, true, ST_);            \
+        else FMM_P2P_LAUNCH(false, 1, true, ST_);              \
+      }                                                        \
+    } else {                                                   \
+      if (two) {                                               \
+        if (ps) FMM_P2P_LAUNCH(true, 2, false, ST_);           \
+        else FMM_P2P_X2_LAUNCH(false, ST_);                    \
+      } else {                                                 \
+        if (ps) FMM_P2P_LAUNCH(true, 1, false, ST_);           \
+        else FMM_P2P_LAUNCH(false, 1, false, ST_);             \
+      }                                                        \
+    }                                                          \
+  } while (0)
+  // without a stretching output the kernels skip T and the stretching sums
+  if (dg) FMM_P2P_ALL(true);
+  else FMM_P2P_ALL(false);
+#undef FMM_P2P_ALL
 #undef FMM_P2P_LAUNCH
 #undef FMM_P2P_X2_LAUNCH
   FMM_CUDA_TRY(cudaGetLastError());

@@ -236,17 +236,29 @@ __device__ inline void cell_ijk(uint64_t key, int l, long long ijk[3]) {
   ijk[2] = r[2];
 }
 
+// Integer coordinates of every cell, 21 bits each (x | y << 21 | z << 42).
+__global__ void k_cell_ijk(const int* __restrict__ level, const uint64_t* __restrict__ ckey, int nc,
+                           uint64_t* __restrict__ ijk) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  long long r[3];
+  cell_ijk(ckey[c], level[c], r);
+  ijk[c] = (uint64_t)r[0] | ((uint64_t)r[1] << 21) | ((uint64_t)r[2] << 42);
+}
+
 __global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __restrict__ level,
-                           const uint64_t* __restrict__ ckey, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           const uint64_t* __restrict__ cijk, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                            int* __restrict__ flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int4 v = raw[i];
   int la = level[v.x], lb = level[v.y];
   int lf = la > lb ? la : lb;
-  long long ia[3], ib[3];
-  cell_ijk(ckey[v.x], la, ia);
-  cell_ijk(ckey[v.y], lb, ib);
+  const uint64_t pa = cijk[v.x], pb = cijk[v.y];
+  const long long ia[3] = {(long long)(pa & 0x1FFFFFull), (long long)((pa >> 21) & 0x1FFFFFull),
+                           (long long)(pa >> 42)};
+  const long long ib[3] = {(long long)(pb & 0x1FFFFFull), (long long)((pb >> 21) & 0x1FFFFFull),
+                           (long long)(pb >> 42)};
   int o[3] = {v.z / 9 - 1, (v.z / 3) % 3 - 1, v.z % 3 - 1};
   long long t[3];
   bool ok = true;
@@ -625,7 +637,11 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       int* flag = p->flags.as<int>();
       // 1. full translation keys and their field ranges
       ++g_launches;
-      k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_key.as<uint64_t>(),
+      FMM_TRY(p->c_ijk.ensure((size_t)(nc + 1) * sizeof(uint64_t)));
+      ++g_launches;
+      k_cell_ijk<<<(unsigned)((nc + T - 1) / T), T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc,
+                                                           p->c_ijk.as<uint64_t>());
+      k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_ijk.as<uint64_t>(),
                                  p->m2l_key.as<uint64_t>(), p->lv0.as<uint32_t>(), flag);
       int* drng = reinterpret_cast<int*>(p->scal.as<double>() + kScalCount + 8);
       const int init[8] = {INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN};

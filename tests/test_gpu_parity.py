@@ -188,6 +188,34 @@ def test_packed_p2p_bitwise_equals_scalar_kernel(case):
     assert np.array_equal(u1, u2) and np.array_equal(s1, s2)
 
 
+@pytest.mark.parametrize("case", ["packed", "one-target-per-lane", "per-particle-sigma"])
+def test_velocity_only_matches_full_evaluation(case):
+    """Without a stretching output the pair kernels skip T and the stretching
+    sums; the velocity takes the same operations, so it must equal the full
+    evaluation's velocity bit for bit."""
+    import torch
+    from paper_1106_5273_gb300 import Params, Plan
+    sig = None
+    if case == "packed":
+        w = workloads.taylor_green(16)
+        kw = dict(p=8, theta=0.4, ncrit=64, periodic=1, box_min=w["box_min"], box_len=w["box_len"])
+    else:
+        w = workloads.plummer(4000)
+        w["sigma"] = np.float32(workloads.plummer_sigma(4000))
+        kw = dict(p=8, theta=0.5, ncrit=16 if case == "one-target-per-lane" else 48)
+        if case == "per-particle-sigma":
+            sig = to_dev((w["sigma"] * np.linspace(0.8, 1.2, 4000)).astype(np.float32))
+    n = w["pos"].shape[0]
+    plan = Plan(n, Params.default(**kw))
+    pos, gam = to_dev(w["pos"]), to_dev(w["gamma"])
+    u1, s1 = plan.eval(pos, gam, sigma=sig, sigma_uniform=float(w["sigma"]))
+    u2, s2 = plan.eval(pos, gam, sigma=sig, sigma_uniform=float(w["sigma"]), stretching=False)
+    torch.cuda.synchronize()
+    assert s2 is None and plan.stats().p2p_pairs > 0
+    assert torch.equal(u1, u2)
+    plan.close()
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 257])
 def test_edge_sizes(n):
     from oracle import direct as od
