@@ -513,7 +513,7 @@ def main():
             "e2e": {"value": job_value(n, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * n * 12), "d2h_bytes_per_step": int(2 * n * 12)},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": "k_p2p", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": "k_p2p_x2", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "flops_per_pair": P2P_FLOPS, "pairs_per_launch": pairs,
                          "pairs_by_class": {"near": st.p2p_pairs_near, "mid": st.p2p_pairs_mid,

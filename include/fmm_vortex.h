@@ -282,6 +282,27 @@ void fmm_plan_destroy(fmm_plan plan);
 const char* fmm_strerror(int code);
 
 /*
+ * Velocity at nt target points from ns source blobs (Sec. 5.2 compares the
+ * kinetic energy spectrum of the vortex-method field with the spectral
+ * method's, which needs the velocity on grid points that are not particles).
+ *   src_pos[ns][3], src_gamma[ns][3]   device float32 sources
+ *   src_sigma[ns] or NULL              per-source core widths, or sigma_uniform (> 0)
+ *   tgt_pos[nt][3]                     device float32 target points (inside the
+ *                                      periodic cube when the plan is periodic)
+ *   vel[nt][3]                         device float32 output
+ * The targets join the plan's tree as blobs of zero strength behind the
+ * sources (ns + nt <= n_max), so the result is the field of the sources alone
+ * evaluated by the same FMM; a target that coincides with a source gets the
+ * regularized field there.  Velocity only.  Per-source core widths: the
+ * targets take the largest source width, so the far-field separation and
+ * the pair classes are those of the sources.  Same stream and blocking
+ * behaviour as fmm_eval_velocity_stretching; FMM_E_INVAL for bad arguments.
+ */
+int fmm_eval_targets(fmm_plan plan, int64_t ns, const float* src_pos, const float* src_gamma,
+                     const float* src_sigma, float sigma_uniform, int64_t nt, const float* tgt_pos,
+                     float* vel, void* cuda_stream);
+
+/*
  * All-pairs direct sum of Eqs. (1)-(3) on the device, free space, without
  * a tree: the same P2P pair kernel over every (target, source) pair of one
  * array (the self pair excluded).  Device arrays as above.  O(n^2).

@@ -77,6 +77,7 @@ lib.fmm_plan_destroy.restype = None
 for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host"):
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
+lib.fmm_eval_targets.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _i64, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
 lib.fmm_selftest_bounded_wait.argtypes = [_i64, ctypes.c_int, _vp]
 lib.fmm_eval_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -156,6 +157,19 @@ class Plan:
             float(sigma_uniform), _dptr(vel, name="vel"), _dptr(dgamma, name="dgamma"),
             _stream_ptr(stream)), "fmm_eval_velocity_stretching")
         return vel, dgamma
+
+    def eval_targets(self, src_pos, src_gamma, tgt_pos, sigma=None, sigma_uniform=0.0, vel=None, stream=None):
+        """fmm_eval_targets on torch CUDA tensors: the velocity of the sources at the
+        target points; returns vel [nt, 3]."""
+        import torch
+        nt = tgt_pos.shape[0]
+        if vel is None:
+            vel = torch.empty((nt, 3), dtype=torch.float32, device=tgt_pos.device)
+        _check(lib.fmm_eval_targets(
+            self._h, src_pos.shape[0], _dptr(src_pos, name="src_pos"), _dptr(src_gamma, name="src_gamma"),
+            _dptr(sigma, name="sigma"), float(sigma_uniform), nt, _dptr(tgt_pos, name="tgt_pos"),
+            _dptr(vel, name="vel"), _stream_ptr(stream)), "fmm_eval_targets")
+        return vel
 
     def eval_host(self, pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, stream=None):
         """fmm_eval_velocity_stretching_host on numpy float32 arrays (synchronous)."""

@@ -71,6 +71,7 @@ struct fmm_plan_s {
   fmm::DBuf far_u, far_s;                // [n][3] far field, sorted order
   fmm::DBuf leaf_of;                     // [n]
   fmm::DBuf in_pos, in_gam, in_sig, out_vel, out_dg;  // staging of the _host entry point
+  fmm::DBuf t_pos, t_gam, t_sig, t_vel;                // sources + zero-strength targets (fmm_eval_targets)
   // cells
   fmm::DBuf c_begin, c_end, c_level, c_parent, c_child, c_nchild;  // int32
   fmm::DBuf c_key;                                                  // u64 level-local Morton index
