@@ -12,6 +12,8 @@
  *   T      = (c exp(-rho^2/2) / sigma_j^3 - 3 S) / r^2   ( = S'(r)/r )
  *   u_i   += S (gamma_j x d) / (4 pi)                                (Eq. 1)
  *   s_i   += [S (gamma_j x gamma_i) + T (gamma_i . d)(gamma_j x d)] / (4 pi)  (Eq. 3)
+ * or, with transpose != 0, the transpose scheme s = (grad u)^T gamma_i:
+ *   s_i   += [S (gamma_i x gamma_j) + T (gamma_i . (gamma_j x d)) d] / (4 pi)
  * For rho^2 < 1/4 the closed forms lose digits to cancellation, so S and T come
  * from the Taylor series of g(rho)/rho^3 in rho^2 (term-by-term integral of
  * g'(rho) = c rho^2 exp(-rho^2/2)).
@@ -74,10 +76,11 @@ void oracle_pair_ST(double r2, double sigma, double* S, double* T) { pair_ST(r2,
  * gt[nt,3] (needed for s only) from sources xs[ns,3], gs[ns,3], sig[ns].
  * img[nimg,3] are shifts added to d (nimg >= 1; pass one zero shift for free
  * space).  If skip_self, target i and source i are the same particle.
+ * transpose selects the stretching scheme (0 classical, 1 transpose).
  */
 void oracle_direct(int64_t nt, const double* xt, const double* gt, int64_t ns,
                    const double* xs, const double* gs, const double* sig,
-                   int64_t nimg, const double* img, int skip_self,
+                   int64_t nimg, const double* img, int skip_self, int transpose,
                    double* u, double* s) {
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < nt; ++i) {
@@ -100,8 +103,14 @@ void oracle_direct(int64_t nt, const double* xt, const double* gt, int64_t ns,
         ux += S * cx; uy += S * cy; uz += S * cz;
         /* gamma_j x gamma_i */
         double kx = gy * giz - gz * giy, ky = gz * gix - gx * giz, kz = gx * giy - gy * gix;
-        double td = T * (gix * dx + giy * dy + giz * dz);
-        sx += S * kx + td * cx; sy += S * ky + td * cy; sz += S * kz + td * cz;
+        if (transpose) {
+          /* gamma_i x gamma_j = -(gamma_j x gamma_i); gamma_i . (gamma_j x d) */
+          double tw = T * (gix * cx + giy * cy + giz * cz);
+          sx += tw * dx - S * kx; sy += tw * dy - S * ky; sz += tw * dz - S * kz;
+        } else {
+          double td = T * (gix * dx + giy * dy + giz * dz);
+          sx += S * kx + td * cx; sy += S * ky + td * cy; sz += S * kz + td * cz;
+        }
       }
     }
     u[3 * i] = ux * ORACLE_INV_4PI; u[3 * i + 1] = uy * ORACLE_INV_4PI; u[3 * i + 2] = uz * ORACLE_INV_4PI;

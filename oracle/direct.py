@@ -34,7 +34,7 @@ def _load():
         lib = ctypes.CDLL(_LIB)
         p = ctypes.POINTER(ctypes.c_double)
         lib.oracle_direct.argtypes = [ctypes.c_int64, p, p, ctypes.c_int64, p, p, p,
-                                      ctypes.c_int64, p, ctypes.c_int, p, p]
+                                      ctypes.c_int64, p, ctypes.c_int, ctypes.c_int, p, p]
         lib.oracle_direct.restype = None
         lib.oracle_pair_ST.argtypes = [ctypes.c_double, ctypes.c_double, p, p]
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -46,12 +46,14 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def direct(xt, gt, xs, gs, sigma, images=None, skip_self=False):
+def direct(xt, gt, xs, gs, sigma, images=None, skip_self=False, transpose=False):
     """u, s [nt,3] FP64 at targets xt (strengths gt) from all sources.
 
     sigma: scalar or [ns]; images: [nimg,3] shifts added to d (default: one
     zero shift); skip_self: targets are the sources, index for index, and the
-    zero-shift self pair is left out (its exact value is zero).
+    zero-shift self pair is left out (its exact value is zero); transpose: the
+    stretching in the transpose scheme (grad u)^T gamma instead of
+    (gamma . grad) u.
     """
     lib = _load()
     xt = np.ascontiguousarray(xt, np.float64).reshape(-1, 3)
@@ -68,7 +70,8 @@ def direct(xt, gt, xs, gs, sigma, images=None, skip_self=False):
     s = np.zeros((nt, 3))
     if nt and ns:
         lib.oracle_direct(nt, _ptr(xt), _ptr(gt), ns, _ptr(xs), _ptr(gs), _ptr(sig),
-                          images.shape[0], _ptr(images), 1 if skip_self else 0, _ptr(u), _ptr(s))
+                          images.shape[0], _ptr(images), 1 if skip_self else 0, 1 if transpose else 0,
+                          _ptr(u), _ptr(s))
     return u, s
 
 

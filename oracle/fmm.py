@@ -53,14 +53,18 @@ def lattice_far_local(M_root, box_len, p, images):
     return L
 
 
-def curl_and_stretch(grad, hess, gamma):
-    """u_l = eps_lmk d_m psi_k; s_l = gamma_n d_n u_l (psi = Phi/(4 pi))."""
+def curl_and_stretch(grad, hess, gamma, transpose=False):
+    """u_l = eps_lmk d_m psi_k; s_l = gamma_n d_n u_l (psi = Phi/(4 pi)), or the
+    transpose scheme s_n = gamma_l d_n u_l."""
     g = grad
     u = np.stack([g[:, 2, 1] - g[:, 1, 2], g[:, 0, 2] - g[:, 2, 0], g[:, 1, 0] - g[:, 0, 1]], 1)
     h = hess  # [n, pot, n_deriv, m_deriv]
     du = np.stack([h[:, 2, :, 1] - h[:, 1, :, 2], h[:, 0, :, 2] - h[:, 2, :, 0],
-                   h[:, 1, :, 0] - h[:, 0, :, 1]], 1)  # [n, l, n_deriv]
-    s = np.einsum("nld,nd->nl", du, gamma)
+                   h[:, 1, :, 0] - h[:, 0, :, 1]], 1)  # [n, l, n_deriv] = d u_l / d x_n
+    if transpose:
+        s = np.einsum("nld,nl->nd", du, gamma)
+    else:
+        s = np.einsum("nld,nd->nl", du, gamma)
     return u * INV_4PI, s * INV_4PI
 
 
@@ -69,8 +73,9 @@ class Result:
 
 
 def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=None,
-        box_len=None, images=3):
-    """FP64 FMM.  pos, gamma [n,3] (float32 values), sigma scalar or [n].
+        box_len=None, images=3, transpose=False):
+    """FP64 FMM.  pos, gamma [n,3] (float32 values), sigma scalar or [n];
+    transpose selects the transpose stretching scheme (grad u)^T gamma.
 
     Returns a Result with u, s [n,3] in input order and the tree / lists used.
     """
@@ -138,7 +143,7 @@ def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=No
     for c in np.nonzero(leaf)[0]:
         b, e = t.begin[c], t.end[c]
         grad, hess = cart.l2p_derivs(Lc[c], x[b:e] - t.center[c], p)
-        uf, sf = curl_and_stretch(grad, hess, g[b:e])
+        uf, sf = curl_and_stretch(grad, hess, g[b:e], transpose)
         us[b:e] += uf
         ss[b:e] += sf
         lst = by_target.get(int(c), [])
@@ -149,7 +154,7 @@ def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=No
             zero = np.concatenate([np.full(t.end[B] - t.begin[B], offs[o].any() == False)
                                    for B, o in lst])
             skip = (idx[None, :] == np.arange(b, e)[:, None]) & zero[None, :]
-            un, sn = pairs.pair_sum(x[b:e], g[b:e], x[idx], g[idx], sg[idx], shift, skip)
+            un, sn = pairs.pair_sum(x[b:e], g[b:e], x[idx], g[idx], sg[idx], shift, skip, transpose)
             us[b:e] += un
             ss[b:e] += sn
     if periodic:

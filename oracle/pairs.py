@@ -7,7 +7,9 @@ Reading of the paper used here (Sec. 2.1, Eqs. 1-3):
   * The cutoff of Eq. (2) uses the SOURCE core width sigma_j.
   * Eq. (3) is the classical scheme (gamma_i . grad) u evaluated at x_i, which
     for one pair gives S (gamma_j x gamma_i) + T (gamma_i . d)(gamma_j x d)
-    with S = g/r^3 and T = S'(r)/r.
+    with S = g/r^3 and T = S'(r)/r.  The transpose scheme (grad u)^T gamma_i
+    (the other reading of the gradient in Eq. 3) gives
+    S (gamma_i x gamma_j) + T (gamma_i . (gamma_j x d)) d.
 Near rho = 0 the closed forms cancel, so rho^2 < 1/4 uses the series of
 g(rho)/rho^3 (g'(rho) = c rho^2 exp(-rho^2/2), c = sqrt(2/pi), integrated
 term by term).  Parity pinned by tests/test_oracle_pins.py (blob quadrature,
@@ -77,12 +79,13 @@ def S_T(r2, sigma):
     return S, T
 
 
-def pair_sum(xt, gt, xs, gs, sig, shift=None, skip=None):
+def pair_sum(xt, gt, xs, gs, sig, shift=None, skip=None, transpose=False):
     """Velocity and stretching at targets xt[nt,3] (strengths gt) from sources.
 
     shift: per-source shift [ns,3] added to d = x_i - x_j (exact difference
     first, then the shift), or None.  skip: boolean [nt, ns] mask of pairs to
-    leave out (the self pair), or None.  Returns u[nt,3], s[nt,3] in FP64.
+    leave out (the self pair), or None.  transpose: the transpose stretching
+    scheme.  Returns u[nt,3], s[nt,3] in FP64.
     """
     xt = np.asarray(xt, np.float64)
     xs = np.asarray(xs, np.float64)
@@ -101,6 +104,10 @@ def pair_sum(xt, gt, xs, gs, sig, shift=None, skip=None):
     cr = np.cross(gj, d)
     u = np.einsum("ij,ijk->ik", S, cr)
     gg = np.cross(gj, np.broadcast_to(gt[:, None, :], d.shape))
-    dot = np.einsum("ik,ijk->ij", gt, d)
-    s = np.einsum("ij,ijk->ik", S, gg) + np.einsum("ij,ijk->ik", T * dot, cr)
+    if transpose:
+        trip = np.einsum("ik,ijk->ij", gt, cr)  # gamma_i . (gamma_j x d)
+        s = -np.einsum("ij,ijk->ik", S, gg) + np.einsum("ij,ijk->ik", T * trip, d)
+    else:
+        dot = np.einsum("ik,ijk->ij", gt, d)
+        s = np.einsum("ij,ijk->ik", S, gg) + np.einsum("ij,ijk->ik", T * dot, cr)
     return u * INV_4PI, s * INV_4PI

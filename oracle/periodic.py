@@ -35,8 +35,10 @@ import numpy as np
 from . import direct as _direct
 
 
-def fourier(xt, gt, xs, gs, sigma, box_len, nmax):
-    """u, s [nt,3] from the Fourier series over modes |n_a| <= nmax."""
+def fourier(xt, gt, xs, gs, sigma, box_len, nmax, transpose=False):
+    """u, s [nt,3] from the Fourier series over modes |n_a| <= nmax.  With
+    u = sum_k c_k e^{ik.x}: s = sum_k i (gamma.k) c_k e^{ik.x} (classical) or
+    s = sum_k i k (gamma.c_k) e^{ik.x} (transpose scheme)."""
     xt = np.asarray(xt, np.float64).reshape(-1, 3)
     gt = np.asarray(gt, np.float64).reshape(-1, 3)
     xs = np.asarray(xs, np.float64).reshape(-1, 3)
@@ -62,8 +64,12 @@ def fourier(xt, gt, xs, gs, sigma, box_len, nmax):
         coef = ikxG * dc[:, None]
         ph_t = np.exp(1j * (xt @ kc.T))  # [nt,nk]
         u += np.real(ph_t @ coef)
-        gk = 1j * (gt @ kc.T)  # [nt,nk]
-        s += np.real((ph_t * gk) @ coef)
+        if transpose:
+            gc = gt @ coef.T  # [nt,nk]: gamma . c_k
+            s += np.real((1j * ph_t * gc) @ kc)
+        else:
+            gk = 1j * (gt @ kc.T)  # [nt,nk]
+            s += np.real((ph_t * gk) @ coef)
     return u / V, s / V
 
 
@@ -110,10 +116,10 @@ def image_shifts(box_len, m):
     return o * float(box_len)
 
 
-def cubic_image_sum(xt, gt, xs, gs, sigma, box_len, m, skip_self=True):
+def cubic_image_sum(xt, gt, xs, gs, sigma, box_len, m, skip_self=True, transpose=False):
     """Direct regularized sum over the (2m+1)^3 images (cubic order)."""
     return _direct.direct(xt, gt, xs, gs, sigma, images=image_shifts(box_len, m),
-                          skip_self=skip_self)
+                          skip_self=skip_self, transpose=transpose)
 
 
 def dipole_velocity(xs, gs, box_len):

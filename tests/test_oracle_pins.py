@@ -148,6 +148,41 @@ def test_stretching_is_gamma_dot_grad_u():
         assert np.linalg.norm(sf - s[i]) < 1e-6 * np.linalg.norm(s[i]) + 1e-9
 
 
+def test_transpose_stretching_is_grad_u_transpose_gamma():
+    # The transpose reading of Eq. (3): s = (grad u)^T gamma_i, i.e.
+    # s_a = sum_l gamma_l d u_l / d x_a, against central differences of the
+    # oracle velocity (small rho pairs included).
+    c = workloads.random_cloud(12, seed=17, box=0.3)
+    x = c["pos"].astype(np.float64)
+    g = c["gamma"].astype(np.float64)
+    sig = 0.12
+    _, s = direct.direct(x, g, x, g, sig, skip_self=True, transpose=True)
+    eps = 1e-5
+    for i in range(x.shape[0]):
+        sf = np.zeros(3)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = eps
+            up, _ = direct.direct((x[i] + e)[None], g[i][None], x, g, sig)
+            um, _ = direct.direct((x[i] - e)[None], g[i][None], x, g, sig)
+            sf[a] = g[i] @ (up[0] - um[0]) / (2 * eps)
+        assert np.linalg.norm(sf - s[i]) < 1e-6 * np.linalg.norm(s[i]) + 1e-9
+
+
+def test_transpose_scheme_conserves_total_vorticity():
+    # With one core width the transpose pair terms are antisymmetric under i <-> j
+    # (S and T symmetric, gamma_i x gamma_j antisymmetric, d antisymmetric with a
+    # symmetric triple product), so the strengths' rates sum to zero; the
+    # classical scheme has no such identity.
+    c = workloads.random_cloud(80, seed=18, box=0.5)
+    x, g = c["pos"], c["gamma"]
+    _, st = direct.direct(x, g, x, g, 0.07, skip_self=True, transpose=True)
+    _, sc = direct.direct(x, g, x, g, 0.07, skip_self=True)
+    scale = np.abs(st).sum(0).max()
+    assert np.abs(st.sum(0)).max() < 1e-12 * scale
+    assert np.abs(sc.sum(0)).max() > 1e-3 * np.abs(sc).sum(0).max()
+
+
 def test_translation_and_rotation_covariance():
     c = workloads.random_cloud(40, seed=8)
     x = c["pos"].astype(np.float64)
@@ -174,6 +209,9 @@ def test_c_and_numpy_direct_agree():
     un, sn = pairs.pair_sum(x, g, x, g, sig, None, skip)
     assert np.allclose(u, un, rtol=1e-12, atol=1e-14 * np.abs(u).max())
     assert np.allclose(s, sn, rtol=1e-12, atol=1e-14 * np.abs(s).max())
+    _, st = direct.direct(x, g, x, g, sig, skip_self=True, transpose=True)
+    _, stn = pairs.pair_sum(x, g, x, g, sig, None, skip, transpose=True)
+    assert np.allclose(st, stn, rtol=1e-12, atol=1e-14 * np.abs(st).max())
 
 
 # ---------------------------------------------------------------- periodic ---
@@ -195,6 +233,15 @@ def test_cubic_image_sum_minus_dipole_converges_to_fourier():
         assert np.linalg.norm(uc - uf) / np.linalg.norm(uf) > 10 * errs[-1]
         assert np.linalg.norm(sc - sf) / np.linalg.norm(sf) < 2e-3
     assert errs[2] < 1.5e-4 and errs[0] > 2.5 * errs[1] > 6 * errs[2]
+    # the transpose scheme: the image sum converges to the Fourier series
+    # sum_k i k (gamma . c_k) e^{ik.x} (a uniform velocity changes no gradient)
+    _, sft = periodic.fourier(x, g, x, g, sig, L, 12, transpose=True)
+    terr = []
+    for m in (4, 16):
+        _, sct = periodic.cubic_image_sum(x, g, x, g, sig, L, m, transpose=True)
+        terr.append(np.linalg.norm(sct - sft) / np.linalg.norm(sft))
+    assert terr[1] < 2e-3 and terr[1] < terr[0]
+    assert np.linalg.norm(sft - sf) > 0.1 * np.linalg.norm(sf)  # a different field than the classical one
 
 
 def test_taylor_green_closed_form_matches_fourier():
@@ -388,6 +435,11 @@ def test_fmm_matches_direct_sum_and_converges():
                      np.linalg.norm(r.s - sd) / np.linalg.norm(sd)))
     assert errs[0][0] > errs[1][0] > errs[2][0]
     assert errs[2][0] < 1e-4 and errs[2][1] < 3e-4
+    # transpose scheme: the far field from the Hessian, the near field from the pair terms
+    _, sdt = direct.direct(x, g, x, g, sig, skip_self=True, transpose=True)
+    terr = [np.linalg.norm(fmm.fmm(x, g, sig, p, 0.5, 8, ksig=3.0, transpose=True).s - sdt) / np.linalg.norm(sdt)
+            for p in (3, 7)]
+    assert terr[1] < 3e-4 and terr[1] < 0.3 * terr[0]
     # the near field alone (no M2L accepted) is the direct sum
     r = fmm.fmm(x, g, sig, 3, 1e-6, 8)
     assert len(r.m2l) == 0
