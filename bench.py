@@ -226,11 +226,12 @@ def serving_inputs(specs):
     return out
 
 
-def serve_stream(specs, inputs, workers, batching, budget):
-    """Submit every request at its arrival time; per-request latency = completion - arrival."""
+def serve_stream(specs, inputs, workers, batching, budget, ncrit=64):
+    """Submit every request at its arrival time; per-request latency = completion - arrival.
+    ncrit = 0: the server autotunes the leaf size per class on the warm-up requests."""
     import numpy as np
     from paper_1106_5273_gb300 import Server
-    srv = Server(workers=workers, batching=batching, theta=0.5, ncrit=64, hbm_budget_bytes=budget,
+    srv = Server(workers=workers, batching=batching, theta=0.5, ncrit=ncrit, hbm_budget_bytes=budget,
                  max_batch_particles=16 << 20)
     # warm-up (untimed): one request of every class creates the plans and operator caches
     seen = {}
@@ -279,27 +280,30 @@ def run_serving(args, horizon=None):
     specs = workloads.request_specs(rate=args.serving_rate, horizon_s=horizon, orders=SERVING_ORDERS)
     inputs = serving_inputs(specs)
     budget = 200 << 30
-    served = serve_stream(specs, inputs, 2, 1, budget)
-    plain = serve_stream(specs, inputs, 1, 0, budget)
+    served = serve_stream(specs, inputs, 2, 1, budget, ncrit=0)
+    plain = serve_stream(specs, inputs, 1, 0, budget, ncrit=64)
     return {"stream": "Poisson %.0f req/s for %.1f s (%d requests, %d particles), N log-uniform [1e4, 4e6], "
                       "p in {4,8,12}, 30%% periodic spectrum / 70%% Plummer, host arrays in and out"
                       % (args.serving_rate, horizon, len(specs), served["particles"]),
             "continuous_batching": served, "one_request_per_call": plain,
+            "ncrit": "continuous batching: autotuned per (p, periodic) class on the warm-up requests; "
+                     "one request per call: 64",
             "speedup_particles_per_s": served["particles_per_s"] / plain["particles_per_s"],
             "p99_ratio": plain["latency_ms"]["p99"] / served["latency_ms"]["p99"]}
 
 
 def run_batched(args):
     """512 independent free-space problems (N log-uniform [1e3, 1e6], ball or Plummer, p in
-    {4, 8, 12}, theta 0.5, ncrit 64): one fmm_eval_batch per order against one
-    fmm_eval_velocity_stretching per problem; inputs resident in HBM.  A step evaluates all 512
+    {4, 8, 12}, theta 0.5): one fmm_eval_batch per order, leaf size autotuned per order on a
+    sample of its problems (untimed), against one fmm_eval_velocity_stretching per problem
+    (ncrit 64); inputs resident in HBM.  A step evaluates all 512
     problems: the three order groups run one after the other (each group's plan is created before
     its timed evaluations and released after them, so one group's workspace is held at a time);
     the step time is the sum of the groups' mean times."""
     import numpy as np
     import torch
     import workloads
-    from paper_1106_5273_gb300 import Params, Plan, kernel_launch_count
+    from paper_1106_5273_gb300 import Params, Plan, autotune_ncrit, kernel_launch_count
     specs = workloads.batch_specs()
     groups = {}
     for sp in specs:
@@ -339,8 +343,15 @@ def run_batched(args):
         sig = np.array([w["sigma"] for w in probs], np.float32)
         del probs
         vel, dg = torch.empty_like(pos), torch.empty_like(pos)
+        # leaf size measured on a sample of the group (its first 24 problems; not timed)
+        ns = min(24, len(off) - 1)
+        tuned, tune_ms = autotune_ncrit(Params.default(p=p, theta=0.5, ncrit=64), off[:ns + 1],
+                                        pos[:int(off[ns])], gam[:int(off[ns])], sig[:ns])
         plan = Plan(n, Params.default(p=p, theta=0.5, ncrit=64))
         fb = lambda: plan.eval_batch(off, pos, gam, sigma_prob=sig, vel=vel, dgamma=dg)
+        t64, _ = timed(fb, steps, warm)
+        plan.close()
+        plan = Plan(n, Params.default(p=p, theta=0.5, ncrit=tuned))
         tb, lb = timed(fb, steps, warm)
         st = plan.stats()
         dev_bytes = plan.device_bytes()
@@ -360,6 +371,7 @@ def run_batched(args):
         l_b += lb
         l_p += lp
         per_group[str(p)] = {"problems": len(lst), "n": n, "batched_ms": tb, "one_per_call_ms": tp,
+                             "ncrit": tuned, "batched_ncrit64_ms": t64, "autotune_sample_ms": tune_ms,
                              "m2l_tensor": st.m2l_tensor, "p2p_pairs": st.p2p_pairs, "m2l_pairs": st.m2l_pairs,
                              "m2l_keys": st.m2l_keys, "device_bytes": dev_bytes}
         del pos, gam, vel, dg
@@ -369,7 +381,8 @@ def run_batched(args):
             "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": t_b,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched-512-free-space", "problems": len(specs), "n_total": ntot,
-                       "n_range": [1000, 1000000], "theta": 0.5, "ncrit": 64,
+                       "n_range": [1000, 1000000], "theta": 0.5,
+                       "ncrit": "autotuned per order on the group's first 24 problems (one per call: 64)",
                        "l2": "flushed (512 MB write) before every timed evaluation"},
             "gpu_launches": l_b, "groups": per_group,
             "one_problem_per_call": {"value": ntot / (t_p * 1e-3), "ms_per_step": t_p, "gpu_launches": l_p},

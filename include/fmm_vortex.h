@@ -41,7 +41,12 @@ enum {
   FMM_E_CUDA = -6      /* a CUDA runtime call failed (sticky device error etc.) */
 };
 
-enum { FMM_OUT_VELOCITY = 1, FMM_OUT_STRETCHING = 2 };
+/* fmm_params.outputs.  FMM_OUT_STRETCHING_TRANSPOSE selects the transpose
+ * scheme for dgamma: s_i = (grad u)^T gamma_i, the other reading of the
+ * gradient in Eq. 3 (pair term S (gamma_i x gamma_j) + T (gamma_i . (gamma_j x d)) d;
+ * with one core width it conserves the total vorticity exactly).  Without it
+ * dgamma is the classical (gamma_i . grad) u. */
+enum { FMM_OUT_VELOCITY = 1, FMM_OUT_STRETCHING = 2, FMM_OUT_STRETCHING_TRANSPOSE = 4 };
 
 /* How M2L products are computed. */
 enum {
@@ -67,8 +72,9 @@ typedef struct fmm_plan_s* fmm_plan;
  *   box_min, box_len   the periodic cube; ignored if !periodic.
  *   sigma_sep  k_sigma: M2L also needs |X_A-X_B| - R_A - R_B >= k_sigma *
  *              max sigma, because the far field uses the singular kernel.
- *   outputs    FMM_OUT_VELOCITY | FMM_OUT_STRETCHING (informational; a
- *              NULL output pointer skips that output).
+ *   outputs    FMM_OUT_VELOCITY | FMM_OUT_STRETCHING, optionally
+ *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
+ *              output pointer skips that output.
  *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR.
  */
 typedef struct {
@@ -180,6 +186,22 @@ int fmm_eval_batch(fmm_plan plan, int32_t nprob, const int64_t* offsets, const f
                    const float* sigma, const float* sigma_prob, const double* boxes, float* vel,
                    float* dgamma, void* cuda_stream);
 
+/*
+ * Leaf-size autotuner for the batched and serving forms (the paper fixes the
+ * leaf size by hand; this measures it).  For each of the ncand candidate
+ * values of ncrit, a plan with base's other parameters evaluates the sample
+ * batch (arguments as fmm_eval_batch, one core width per problem): one
+ * untimed evaluation, then `reps` evaluations timed with CUDA events on
+ * cuda_stream.  *best_ncrit receives the fastest candidate; ms_out[ncand]
+ * (HOST, may be NULL) the mean milliseconds of each.  Allocates and frees
+ * its own plans and output buffers; synchronous.  FMM_E_INVAL for bad
+ * arguments (ncand >= 1, 1 <= reps <= 100, candidates in 1..4096).
+ */
+int fmm_autotune_ncrit(const fmm_params* base, int32_t nprob, const int64_t* offsets, const float* pos,
+                       const float* gamma, const float* sigma_prob, const double* boxes,
+                       const int32_t* candidates, int32_t ncand, int32_t reps, int32_t* best_ncrit,
+                       double* ms_out, void* cuda_stream);
+
 /* Bytes of device memory the plan holds now (its workspace grows to the
  * largest evaluation seen and is kept for the next one). */
 int64_t fmm_plan_device_bytes(fmm_plan plan);
@@ -221,7 +243,8 @@ typedef struct {
   int64_t max_batch_particles;  /* particles per batch (a larger single request runs alone) */
   int32_t max_batch_problems;   /* requests per batch, 1..FMM_BATCH_MAX */
   float theta;                  /* as fmm_params; shared by every request */
-  int32_t ncrit;
+  int32_t ncrit;                /* leaf capacity; 0: autotuned per (p, periodic) class on its
+                                   first batch (fmm_autotune_ncrit over 32 ... 256) */
   float sigma_sep;
   int32_t images;
   int32_t m2l_mode;

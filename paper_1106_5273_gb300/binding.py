@@ -14,7 +14,7 @@ library_path = os.path.join(HERE, "_lib", "libfmm_vortex.so")
 
 FMM_OK = 0
 FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
-FMM_OUT_VELOCITY, FMM_OUT_STRETCHING = 1, 2
+FMM_OUT_VELOCITY, FMM_OUT_STRETCHING, FMM_OUT_STRETCHING_TRANSPOSE = 1, 2, 4
 
 
 class FmmError(RuntimeError):
@@ -78,6 +78,8 @@ for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_eval_targets.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _i64, _vp, _vp, _vp]
+lib.fmm_autotune_ncrit.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
 lib.fmm_selftest_bounded_wait.argtypes = [_i64, ctypes.c_int, _vp]
 lib.fmm_eval_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -295,6 +297,25 @@ def direct(pos, gamma, sigma=None, sigma_uniform=0.0, vel=None, dgamma=None, str
 
 
 # ---------------------------------------------------------------- serving loop
+
+def autotune_ncrit(params, offsets, pos, gamma, sigma_prob, boxes=None, candidates=(32, 48, 64, 96, 128, 192, 256),
+                   reps=1, stream=None):
+    """fmm_autotune_ncrit on a sample batch (torch CUDA tensors, host offsets /
+    sigma_prob / boxes as for Plan.eval_batch); returns (best ncrit, {ncrit: ms})."""
+    import numpy as np
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    sp = np.ascontiguousarray(sigma_prob, dtype=np.float32)
+    bx = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64)
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    ms = np.zeros(cand.shape[0], np.float64)
+    best = ctypes.c_int32(0)
+    _check(lib.fmm_autotune_ncrit(ctypes.byref(params), off.shape[0] - 1, off.ctypes.data, _dptr(pos, name="pos"),
+                                  _dptr(gamma, name="gamma"), sp.ctypes.data,
+                                  None if bx is None else bx.ctypes.data, cand.ctypes.data, cand.shape[0],
+                                  int(reps), ctypes.byref(best), ms.ctypes.data, _stream_ptr(stream)),
+           "fmm_autotune_ncrit")
+    return int(best.value), {int(c): float(m) for c, m in zip(cand, ms)}
+
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("batching", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),

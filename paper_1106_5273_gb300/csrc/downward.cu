@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, cons
                                             const int* __restrict__ cseg,
                                             const float4* __restrict__ A, const float4* __restrict__ B,
                                             const float* __restrict__ L, const float* __restrict__ Wg, int p,
-                                            float* __restrict__ far_u, float* __restrict__ far_s) {
+                                            int transpose, float* __restrict__ far_u, float* __restrict__ far_s) {
   extern __shared__ float sm[];
   const int P = p * p;
   float* sL = sm;           // [3][P]
@@ -156,11 +156,22 @@ __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, cons
     float ux = G[2][1] - G[1][2], uy = G[0][2] - G[2][0], uz = G[1][0] - G[0][1];
     const float gv[3] = {g.x, g.y, g.z};
     float sx = 0.f, sy = 0.f, sz = 0.f;
+    if (transpose) {  // s_d = sum_l gamma_l d u_l / d x_d
+      float sd[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      sx += gv[d] * (H[2][d][1] - H[1][d][2]);
-      sy += gv[d] * (H[0][d][2] - H[2][d][0]);
-      sz += gv[d] * (H[1][d][0] - H[0][d][1]);
+      for (int d = 0; d < 3; ++d)
+        sd[d] = gv[0] * (H[2][d][1] - H[1][d][2]) + gv[1] * (H[0][d][2] - H[2][d][0]) +
+                gv[2] * (H[1][d][0] - H[0][d][1]);
+      sx = sd[0];
+      sy = sd[1];
+      sz = sd[2];
+    } else {  // s_l = sum_d gamma_d d u_l / d x_d
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        sx += gv[d] * (H[2][d][1] - H[1][d][2]);
+        sy += gv[d] * (H[0][d][2] - H[2][d][0]);
+        sz += gv[d] * (H[1][d][0] - H[0][d][1]);
+      }
     }
     far_u[3 * j] = ux * c4;
     far_u[3 * j + 1] = uy * c4;
@@ -189,7 +200,7 @@ int downward_pass(fmm_plan p, int64_t n, cudaStream_t s) {
       p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(), p->c_center.as<double>(),
       p->batched ? p->seg_box.as<double>() : p->scal.as<double>(), p->batched ? p->c_seg.as<int>() : nullptr,
       p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_w.as<float>(),
-      p->prm.p, p->far_u.as<float>(), p->far_s.as<float>());
+      p->prm.p, (p->prm.outputs & FMM_OUT_STRETCHING_TRANSPOSE) ? 1 : 0, p->far_u.as<float>(), p->far_s.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

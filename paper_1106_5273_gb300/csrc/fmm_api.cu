@@ -25,6 +25,7 @@ int check_params(const fmm_params* q) {
   if (q->periodic && (q->images < 1 || q->images > 8 || !(q->box_len > 0.0))) return FMM_E_INVAL;
   if (!(q->sigma_sep >= 0.f)) return FMM_E_INVAL;
   if (q->m2l_mode < FMM_M2L_AUTO || q->m2l_mode > FMM_M2L_TENSOR) return FMM_E_INVAL;
+  if (q->outputs & ~(FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE)) return FMM_E_INVAL;
   return FMM_OK;
 }
 

@@ -12,6 +12,8 @@
 //   T = (c q / sigma^3 - 3 S) / r^2 = S'(r)/r
 //   u_i += S (gamma_j x d)                                            (Eq. 1)
 //   s_i += S (gamma_j x gamma_i) + T (gamma_i . d)(gamma_j x d)       (Eq. 3)
+//   or, transpose scheme (grad u)^T gamma_i:
+//   s_i += S (gamma_i x gamma_j) + T (gamma_i . (gamma_j x d)) d
 // The gamma_j x gamma_i part is summed as (sum_j S gamma_j) x gamma_i.  The
 // self pair is skipped explicitly (its exact value is zero).  Periodic image
 // pairs form the exact FP32 difference first and then add the image shift.
@@ -92,9 +94,9 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   return k;
 }
 
-// S = g/r^3 and T = S'(r)/r for one pair (see the file header); ST = false:
+// S = g/r^3 and T = S'(r)/r for one pair (see the file header); ST = 0:
 // S only (velocity without stretching).
-template <int MODE, bool ST = true>
+template <int MODE, int ST = 1>
 __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float& T) {
   const float rinv = rsqrt_approx(r2);
   const float rinv2 = rinv * rinv;
@@ -156,13 +158,17 @@ __device__ __forceinline__ void pair_acc(float dx, float dy, float dz, const flo
 // source,  sum_j S (gamma_j x d) = A x X_i - B  and
 // sum_j T (gamma_i . d)(gamma_j x d) = C x X_i - D, where
 // A = sum S gamma_j, B = sum S k_j, C = sum td gamma_j, D = sum td k_j, td = T (gamma_i . d).
+// Transpose scheme: with m_i = X_i x gamma_i, w = T gamma_i . (gamma_j x d) = T (gamma_j . m_i -
+// gamma_i . k_j); C.x = sum w, D = sum w X_j, and s = gamma_i x A + (sum w) X_i - D.
 struct AccR {
   float ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz;
 };
 
-template <int MODE, bool ST>
-__device__ __forceinline__ void pair_acc_rel(float dx, float dy, float dz, const float4& gj, const float4& kj,
-                                             float gix, float giy, float giz, const SigK& K, AccR& a) {
+// ST: 0 velocity only, 1 classical stretching, 2 transpose stretching.
+template <int MODE, int ST>
+__device__ __forceinline__ void pair_acc_rel(float dx, float dy, float dz, const float4& xj, const float4& gj,
+                                             const float4& kj, float gix, float giy, float giz, float mix,
+                                             float miy, float miz, const SigK& K, AccR& a) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   float S, T;
   pair_ST<MODE, ST>(r2, K, S, T);
@@ -172,7 +178,16 @@ __device__ __forceinline__ void pair_acc_rel(float dx, float dy, float dz, const
   a.bx = fmaf(S, kj.x, a.bx);
   a.by = fmaf(S, kj.y, a.by);
   a.bz = fmaf(S, kj.z, a.bz);
-  if (!ST) return;
+  if (ST == 0) return;
+  if (ST == 2) {
+    const float e = fmaf(-giz, kj.z, fmaf(-giy, kj.y, fmaf(-gix, kj.x, fmaf(gj.x, mix, fmaf(gj.y, miy, gj.z * miz)))));
+    const float w = T * e;
+    a.cx += w;
+    a.dx = fmaf(w, xj.x, a.dx);
+    a.dy = fmaf(w, xj.y, a.dy);
+    a.dz = fmaf(w, xj.z, a.dz);
+    return;
+  }
   const float td = T * fmaf(gix, dx, fmaf(giy, dy, giz * dz));
   a.cx = fmaf(td, gj.x, a.cx);
   a.cy = fmaf(td, gj.y, a.cy);
@@ -185,11 +200,12 @@ __device__ __forceinline__ void pair_acc_rel(float dx, float dy, float dz, const
 template <int TPT>
 struct TgtR {
   float x[TPT], y[TPT], z[TPT], gx[TPT], gy[TPT], gz[TPT];  // X_i (leaf-relative) and gamma_i
+  float mx[TPT], my[TPT], mz[TPT];                          // m_i = X_i x gamma_i (transpose scheme)
   int self[TPT];
   AccR a[TPT];
 };
 
-template <bool PS, int MODE, bool SELF, int TPT, bool ST>
+template <bool PS, int MODE, bool SELF, int TPT, int ST>
 __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
                                               int jb, int je, TgtR<TPT>& t, const SigK& K0) {
 #pragma unroll 4
@@ -200,8 +216,8 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       if (SELF && j == t.self[q]) continue;
-      pair_acc_rel<MODE, ST>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, gj, kj, t.gx[q], t.gy[q], t.gz[q],
-                         PS ? sK[j] : K0, t.a[q]);
+      pair_acc_rel<MODE, ST>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, xj, gj, kj, t.gx[q], t.gy[q], t.gz[q],
+                             t.mx[q], t.my[q], t.mz[q], PS ? sK[j] : K0, t.a[q]);
     }
   }
 }
@@ -209,7 +225,7 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
 // The groups of a staged chunk: sources [0, nf) far, [nf, nf + nm) mid, the
 // rest near; the self entry (not grouped) runs the near form with the self
 // pair skipped.
-template <bool PS, int TPT, bool ST>
+template <bool PS, int TPT, int ST>
 __device__ __forceinline__ void dispatch_rel(bool self, int nf, int nm, const float4* sA, const float4* sB,
                                              const float4* sC, const SigK* sK, int cnt, TgtR<TPT>& t,
                                              const SigK& K0) {
@@ -316,8 +332,8 @@ __device__ __forceinline__ void run_chunk(const float4* sA, const float4* sB, co
 // the target leaf centre.
 // SEG: a batch of problems; the leaf's problem supplies sigma, the class
 // bounds, the image shift and the dipole correction instead of the arguments.
-// ST = false: velocity only (dg is not written).
-template <bool PS, int TPT, bool SEG, bool ST>
+// ST: 0 velocity only (dg is not written), 1 classical, 2 transpose stretching.
+template <bool PS, int TPT, bool SEG, int ST>
 __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
                                             const int2* __restrict__ list, const int* __restrict__ begin,
                                             const int* __restrict__ end, const float4* __restrict__ cf,
@@ -389,6 +405,9 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       t.gx[q] = gi.x;
       t.gy[q] = gi.y;
       t.gz[q] = gi.z;
+      t.mx[q] = t.y[q] * gi.z - t.z[q] * gi.y;
+      t.my[q] = t.z[q] * gi.x - t.x[q] * gi.z;
+      t.mz[q] = t.x[q] * gi.y - t.y[q] * gi.x;
       t.a[q] = AccR{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     }
     const unsigned long long nt = (unsigned long long)min(CH, te - t0);
@@ -460,11 +479,17 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
         vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * ((a.az * X - a.ax * Z) - a.by) + duy;
         vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * ((a.ax * Y - a.ay * X) - a.bz) + duz;
       }
-      if (ST && dg) {  // s = A x gamma_i + C x X_i - D
+      if (ST == 1 && dg) {  // s = A x gamma_i + C x X_i - D
         const float gx = t.gx[q], gy = t.gy[q], gz = t.gz[q];
         dg[3 * o] = far_s[3 * i] + kInv4Pi * ((a.ay * gz - a.az * gy) + (a.cy * Z - a.cz * Y) - a.dx);
         dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((a.az * gx - a.ax * gz) + (a.cz * X - a.cx * Z) - a.dy);
         dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((a.ax * gy - a.ay * gx) + (a.cx * Y - a.cy * X) - a.dz);
+      }
+      if (ST == 2 && dg) {  // s = gamma_i x A + W X_i - D (W = C.x)
+        const float gx = t.gx[q], gy = t.gy[q], gz = t.gz[q];
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((gy * a.az - gz * a.ay) + (a.cx * X - a.dx));
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((gz * a.ax - gx * a.az) + (a.cx * Y - a.dy));
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((gx * a.ay - gy * a.ax) + (a.cx * Z - a.dz));
       }
     }
   }
@@ -507,7 +532,7 @@ struct AccR2 {
 };
 
 // S and T of two pairs (see pair_ST).
-template <int MODE, bool ST>
+template <int MODE, int ST>
 __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, float2& T) {
   const float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
   const float2 rinv2 = mul2(rinv, rinv);
@@ -545,11 +570,17 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
   }
 }
 
-template <int MODE, bool SELF, bool ST>
+// Transpose scheme (ST = 2): cx accumulates W = sum w and dx, dy, dz the sum
+// of w (-X_j) (the staged coordinates are negated), mx.. = m_i, ngx.. = -gamma_i.
+struct TgtT2 {
+  float2 mx, my, mz, ngx, ngy, ngz;
+};
+
+template <int MODE, bool SELF, int ST>
 __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
                                              const float2* s4, int jb, int je, float2 tx, float2 ty, float2 tz,
-                                             float2 gix, float2 giy, float2 giz, int self_lo, int self_hi,
-                                             const SigK2& K, AccR2& a) {
+                                             float2 gix, float2 giy, float2 giz, const TgtT2& tt, int self_lo,
+                                             int self_hi, const SigK2& K, AccR2& a) {
 #pragma unroll 4
   for (int j = jb; j < je; ++j) {
     const float4 v0 = s0[j], v1 = s1[j], v2 = s2[j], v3 = s3[j];
@@ -562,7 +593,11 @@ __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1,
     const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     float2 S, T;
     pair_ST2<MODE, ST>(r2, K, S, T);
-    float2 td = ST ? mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz)))) : dup2(0.f);
+    float2 td = dup2(0.f);
+    if (ST == 1) td = mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz))));
+    if (ST == 2)
+      td = mul2(T, fma2(tt.ngz, kjz, fma2(tt.ngy, kjy, fma2(tt.ngx, kjx, fma2(gjx, tt.mx, fma2(gjy, tt.my,
+                                                                                            mul2(gjz, tt.mz)))))));
     if (SELF) {
       if (j == self_lo) {
         S.x = 0.f;
@@ -579,7 +614,14 @@ __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1,
     a.bx = fma2(S, kjx, a.bx);
     a.by = fma2(S, kjy, a.by);
     a.bz = fma2(S, kjz, a.bz);
-    if (!ST) continue;
+    if (ST == 0) continue;
+    if (ST == 2) {  // td holds w
+      a.cx = add2(a.cx, td);
+      a.dx = fma2(td, make_float2(v0.x, v0.y), a.dx);
+      a.dy = fma2(td, make_float2(v0.z, v0.w), a.dy);
+      a.dz = fma2(td, make_float2(v1.x, v1.y), a.dz);
+      continue;
+    }
     a.cx = fma2(td, gjx, a.cx);
     a.cy = fma2(td, gjy, a.cy);
     a.cz = fma2(td, gjz, a.cz);
@@ -592,7 +634,7 @@ __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1,
 // k_p2p for a uniform core width and two targets per lane, in the packed
 // form.  Same lists, classes, staging order and output as k_p2p<false, 2, SEG>;
 // the staged source holds its negated coordinates and every value twice.
-template <bool SEG, bool ST>
+template <bool SEG, int ST>
 __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, const int2* __restrict__ off,
                                                const int2* __restrict__ list, const int* __restrict__ begin,
                                                const int* __restrict__ end, const float4* __restrict__ cf,
@@ -670,6 +712,22 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
     const float2 tx = make_float2(xs[0], xs[1]), ty = make_float2(ys[0], ys[1]), tz = make_float2(zs[0], zs[1]);
     const float2 gix = make_float2(gxs[0], gxs[1]), giy = make_float2(gys[0], gys[1]),
                  giz = make_float2(gzs[0], gzs[1]);
+    TgtT2 tt;
+    if (ST == 2) {
+      float m[3][2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        m[0][q] = ys[q] * gzs[q] - zs[q] * gys[q];
+        m[1][q] = zs[q] * gxs[q] - xs[q] * gzs[q];
+        m[2][q] = xs[q] * gys[q] - ys[q] * gxs[q];
+      }
+      tt.mx = make_float2(m[0][0], m[0][1]);
+      tt.my = make_float2(m[1][0], m[1][1]);
+      tt.mz = make_float2(m[2][0], m[2][1]);
+      tt.ngx = make_float2(-gxs[0], -gxs[1]);
+      tt.ngy = make_float2(-gys[0], -gys[1]);
+      tt.ngz = make_float2(-gzs[0], -gzs[1]);
+    }
     AccR2 a;
     a.ax = a.ay = a.az = a.bx = a.by = a.bz = a.cx = a.cy = a.cz = a.dx = a.dy = a.dz = dup2(0.f);
     const unsigned long long nt = (unsigned long long)min(CH, te - t0);
@@ -716,15 +774,18 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       const float2* c4 = s4[buf];
       if (self) {
         const int slo = (t0 + lane) - cur_c0, shi = (t0 + lane + 32) - cur_c0;
-        run_chunk_x2<kNear, true, ST>(c0, c1, c2, c3, c4, 0, cur_cnt, tx, ty, tz, gix, giy, giz, slo, shi, K, a);
+        run_chunk_x2<kNear, true, ST>(c0, c1, c2, c3, c4, 0, cur_cnt, tx, ty, tz, gix, giy, giz, tt, slo, shi, K,
+                                      a);
       } else {
         const int nfm = cur_nf + cur_nm;
         if (cur_nf > 0)
-          run_chunk_x2<kFar, false, ST>(c0, c1, c2, c3, c4, 0, cur_nf, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+          run_chunk_x2<kFar, false, ST>(c0, c1, c2, c3, c4, 0, cur_nf, tx, ty, tz, gix, giy, giz, tt, -1, -1, K, a);
         if (cur_nm > 0)
-          run_chunk_x2<kMid, false, ST>(c0, c1, c2, c3, c4, cur_nf, nfm, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+          run_chunk_x2<kMid, false, ST>(c0, c1, c2, c3, c4, cur_nf, nfm, tx, ty, tz, gix, giy, giz, tt, -1, -1, K,
+                                        a);
         if (nfm < cur_cnt)
-          run_chunk_x2<kNear, false, ST>(c0, c1, c2, c3, c4, nfm, cur_cnt, tx, ty, tz, gix, giy, giz, -1, -1, K, a);
+          run_chunk_x2<kNear, false, ST>(c0, c1, c2, c3, c4, nfm, cur_cnt, tx, ty, tz, gix, giy, giz, tt, -1, -1,
+                                         K, a);
       }
       c_far += nt * (unsigned long long)cur_nf;
       c_mid += nt * (unsigned long long)cur_nm;
@@ -758,7 +819,13 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
         vel[3 * o + 1] = far_u[3 * i + 1] + kInv4Pi * ((az * X - ax * Z) - by) + duy;
         vel[3 * o + 2] = far_u[3 * i + 2] + kInv4Pi * ((ax * Y - ay * X) - bz) + duz;
       }
-      if (ST && dg) {  // s = A x gamma_i + C x X_i - D
+      if (ST == 2 && dg) {  // s = gamma_i x A + W X_i + (sum w (-X_j)), W = C.x
+        const float gx = gxs[q], gy = gys[q], gz = gzs[q];
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((gy * az - gz * ay) + (cx * X + ex));
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((gz * ax - gx * az) + (cx * Y + ey));
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((gx * ay - gy * ax) + (cx * Z + ez));
+      }
+      if (ST == 1 && dg) {  // s = A x gamma_i + C x X_i - D
         const float gx = gxs[q], gy = gys[q], gz = gzs[q];
         dg[3 * o] = far_s[3 * i] + kInv4Pi * ((ay * gz - az * gy) + (cy * Z - cz * Y) - ex);
         dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((az * gx - ax * gz) + (cz * X - cx * Z) - ey);
@@ -928,8 +995,9 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   // the packed kernel stages 9 KB per warp: ask for the largest shared-memory carveout
   static bool carveout_set = false;
   if (!carveout_set) {
-    const void* kx2[4] = {(const void*)k_p2p_x2<false, false>, (const void*)k_p2p_x2<false, true>,
-                          (const void*)k_p2p_x2<true, false>, (const void*)k_p2p_x2<true, true>};
+    const void* kx2[6] = {(const void*)k_p2p_x2<false, 0>, (const void*)k_p2p_x2<false, 1>,
+                          (const void*)k_p2p_x2<false, 2>, (const void*)k_p2p_x2<true, 0>,
+                          (const void*)k_p2p_x2<true, 1>,  (const void*)k_p2p_x2<true, 2>};
     for (const void* k : kx2)
       FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     carveout_set = true;
@@ -961,8 +1029,9 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
     }                                                          \
   } while (0)
   // without a stretching output the kernels skip T and the stretching sums
-  if (dg) FMM_P2P_ALL(true);
-  else FMM_P2P_ALL(false);
+  if (!dg) FMM_P2P_ALL(0);
+  else if (p->prm.outputs & FMM_OUT_STRETCHING_TRANSPOSE) FMM_P2P_ALL(2);
+  else FMM_P2P_ALL(1);
 #undef FMM_P2P_ALL
 #undef FMM_P2P_LAUNCH
 #undef FMM_P2P_X2_LAUNCH

@@ -73,6 +73,7 @@ struct fmm_server_s {
   std::vector<Worker*> workers;
   int64_t held_total = 0;
   std::map<int, Model> model;  // workspace model by class, learned from evaluations
+  std::map<int, int> tuned;    // autotuned leaf capacity by class (server ncrit = 0)
   int mem_waiters = 0;
   int probing = 0;  // a first batch of a class is running
   fmm_server_counters ctr{};
@@ -128,31 +129,29 @@ void drop_plans(fmm_server S, Worker* W, int keep) {
   recount(S, W);
 }
 
-// One batch on the worker's stream; the lock is not held.
-int run_batch(fmm_server S, Worker* W, std::vector<fmm_request>& rs, int64_t ntot, PlanRec* rec) {
+constexpr int32_t kTuneCandidates[] = {32, 48, 64, 96, 128, 192, 256};
+
+// One batch on the worker's stream; the lock is not held.  ncrit = 0: the
+// class has no tuned leaf capacity yet; this batch measures it (*ncrit_out).
+int run_batch(fmm_server S, Worker* W, std::vector<fmm_request>& rs, int64_t ntot, PlanRec* rec, int ncrit,
+              int* ncrit_out) {
   const cudaStream_t st = W->stream;
   fmm_plan& plan = rec->plan;
   const fmm_request& r0 = rs[0];
-  if (!plan || plan->n_max < ntot) {
-    if (plan) fmm_plan_destroy(plan);
-    plan = nullptr;
-    rec->n_seen = 0;
-    fmm_params q;
-    fmm_params_default(&q);
-    q.p = r0.p;
-    q.theta = S->prm.theta;
-    q.ncrit = S->prm.ncrit;
-    q.sigma_sep = S->prm.sigma_sep;
-    q.images = S->prm.images;
-    q.m2l_mode = S->prm.m2l_mode;
-    q.periodic = r0.periodic ? 1 : 0;
-    if (r0.periodic) {
-      for (int k = 0; k < 3; ++k) q.box_min[k] = r0.box[k];
-      q.box_len = r0.box[3];
-    }
-    FMM_TRY(fmm_plan_create(&q, new_plan_capacity(S, ntot), &plan));
-    rec->base = plan_bytes(plan);
+  fmm_params q;
+  fmm_params_default(&q);
+  q.p = r0.p;
+  q.theta = S->prm.theta;
+  q.ncrit = ncrit > 0 ? ncrit : 64;
+  q.sigma_sep = S->prm.sigma_sep;
+  q.images = S->prm.images;
+  q.m2l_mode = S->prm.m2l_mode;
+  q.periodic = r0.periodic ? 1 : 0;
+  if (r0.periodic) {
+    for (int k = 0; k < 3; ++k) q.box_min[k] = r0.box[k];
+    q.box_len = r0.box[3];
   }
+  *ncrit_out = ncrit;
   const size_t b3 = (size_t)std::max<int64_t>(ntot, 1) * 3 * sizeof(float);
   FMM_TRY(W->d_pos.ensure(b3));
   FMM_TRY(W->d_gam.ensure(b3));
@@ -174,6 +173,24 @@ int run_batch(fmm_server S, Worker* W, std::vector<fmm_request>& rs, int64_t nto
     if (rs[k].n == 0) continue;
     FMM_CUDA_TRY(cudaMemcpyAsync(dp + 3 * off[k], rs[k].pos, (size_t)rs[k].n * 12, cudaMemcpyHostToDevice, st));
     FMM_CUDA_TRY(cudaMemcpyAsync(dg + 3 * off[k], rs[k].gamma, (size_t)rs[k].n * 12, cudaMemcpyHostToDevice, st));
+  }
+  if (ncrit == 0 && ntot > 0) {  // first batch of the class: measure the leaf capacity on it
+    int32_t best = 64;
+    FMM_TRY(fmm_autotune_ncrit(&q, (int32_t)rs.size(), off.data(), dp, dg, sig.data(),
+                               r0.periodic ? box.data() : nullptr, kTuneCandidates,
+                               (int32_t)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0])), 1, &best, nullptr,
+                               st));
+    q.ncrit = best;
+    *ncrit_out = best;
+  }
+  if (plan && (plan->n_max < ntot || plan->prm.ncrit != q.ncrit)) {
+    fmm_plan_destroy(plan);
+    plan = nullptr;
+  }
+  if (!plan) {
+    rec->n_seen = 0;
+    FMM_TRY(fmm_plan_create(&q, new_plan_capacity(S, ntot), &plan));
+    rec->base = plan_bytes(plan);
   }
   if (S->prm.batching) {
     FMM_TRY(fmm_eval_batch(plan, (int32_t)rs.size(), off.data(), dp, dg, nullptr, sig.data(),
@@ -290,9 +307,12 @@ void worker_loop(fmm_server S, Worker* W) {
     const bool probe = !S->model.count(c);
     if (probe) S->probing = 1;
     PlanRec rec = W->plans.count(c) ? W->plans[c] : PlanRec();
+    const int ncrit = S->prm.ncrit > 0 ? S->prm.ncrit : (S->tuned.count(c) ? S->tuned[c] : 0);
+    int ncrit_used = ncrit;
     lk.unlock();
-    int rc = run_batch(S, W, rs, ntot, &rec);
+    int rc = run_batch(S, W, rs, ntot, &rec, ncrit, &ncrit_used);
     lk.lock();
+    if (rc == FMM_OK && ncrit_used > 0 && !S->tuned.count(c)) S->tuned[c] = ncrit_used;
     W->busy = false;
     if (probe) S->probing = 0;
     if (rec.plan) W->plans[c] = rec;
@@ -368,7 +388,7 @@ int fmm_server_create(const fmm_server_params* prm, fmm_server* out) {
   fmm_params q;
   fmm_params_default(&q);
   q.theta = prm->theta;
-  q.ncrit = prm->ncrit;
+  q.ncrit = prm->ncrit == 0 ? 64 : prm->ncrit;  // 0: autotuned per class
   q.sigma_sep = prm->sigma_sep;
   q.images = prm->images;
   q.m2l_mode = prm->m2l_mode;

@@ -13,7 +13,7 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None):
+def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None, outputs=None):
     import torch
     from paper_1106_5273_gb300 import Plan, Params
     pos, gam = w["pos"], w["gamma"]
@@ -22,6 +22,8 @@ def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=N
               sigma_sep=ksig, m2l_mode=m2l_mode)
     if w.get("periodic"):
         kw.update(periodic=1, box_min=w["box_min"], box_len=w["box_len"], images=images or w.get("images", 3))
+    if outputs is not None:
+        kw.update(outputs=outputs)
     plan = Plan(max(n, 1), Params.default(**kw))
     dp, dg = to_dev(pos), to_dev(gam)
     ds = to_dev(sigma_arr) if sigma_arr is not None else None

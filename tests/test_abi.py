@@ -74,7 +74,7 @@ def test_server_params_validated_without_gpu(lib):
     from paper_1106_5273_gb300 import binding as b
     h = ctypes.c_void_p()
     for bad in (dict(workers=0), dict(workers=17), dict(batching=2), dict(hbm_budget_bytes=0),
-                dict(max_batch_problems=0), dict(theta=1.0), dict(ncrit=0), dict(images=0)):
+                dict(max_batch_problems=0), dict(theta=1.0), dict(ncrit=-1), dict(images=0)):
         q = b.ServerParams.default(**bad)
         assert lib.fmm_server_create(ctypes.byref(q), ctypes.byref(h)) == -1
     assert lib.fmm_server_submit(None, None, None) == -1

@@ -148,6 +148,31 @@ def test_batch_per_particle_sigma():
         assert rel_l2(u[off[k]:off[k + 1]], ud) < 2e-4 and rel_l2(s[off[k]:off[k + 1]], sd) < 1e-3
 
 
+def test_autotune_ncrit_picks_the_fastest_candidate():
+    """fmm_autotune_ncrit times each candidate leaf size on the sample batch and
+    returns the fastest; the batch evaluated with it matches the direct sum."""
+    import torch
+    from oracle import direct as od
+    from paper_1106_5273_gb300 import Params, Plan, autotune_ncrit
+    probs = _free_problems()[2:5]
+    off, pos, gam, sig, _ = _concat(probs)
+    prm = Params.default(p=8, theta=0.5, ncrit=64)
+    best, ms = autotune_ncrit(prm, off, to_dev(pos), to_dev(gam), sig, candidates=(16, 32, 64, 128), reps=2)
+    assert best in (16, 32, 64, 128) and set(ms) == {16, 32, 64, 128}
+    assert all(v > 0 for v in ms.values()) and ms[best] == min(ms.values())
+    plan = Plan(int(off[-1]), Params.default(p=8, theta=0.5, ncrit=best))
+    u, s = plan.eval_batch(off, to_dev(pos), to_dev(gam), sigma_prob=sig)
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()
+    for k in range(len(probs)):
+        a, b = int(off[k]), int(off[k + 1])
+        if b - a < 2:
+            continue
+        ud, _ = od.direct(pos[a:b], gam[a:b], pos[a:b], gam[a:b], float(sig[k]), skip_self=True)
+        assert rel_l2(u[a:b], ud) < 2e-4
+    plan.close()
+
+
 def test_batch_argument_errors():
     import torch
     from paper_1106_5273_gb300 import Plan, Params, FmmError, BATCH_MAX

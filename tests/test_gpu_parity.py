@@ -27,12 +27,12 @@ def _built():
     __graft_entry__.build()
 
 
-def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3):
+def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3, transpose=False):
     from oracle import fmm as ofmm
     kw = {}
     if w.get("periodic"):
         kw = dict(periodic=True, box_min=w["box_min"], box_len=w["box_len"], images=images)
-    return ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), p, theta, ncrit, ksig=ksig, **kw)
+    return ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), p, theta, ncrit, ksig=ksig, transpose=transpose, **kw)
 
 
 def _canon(lst, periodic):
@@ -113,6 +113,43 @@ def test_fmm_periodic_taylor_green_small(m2l_mode):
     assert rel_l2(u, ut) < 1.5 * rel_l2(ref.u, ut) + TOL_U
 
 
+@pytest.mark.parametrize("case", ["free-space", "periodic"])
+def test_fmm_transpose_scheme(case):
+    """The transpose stretching scheme (grad u)^T gamma against the oracle FMM
+    on the same lists (one-target-per-lane kernel in free space, the packed
+    kernel in the periodic cube) and against the FP64 direct sum / the Fourier
+    series; the velocity does not depend on the scheme."""
+    from oracle import direct as od
+    from oracle import periodic as op
+    from paper_1106_5273_gb300 import FMM_OUT_STRETCHING, FMM_OUT_STRETCHING_TRANSPOSE, FMM_OUT_VELOCITY
+    outs = FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE
+    if case == "free-space":
+        w = workloads.jittered_lattice(16)
+        p, theta, ncrit = 6, 0.5, 32
+    else:
+        w = workloads.taylor_green(16)
+        p, theta, ncrit = 6, 0.4, 64
+    plan, u, s = run_fmm(w, p, theta, ncrit, m2l_mode=2, outputs=outs)
+    _, uc, sc = run_fmm(w, p, theta, ncrit, m2l_mode=2)
+    assert np.array_equal(u, uc)
+    ref = _oracle_fmm(w, p, theta, ncrit, transpose=True)
+    _check_tree_and_lists(plan, ref, case == "periodic")
+    assert rel_l2(s, ref.s) < TOL_S
+    x, g = w["pos"].astype(np.float64), w["gamma"].astype(np.float64)
+    if case == "free-space":
+        _, sd = od.direct(x, g, x, g, float(w["sigma"]), skip_self=True, transpose=True)
+    else:
+        _, sd = op.fourier(x, g, x, g, float(w["sigma"]), w["box_len"], 6, transpose=True)
+    assert rel_l2(s, sd) <= 1.5 * rel_l2(ref.s, sd) + TOL_S
+    # the schemes differ by -(gamma_i x omega(x_i)): random strengths give a
+    # different field; Taylor-Green strengths are omega h^3, parallel to the
+    # blob field's vorticity, so there the two agree to the method error
+    if case == "free-space":
+        assert rel_l2(s, sc) > 0.05
+    else:
+        assert rel_l2(s, sc) < 1e-3
+
+
 def test_fmm_periodic_random_matches_fourier():
     from oracle import periodic as op
     L = 2 * math.pi
@@ -165,7 +202,7 @@ def test_fmm_per_particle_sigma_and_plummer():
     assert rel_l2(u, ud) < 2e-4 and rel_l2(s, sd) < 1e-3
 
 
-@pytest.mark.parametrize("case", ["taylor-green-16", "plummer-free"])
+@pytest.mark.parametrize("case", ["taylor-green-16", "plummer-free", "plummer-free-transpose"])
 def test_packed_p2p_bitwise_equals_scalar_kernel(case):
     """Two targets per lane (ncrit > 32) with one core width run the packed
     FP32x2 pair kernel; the same problem with a per-particle sigma array of
@@ -181,8 +218,9 @@ def test_packed_p2p_bitwise_equals_scalar_kernel(case):
         p, theta, ncrit = 8, 0.5, 48
     n = w["pos"].shape[0]
     sig = np.full(n, np.float32(w["sigma"]), np.float32)
-    plan1, u1, s1 = run_fmm(w, p, theta, ncrit, m2l_mode=1)
-    plan2, u2, s2 = run_fmm(w, p, theta, ncrit, m2l_mode=1, sigma_arr=sig)
+    outs = 7 if case.endswith("transpose") else None  # velocity | stretching | transpose scheme
+    plan1, u1, s1 = run_fmm(w, p, theta, ncrit, m2l_mode=1, outputs=outs)
+    plan2, u2, s2 = run_fmm(w, p, theta, ncrit, m2l_mode=1, sigma_arr=sig, outputs=outs)
     st = plan1.stats()
     assert st.p2p_pairs_near > 0 and st.p2p_pairs_mid + st.p2p_pairs_far > 0
     assert np.array_equal(u1, u2) and np.array_equal(s1, s2)

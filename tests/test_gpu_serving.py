@@ -81,6 +81,28 @@ def test_serving_results_identical_alone_and_in_mix():
     srv.close()
 
 
+def test_serving_autotuned_leaf_size():
+    """Server ncrit = 0: the first batch of each (p, periodic) class measures the
+    leaf size on its own requests (fmm_autotune_ncrit over 32 ... 256) and the
+    class keeps it.  Every result is the FMM with one of those leaf sizes, so it
+    stays within the method error measured by the CPU oracle FMM at the
+    smallest of them (ncrit 32: p = 4 gives rel-L2 ~1.3e-3 (u) and ~3.8e-3 (s),
+    p = 8 ~9e-6 and ~1.7e-5 on these clouds)."""
+    from oracle import direct as od
+    from paper_1106_5273_gb300 import Server
+    reqs = _requests()[:6]
+    srv = Server(workers=2, batching=1, theta=THETA, ncrit=0, max_batch_problems=64)
+    tickets = _submit_all(srv, reqs)
+    results = [srv.wait(t, 300.0) for t in tickets]
+    assert all(res["status"] == 0 for res, _, _ in results)
+    for r, (res, u, s) in zip(reqs, results):
+        w = r["w"]
+        ud, sd = od.direct(w["pos"], w["gamma"], w["pos"], w["gamma"], float(w["sigma"]), skip_self=True)
+        tu, ts = (3e-3, 8e-3) if r["p"] == 4 else (5e-5, 1e-4)
+        assert rel_l2(u, ud) < tu and rel_l2(s, sd) < ts, (r["p"], w["pos"].shape[0], rel_l2(u, ud))
+    srv.close()
+
+
 def test_serving_one_request_per_call_mode():
     from paper_1106_5273_gb300 import Server
     reqs = _requests()
