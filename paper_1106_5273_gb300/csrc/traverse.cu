@@ -311,33 +311,36 @@ __device__ inline uint64_t compact_key(uint64_t k, const KeyPack& kp) {
   return c;
 }
 
-// (tile, compact key, slot in tile) sort keys of the M2L pairs.
+// (tile, compact key) sort keys of the M2L pairs: a run of equal keys is one
+// step.  A target has at most one source per translation, so the pairs of a
+// step have distinct slots and their order within the run does not matter.
 __global__ void k_step_keys2(const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
                              const int* __restrict__ ctile, KeyPack kp, uint64_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int ts = ctile[raw[i].x];
-  const uint64_t tile = (uint64_t)(ts / kTile), s_in = (uint64_t)(ts % kTile);
-  keys[i] = (tile << (kp.bits + 6)) | (compact_key(fkeys[i], kp) << 6) | s_in;
+  const uint64_t tile = (uint64_t)(ctile[raw[i].x] / kTile);
+  keys[i] = (tile << kp.bits) | compact_key(fkeys[i], kp);
   vals[i] = (uint32_t)i;
 }
 
 __global__ void k_step_write2(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
                               const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
-                              const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int kbits,
-                              int* __restrict__ st_tile, uint64_t* __restrict__ st_ckey,
-                              uint64_t* __restrict__ st_fkey, int* __restrict__ st_src) {
+                              const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys,
+                              const int* __restrict__ ctile, int kbits, int* __restrict__ st_tile,
+                              uint64_t* __restrict__ st_ckey, uint64_t* __restrict__ st_fkey,
+                              int* __restrict__ st_src) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t s = e[i] + f[i] - 1u;
   const uint64_t key = k[i];
   if (f[i]) {
-    st_tile[s] = (int)(key >> (kbits + 6));
-    st_ckey[s] = (key >> 6) & ((1ull << kbits) - 1ull);
+    st_tile[s] = (int)(key >> kbits);
+    st_ckey[s] = key & ((1ull << kbits) - 1ull);
     st_fkey[s] = fkeys[idx[i]];
   }
-  st_src[(size_t)s * kTile + (key & 63ull)] = raw[idx[i]].y;
+  const int4 v = raw[idx[i]];
+  st_src[(size_t)s * kTile + (ctile[v.x] % kTile)] = v.y;
 }
 
 __global__ void k_step_slots(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, int ns,
@@ -401,7 +404,7 @@ __global__ void k_cell_tiles(int nc, int ntiles, const uint32_t* __restrict__ or
 
 __global__ void k_step_flags(const uint64_t* __restrict__ k, int n, uint32_t* __restrict__ f) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) f[i] = (i == 0 || (k[i] >> 6) != (k[i - 1] >> 6)) ? 1u : 0u;
+  if (i < n) f[i] = (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
 }
 
 __global__ void k_tile_ranges(const int* __restrict__ st_tile, int ns, int2* __restrict__ tr) {
@@ -665,14 +668,14 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       kp.bits = sh;
       int tb = 1;
       while ((1ll << tb) < (long long)p->ntiles) ++tb;
-      if (tb + kp.bits + 6 > 63) return FMM_E_DEPTH;
-      // 2. sort pairs by (tile, compact key, slot): consecutive runs are the steps
+      if (tb + kp.bits > 63) return FMM_E_DEPTH;
+      // 2. sort pairs by (tile, compact key): consecutive runs are the steps
       ++g_launches;
       k_step_keys2<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
                                    p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
       int second = 0;
       FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
-                             p->lv1.as<uint32_t>(), n, 0, tb + kp.bits + 6, &second, p->sort_hist, p->scan_tmp, s));
+                             p->lv1.as<uint32_t>(), n, 0, tb + kp.bits, &second, p->sort_hist, p->scan_tmp, s));
       uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
       uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
       ++g_launches;
@@ -690,7 +693,8 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (ns + 1) * kTile * sizeof(int), s));
       ++g_launches;
       k_step_write2<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
-                                    p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), kp.bits, p->st_tile.as<int>(),
+                                    p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), p->c_tile.as<int>(), kp.bits,
+                                    p->st_tile.as<int>(),
                                     p->st_ckey.as<uint64_t>(), p->st_fkey.as<uint64_t>(), p->st_src.as<int>());
       ++g_launches;
       k_tile_ranges<<<(unsigned)((ns + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)ns, p->tile_range.as<int2>());
