@@ -30,15 +30,15 @@ UNIT = "particles/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # FP32 flops per P2P pair counted from the CUDA source of the packed pair
-# kernel (per element; FMA = 2): difference 3, r^2 5, S and T (near 21 / mid
-# 20 / far 4: 1/r^2, 1/r^3, ex2 argument, degree-4 Horner in 1/r, S, T; near
-# adds the series test), T (gamma_i . d) 6, the four accumulated sums 24; plus
-# MUFU ops (rsqrt and ex2; far pairs rsqrt only).  The near-class series
-# branch (rho^2 < 2) is not counted.
-P2P_FLOPS = {"near": 57, "mid": 56, "far": 42}
+# kernel (per element; FMA = 2): difference 3, r^2 5, S and T' = -T/3 (near
+# 20 / mid 19 / far 3: 1/r^2, 1/r^3, ex2 argument, degree-4 Horner in 1/r, S,
+# T'; near adds the series test), T' (gamma_i . d) 6, the four accumulated
+# sums 24; plus MUFU ops (rsqrt and ex2; far pairs rsqrt only).  The
+# near-class series branch (rho^2 < 2) is not counted.
+P2P_FLOPS = {"near": 56, "mid": 55, "far": 41}
 # FP32-pipe instructions per pair (FMA, MUL and ADD alike), for the pipe-slot
 # utilisation reported beside the flop rate.
-P2P_SLOTS = {"near": 35, "mid": 34, "far": 26}
+P2P_SLOTS = {"near": 34, "mid": 33, "far": 25}
 
 
 def parse():

@@ -9,7 +9,9 @@
 //   S = g / r^3 = 1/r^3 - q H / r^2 with H = (erfcx fit + 2x/sqrt(pi)) / r, i.e.
 //       H = sqrt(2/pi)/sigma + e_0/r + e_1/r^2 + e_2/r^3 + e_3/r^4,  e_k = c_k (sqrt2 sigma)^k
 //       (one Horner polynomial in 1/r: 2x/sqrt(pi) / r is the constant term)
-//   T = (c q / sigma^3 - 3 S) / r^2 = S'(r)/r
+//   T = (c q / sigma^3 - 3 S) / r^2 = S'(r)/r; the kernels carry T' = -T/3 =
+//       (S - c q / (3 sigma^3)) / r^2 (no multiply by -3 per pair) and scale the
+//       stretching sums by -3 once per target
 //   u_i += S (gamma_j x d)                                            (Eq. 1)
 //   s_i += S (gamma_j x gamma_i) + T (gamma_i . d)(gamma_j x d)       (Eq. 3)
 //   or, transpose scheme (grad u)^T gamma_i:
@@ -33,6 +35,7 @@ namespace {
 
 constexpr int kMaxBlock = 128;
 constexpr float kInv4Pi = 0.0795774715459476679f;
+constexpr float kM3 = -3.f;  // T = -3 T': scales the stretching sums built from T'
 // erfcx(1/y) ~ sum c_k y^k on [1/4.6, 1] (gen_cutoff_fit.py, degree 3)
 constexpr float kE0 = -1.202012900e-02f, kE1 = 6.541014877e-01f, kE2 = -2.626216807e-01f,
                 kE3 = 4.812366022e-02f;
@@ -70,10 +73,10 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 // (hn = -H) so that S = 1/r^3 + q (hn / r^2) is one FMA.
 struct SigK {
   float kq;   // -log2(e) / (2 sigma^2)
-  float kc;   // sqrt(2/pi) / sigma^3
+  float kc;   // -sqrt(2/pi) / (3 sigma^3)   (T' = (S + kc q) / r^2)
   float ku;   // 1 / sigma^2
   float is3;  // 1 / sigma^3
-  float is5;  // 2 / sigma^5
+  float is5;  // -2 / (3 sigma^5)            (near series: T' = f'(u) is5)
   float hn0;  // -sqrt(2/pi) / sigma          (constant term of -H)
   float hn1, hn2, hn3, hn4;  // -e_0 .. -e_3,  e_k = c_k (sqrt2 sigma)^k
 };
@@ -82,10 +85,10 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   SigK k;
   const double s = (double)sigma, ky = 1.4142135623730951 * s;
   k.kq = (float)(-1.4426950408889634 / (2.0 * s * s));
-  k.kc = (float)(0.79788456080286535588 / (s * s * s));
+  k.kc = (float)(-0.79788456080286535588 / (3.0 * s * s * s));
   k.ku = (float)(1.0 / (s * s));
   k.is3 = (float)(1.0 / (s * s * s));
-  k.is5 = (float)(2.0 / (s * s * s * s * s));
+  k.is5 = (float)(-2.0 / (3.0 * s * s * s * s * s));
   k.hn0 = (float)(-0.79788456080286535588 / s);
   k.hn1 = (float)(-(double)kE0);
   k.hn2 = (float)(-(double)kE1 * ky);
@@ -94,7 +97,7 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   return k;
 }
 
-// S = g/r^3 and T = S'(r)/r for one pair (see the file header); ST = 0:
+// S = g/r^3 and T' = -S'(r)/(3r) for one pair (see the file header); ST = 0:
 // S only (velocity without stretching).
 template <int MODE, int ST = 1>
 __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float& T) {
@@ -103,7 +106,7 @@ __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float
   T = 0.f;
   if (MODE == kFar) {
     S = rinv2 * rinv;
-    if (ST) T = -3.f * S * rinv2;
+    if (ST) T = S * rinv2;
     return;
   }
   const float rinv3 = rinv2 * rinv;
@@ -112,7 +115,7 @@ __device__ __forceinline__ void pair_ST(float r2, const SigK& K, float& S, float
   // polynomial, so g = 1 to FP32 precision without clamping
   const float hn = fmaf(fmaf(fmaf(fmaf(K.hn4, rinv, K.hn3), rinv, K.hn2), rinv, K.hn1), rinv, K.hn0);
   S = fmaf(q, rinv2 * hn, rinv3);
-  if (ST) T = fmaf(K.kc, q, -3.f * S) * rinv2;
+  if (ST) T = fmaf(K.kc, q, S) * rinv2;
   if (MODE == kNear) {
     const float u = r2 * K.ku;
     if (u < 2.f) {
@@ -157,9 +160,10 @@ __device__ __forceinline__ void pair_acc(float dx, float dy, float dz, const flo
 // image shifts folded into the source's X) and k_j = gamma_j x X_j staged per
 // source,  sum_j S (gamma_j x d) = A x X_i - B  and
 // sum_j T (gamma_i . d)(gamma_j x d) = C x X_i - D, where
-// A = sum S gamma_j, B = sum S k_j, C = sum td gamma_j, D = sum td k_j, td = T (gamma_i . d).
-// Transpose scheme: with m_i = X_i x gamma_i, w = T gamma_i . (gamma_j x d) = T (gamma_j . m_i -
-// gamma_i . k_j); C.x = sum w, D = sum w X_j, and s = gamma_i x A + (sum w) X_i - D.
+// A = sum S gamma_j, B = sum S k_j, C = sum td gamma_j, D = sum td k_j, td = T' (gamma_i . d)
+// (T' = -T/3, so the stretching is s = A x gamma_i - 3 (C x X_i - D)).
+// Transpose scheme: with m_i = X_i x gamma_i, w = T' gamma_i . (gamma_j x d) = T' (gamma_j . m_i -
+// gamma_i . k_j); C.x = sum w, D = sum w X_j, and s = gamma_i x A - 3 ((sum w) X_i - D).
 struct AccR {
   float ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz;
 };
@@ -481,15 +485,15 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       }
       if (ST == 1 && dg) {  // s = A x gamma_i + C x X_i - D
         const float gx = t.gx[q], gy = t.gy[q], gz = t.gz[q];
-        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((a.ay * gz - a.az * gy) + (a.cy * Z - a.cz * Y) - a.dx);
-        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((a.az * gx - a.ax * gz) + (a.cz * X - a.cx * Z) - a.dy);
-        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((a.ax * gy - a.ay * gx) + (a.cx * Y - a.cy * X) - a.dz);
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((a.ay * gz - a.az * gy) + kM3 * ((a.cy * Z - a.cz * Y) - a.dx));
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((a.az * gx - a.ax * gz) + kM3 * ((a.cz * X - a.cx * Z) - a.dy));
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((a.ax * gy - a.ay * gx) + kM3 * ((a.cx * Y - a.cy * X) - a.dz));
       }
       if (ST == 2 && dg) {  // s = gamma_i x A + W X_i - D (W = C.x)
         const float gx = t.gx[q], gy = t.gy[q], gz = t.gz[q];
-        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((gy * a.az - gz * a.ay) + (a.cx * X - a.dx));
-        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((gz * a.ax - gx * a.az) + (a.cx * Y - a.dy));
-        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((gx * a.ay - gy * a.ax) + (a.cx * Z - a.dz));
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((gy * a.az - gz * a.ay) + kM3 * (a.cx * X - a.dx));
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((gz * a.ax - gx * a.az) + kM3 * (a.cx * Y - a.dy));
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((gx * a.ay - gy * a.ax) + kM3 * (a.cx * Z - a.dz));
       }
     }
   }
@@ -539,7 +543,7 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
   T = dup2(0.f);
   if (MODE == kFar) {
     S = mul2(rinv2, rinv);
-    if (ST) T = mul2(mul2(dup2(-3.f), S), rinv2);
+    if (ST) T = mul2(S, rinv2);
     return;
   }
   const float2 rinv3 = mul2(rinv2, rinv);
@@ -547,7 +551,7 @@ __device__ __forceinline__ void pair_ST2(float2 r2, const SigK2& K, float2& S, f
   const float2 q = make_float2(ex2_approx(qa.x), ex2_approx(qa.y));
   const float2 hn = fma2(fma2(fma2(fma2(K.hn4, rinv, K.hn3), rinv, K.hn2), rinv, K.hn1), rinv, K.hn0);
   S = fma2(q, mul2(rinv2, hn), rinv3);
-  if (ST) T = mul2(fma2(K.kc, q, mul2(dup2(-3.f), S)), rinv2);
+  if (ST) T = mul2(fma2(K.kc, q, S), rinv2);
   if (MODE == kNear) {
     const float2 u = mul2(r2, K.ku);
     if (u.x < 2.f || u.y < 2.f) {
@@ -821,15 +825,15 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       }
       if (ST == 2 && dg) {  // s = gamma_i x A + W X_i + (sum w (-X_j)), W = C.x
         const float gx = gxs[q], gy = gys[q], gz = gzs[q];
-        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((gy * az - gz * ay) + (cx * X + ex));
-        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((gz * ax - gx * az) + (cx * Y + ey));
-        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((gx * ay - gy * ax) + (cx * Z + ez));
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((gy * az - gz * ay) + kM3 * (cx * X + ex));
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((gz * ax - gx * az) + kM3 * (cx * Y + ey));
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((gx * ay - gy * ax) + kM3 * (cx * Z + ez));
       }
       if (ST == 1 && dg) {  // s = A x gamma_i + C x X_i - D
         const float gx = gxs[q], gy = gys[q], gz = gzs[q];
-        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((ay * gz - az * gy) + (cy * Z - cz * Y) - ex);
-        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((az * gx - ax * gz) + (cz * X - cx * Z) - ey);
-        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((ax * gy - ay * gx) + (cx * Y - cy * X) - ez);
+        dg[3 * o] = far_s[3 * i] + kInv4Pi * ((ay * gz - az * gy) + kM3 * ((cy * Z - cz * Y) - ex));
+        dg[3 * o + 1] = far_s[3 * i + 1] + kInv4Pi * ((az * gx - ax * gz) + kM3 * ((cz * X - cx * Z) - ey));
+        dg[3 * o + 2] = far_s[3 * i + 2] + kInv4Pi * ((ax * gy - ay * gx) + kM3 * ((cx * Y - cy * X) - ez));
       }
     }
   }
@@ -882,9 +886,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_direct(int64_t n, const float* __
       vel[3 * i + 2] = kInv4Pi * a.uz;
     }
     if (dg) {
-      dg[3 * i] = kInv4Pi * (a.sx + (a.ay * t.gz[0] - a.az * t.gy[0]));
-      dg[3 * i + 1] = kInv4Pi * (a.sy + (a.az * t.gx[0] - a.ax * t.gz[0]));
-      dg[3 * i + 2] = kInv4Pi * (a.sz + (a.ax * t.gy[0] - a.ay * t.gx[0]));
+      dg[3 * i] = kInv4Pi * (kM3 * a.sx + (a.ay * t.gz[0] - a.az * t.gy[0]));
+      dg[3 * i + 1] = kInv4Pi * (kM3 * a.sy + (a.az * t.gx[0] - a.ax * t.gz[0]));
+      dg[3 * i + 2] = kInv4Pi * (kM3 * a.sz + (a.ax * t.gy[0] - a.ay * t.gx[0]));
     }
   }
 }
