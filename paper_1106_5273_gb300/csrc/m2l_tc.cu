@@ -20,8 +20,9 @@
 // and commits them to the stage's empty barrier.  One stage per CTA and two
 // CTAs per SM (81 KB of shared memory and 256 TMEM columns each): while one
 // CTA waits on its gathers and barriers the other's MMAs keep the tensor pipe
-// busy.  Measured at 2M blobs: 6.6 ms against 7.8 ms for two stages in one CTA
-// per SM.  Every wait is
+// busy.  The producers load a stage's rows into registers before they wait
+// for its buffer.  Measured at 2M blobs: 5.6 ms, against 6.6 ms without the
+// early loads and 7.8 ms for two stages in one CTA per SM.  Every wait is
 // bounded; on expiry the kernel records FMM_E_TIMEOUT, waits (bounded) for
 // its own bulk copies, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -168,31 +169,31 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int niter = (rg.y - rg.x) * nkc;
 
   if (warp < kProducerWarps) {
-    // ---- producers: gather the B rows of each stage
+    // ---- producers: thread t stores 16-byte chunk j = t % 8 of rows n = t/8 + 32k
+    // (k = 0..5) of both halves, i.e. of the sources in slots t/8 and t/8 + 32;
+    // the rows are loaded before the stage's buffer is waited for.
+    const int j = threadIdx.x & 7, r0 = threadIdx.x >> 3;
     for (int it = 0; it < niter; ++it) {
       const int stage = it % kStages;
       const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-      if (!mbar_wait(empty(stage), ph ^ 1u, abort)) break;
       const int st = rg.x + it / nkc, kc = it % nkc;
+      const int srcA = __ldg(st_src + (size_t)st * kTile + r0), srcB = __ldg(st_src + (size_t)st * kTile + r0 + 32);
       uint4 v[kGather];
-      int dst[kGather];
 #pragma unroll
       for (int q = 0; q < kGather; ++q) {
-        const int item = threadIdx.x + kProducers * q;
-        const int h = item / (kN * 8);
-        const int rem = item % (kN * 8);
-        const int n = rem >> 3, j = rem & 7;
-        const int comp = n / kTile, slot = n % kTile;
-        const int src = st_src[(size_t)st * kTile + slot];
+        const int h = q / 6, k = q % 6;
+        const int src = (k & 1) ? srcB : srcA;
         v[q] = make_uint4(0u, 0u, 0u, 0u);
-        if (src >= 0) {
-          const uint4* gp = reinterpret_cast<const uint4*>(Mbf + (((size_t)src * 2 + h) * 3 + comp) * kpad + kc * 64) + j;
-          v[q] = __ldg(gp);
-        }
-        dst[q] = (int)(stage * kStageBytes + 2 * kABytes + h * kBBytes + n * 128 + ((j ^ (n & 7)) << 4));
+        if (src >= 0)
+          v[q] = __ldg(reinterpret_cast<const uint4*>(Mbf + (((size_t)src * 2 + h) * 3 + (k >> 1)) * kpad + kc * 64) + j);
       }
+      if (!mbar_wait(empty(stage), ph ^ 1u, abort)) break;
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) *reinterpret_cast<uint4*>(smem + dst[q]) = v[q];
+      for (int q = 0; q < kGather; ++q) {
+        const int h = q / 6, n = r0 + 32 * (q % 6);
+        *reinterpret_cast<uint4*>(smem + stage * kStageBytes + 2 * kABytes + h * kBBytes + n * 128 +
+                                  ((j ^ (n & 7)) << 4)) = v[q];
+      }
       fence_proxy_async();
       mbar_arrive(fullB(stage));
     }
