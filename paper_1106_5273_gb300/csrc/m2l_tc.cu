@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- producers: thread t stores 16-byte chunk j = t % 8 of rows n = t/8 + 32k
     // (k = 0..5) of both halves, i.e. of the sources in slots t/8 and t/8 + 32;
     // the rows are loaded before the stage's buffer is waited for.
+    static_assert(kGather == 12 && kProducers == 256 && kN == 192, "producer row mapping");
     const int j = threadIdx.x & 7, r0 = threadIdx.x >> 3;
     for (int it = 0; it < niter; ++it) {
       const int stage = it % kStages;
