@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(128) k_l2l(int lb, const int* __restrict__ par
     int r = threadIdx.x + 128 * h;
     if (r >= P) break;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 8
     for (int k = 0; k < P; ++k) {
       float w = W[(size_t)k * P + r];
       a0 = fmaf(w, sLp[k], a0);

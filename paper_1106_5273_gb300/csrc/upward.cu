@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(128) k_m2m(int lb, const int* __restrict__ chi
     for (int h = 0; h < 2; ++h) {
       int r = threadIdx.x + 128 * h;
       if (r >= P) break;
+#pragma unroll 8
       for (int k = 0; k < P; ++k) {
         float w = W[(size_t)k * P + r];
         acc[0][h] = fmaf(w, sMc[k], acc[0][h]);
