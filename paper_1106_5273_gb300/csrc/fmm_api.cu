@@ -46,10 +46,21 @@ struct Timer {
   fmm_plan p;
   cudaStream_t s;
   int k = 0;
-  void mark() {
-    if (p->timing && k < 8) cudaEventRecord(p->ev[k++], s);
+  void mark() { mark_on(s); }
+  void mark_on(cudaStream_t st) {
+    if (p->timing && k < 8) cudaEventRecord(p->ev[k++], st);
   }
 };
+
+// The plan's second stream and its fork / join events (created on the plan's
+// device by its first evaluation).
+int ensure_aux_stream(fmm_plan p) {
+  if (p->s_up) return FMM_OK;
+  FMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_up, cudaStreamNonBlocking));
+  FMM_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  FMM_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  return FMM_OK;
+}
 
 // sg: nullptr for one problem, else the (non-empty) problems of a batch.
 int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const float* sig, float sig_u, float* vel,
@@ -72,8 +83,29 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   if (sg) FMM_TRY(build_forest(p, n, pos, gam, sig, *sg, s));
   else FMM_TRY(build_tree(p, n, pos, gam, sig, sig_u, s));
   tm.mark();
-  FMM_TRY(upward_pass(p, s));
-  tm.mark();
+  // Fork: P2M / M2M on the plan's second stream while the traversal (which
+  // reads only the tree) runs on the caller's stream; join before M2L.
+  FMM_TRY(ensure_aux_stream(p));
+  FMM_CUDA_TRY(cudaEventRecord(p->ev_fork, s));
+  FMM_CUDA_TRY(cudaStreamWaitEvent(p->s_up, p->ev_fork, 0));
+  {
+    const int urc = upward_pass(p, p->s_up);
+    if (urc != FMM_OK) {
+      cudaStreamSynchronize(p->s_up);
+      return urc;
+    }
+  }
+  tm.mark_on(p->s_up);
+  FMM_CUDA_TRY(cudaEventRecord(p->ev_join, p->s_up));
+  // from here on an early return must not leave the upward pass running
+  struct JoinOnExit {
+    fmm_plan p;
+    cudaStream_t s;
+    bool joined = false;
+    ~JoinOnExit() {
+      if (!joined) cudaStreamSynchronize(p->s_up);
+    }
+  } join_guard{p, s};
   double smax = (double)sig_u;
   if (sg) {
     FMM_TRY(segment_tables(p, sig ? 1 : 0, s));
@@ -89,6 +121,8 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   FMM_TRY(traverse(p, smax, s));
   FMM_TRY(build_m2l_operators(p, s));
   tm.mark();
+  FMM_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_join, 0));
+  join_guard.joined = true;
   const int nc = (int)p->ncells;
   FMM_TRY(p->L.ensure((size_t)nc * 3 * p->P * sizeof(float)));
   FMM_CUDA_TRY(cudaMemsetAsync(p->L.ptr, 0, (size_t)nc * 3 * p->P * sizeof(float), s));
@@ -130,7 +164,9 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
     for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
     st.ms_tree = ms[0];
     st.ms_upward = ms[1];
-    st.ms_traverse = ms[2];
+    float trav = 0.f;  // the traversal starts with the upward pass (they overlap)
+    cudaEventElapsedTime(&trav, p->ev[1], p->ev[3]);
+    st.ms_traverse = trav;
     st.ms_m2l = ms[3];
     st.ms_downward = ms[4];
     st.ms_p2p = ms[5];
@@ -221,6 +257,9 @@ void fmm_plan_destroy(fmm_plan p) {
   if (p->seg_pinned) cudaFreeHost(p->seg_pinned);
   if (p->have_events)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(p->ev[i]);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->s_up) cudaStreamDestroy(p->s_up);
   delete p;
 }
 

@@ -118,6 +118,10 @@ struct fmm_plan_s {
   fmm_stats stats;
   cudaEvent_t ev[8];
   int have_events = 0;
+  // the upward pass runs on this plan stream while the traversal runs on the
+  // caller's stream (both read only the tree); fork / join by events
+  cudaStream_t s_up = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace fmm {
