@@ -120,6 +120,106 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* t
   return FMM_OK;
 }
 
+// ---------------------------------------------------------- three scans ---
+// Exclusive scans of three u32 arrays of one length in the same passes (the
+// traversal's per-pair M2L, P2P and push counts).  Each array is scanned
+// exactly as exclusive_scan_u32 scans it.
+
+namespace {
+
+struct Scan3Ptrs {
+  const uint32_t* in[3];
+  uint32_t* out[3];
+};
+
+__global__ void k_scan3_reduce(Scan3Ptrs a, int64_t n, uint32_t* __restrict__ sums, int64_t ld) {
+  __shared__ uint32_t s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+      if (idx < n) acc += a.in[c][idx];
+    }
+    uint32_t total;
+    block_excl_scan(acc, s_warp, total);
+    if (threadIdx.x == 0) sums[c * ld + blockIdx.x] = total;
+  }
+}
+
+__global__ void k_scan3_apply(Scan3Ptrs a, int64_t n, const uint32_t* __restrict__ offs, int64_t ld,
+                              uint32_t* __restrict__ total_out) {
+  __shared__ uint32_t s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    uint32_t v[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+      v[i] = idx < n ? a.in[c][idx] : 0u;
+      acc += v[i];
+    }
+    uint32_t total;
+    uint32_t pre = block_excl_scan(acc, s_warp, total);
+    const uint32_t off = offs ? offs[c * ld + blockIdx.x] : 0u;
+    pre += off;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+      if (idx < n) a.out[c][idx] = pre;
+      pre += v[i];
+    }
+    if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) total_out[c] = off + total;
+  }
+}
+
+}  // namespace
+
+int exclusive_scan3_u32(const uint32_t* const in[3], uint32_t* const out[3], int64_t n, uint32_t* total_dev,
+                        DBuf& tmp, DBuf& tmp2, cudaStream_t s) {
+  if (n <= 0) {
+    if (total_dev) FMM_CUDA_TRY(cudaMemsetAsync(total_dev, 0, 3 * sizeof(uint32_t), s));
+    return FMM_OK;
+  }
+  Scan3Ptrs a;
+  for (int c = 0; c < 3; ++c) {
+    a.in[c] = in[c];
+    a.out[c] = out[c];
+  }
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb <= 1) {
+    ++g_launches;
+    k_scan3_apply<<<1, kScanThreads, 0, s>>>(a, n, nullptr, 0, total_dev);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+  }
+  // block sums of the three arrays, scanned in place by the one-array scan
+  const int64_t ld = nb + 1;
+  FMM_TRY(tmp.ensure((size_t)(3 * ld) * sizeof(uint32_t) + 64));
+  uint32_t* sums = tmp.as<uint32_t>();
+  ++g_launches;
+  k_scan3_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(a, n, sums, ld);
+  if (nb <= kScanTile) {  // the three block-sum arrays in one single-block pass (in place)
+    Scan3Ptrs b;
+    for (int c = 0; c < 3; ++c) {
+      b.in[c] = sums + c * ld;
+      b.out[c] = sums + c * ld;
+    }
+    ++g_launches;
+    k_scan3_apply<<<1, kScanThreads, 0, s>>>(b, nb, nullptr, 0, nullptr);
+  } else {
+    for (int c = 0; c < 3; ++c) FMM_TRY(exclusive_scan_u32(sums + c * ld, sums + c * ld, nb, nullptr, tmp2, s));
+  }
+  ++g_launches;
+  k_scan3_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(a, n, sums, ld, total_dev);
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
 // ------------------------------------------------------------------ sort ---
 
 namespace {

@@ -529,9 +529,11 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     uint32_t* cf = p->tscan2.as<uint32_t>();
     ++g_launches;
     k_trav_classify<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf);
-    FMM_TRY(exclusive_scan_u32(cm, cm, nf, dcnt + 0, p->scan_tmp, s));
-    FMM_TRY(exclusive_scan_u32(cp, cp, nf, dcnt + 1, p->scan_tmp, s));
-    FMM_TRY(exclusive_scan_u32(cf, cf, nf, dcnt + 2, p->scan_tmp, s));
+    {  // the three counts in shared passes (sort_hist is free during the traversal)
+      const uint32_t* const cin[3] = {cm, cp, cf};
+      uint32_t* const cout[3] = {cm, cp, cf};
+      FMM_TRY(exclusive_scan3_u32(cin, cout, nf, dcnt, p->scan_tmp, p->sort_hist, s));
+    }
     FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     int64_t am = hc[0], ap = hc[1], af = hc[2];
