@@ -23,7 +23,8 @@
 // One warp per target leaf, two target particles per lane (one when ncrit <=
 // 32); the source leaves of the leaf's list are staged through shared memory
 // in double-buffered chunks.  Each staged source is classified by a lower
-// bound on its distance to every target of the leaf: the singular kernel where
+// bound on its distance to every target of the tile (its distance to the
+// targets' bounding box, rounding margin off): the singular kernel where
 // g = 1 to FP32 precision (rho >= 6.5), the cutoff without the series test
 // (rho^2 >= 2), or the full form; a chunk is staged grouped by class, so each
 // group runs its own branch-free loop.
@@ -242,14 +243,52 @@ __device__ __forceinline__ void dispatch_rel(bool self, int nf, int nm, const fl
   if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT, ST>(sA, sB, sC, sK, nf + nm, cnt, t, K0);
 }
 
+// Axis-aligned bounding box of the targets of one tile, relative to the leaf
+// centre (the coordinates the targets carry).
+struct TileBox {
+  float lx, ly, lz, hx, hy, hz;
+};
+
+// Box of the target coordinates x[q], y[q], z[q] (q < TPT) over the warp;
+// lanes flag the targets that exist (valid[q]).
+template <int TPT>
+__device__ __forceinline__ TileBox tile_box(const float* x, const float* y, const float* z, const bool* valid) {
+  TileBox b{INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+  for (int q = 0; q < TPT; ++q)
+    if (valid[q]) {
+      b.lx = fminf(b.lx, x[q]);
+      b.ly = fminf(b.ly, y[q]);
+      b.lz = fminf(b.lz, z[q]);
+      b.hx = fmaxf(b.hx, x[q]);
+      b.hy = fmaxf(b.hy, y[q]);
+      b.hz = fmaxf(b.hz, z[q]);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    b.lx = fminf(b.lx, __shfl_xor_sync(0xffffffffu, b.lx, o));
+    b.ly = fminf(b.ly, __shfl_xor_sync(0xffffffffu, b.ly, o));
+    b.lz = fminf(b.lz, __shfl_xor_sync(0xffffffffu, b.lz, o));
+    b.hx = fmaxf(b.hx, __shfl_xor_sync(0xffffffffu, b.hx, o));
+    b.hy = fmaxf(b.hy, __shfl_xor_sync(0xffffffffu, b.hy, o));
+    b.hz = fmaxf(b.hz, __shfl_xor_sync(0xffffffffu, b.hz, o));
+  }
+  return b;
+}
+
 // Class of a staged source at X (relative to the target leaf centre, image
-// shift included) for a target leaf of radius Rt: its distance to the centre
-// minus Rt bounds its distance to every target from below; the bound is
-// lowered by a margin covering the FP32 rounding of the coordinates, so the
-// class is never more optimistic than exact arithmetic would give.
-__device__ __forceinline__ int source_class(float X, float Y, float Z, float Rt, float smax, float margin0) {
-  const float d = sqrtf(X * X + Y * Y + Z * Z);
-  const float dmin = d - Rt - (margin0 + 1e-6f * (d + Rt));
+// shift included) for the targets of a tile inside box b of a leaf of radius
+// Rt: the distance from X to the box bounds its distance to every target from
+// below; the bound is lowered by a margin covering the FP32 rounding of the
+// coordinates (which are at most d + 2 Rt in size), so the class is never
+// more optimistic than exact arithmetic would give.
+__device__ __forceinline__ int source_class(float X, float Y, float Z, const TileBox& b, float Rt, float smax,
+                                            float margin0) {
+  const float ex = fmaxf(fmaxf(b.lx - X, X - b.hx), 0.f);
+  const float ey = fmaxf(fmaxf(b.ly - Y, Y - b.hy), 0.f);
+  const float ez = fmaxf(fmaxf(b.lz - Z, Z - b.hz), 0.f);
+  const float d = sqrtf(ex * ex + ey * ey + ez * ez);
+  const float dmin = d - (margin0 + 1e-6f * (d + 2.f * Rt));
   if (dmin >= (float)kFarRho * smax) return kFar;
   if (dmin >= (float)kMidRho * smax) return kMid;
   return kNear;
@@ -368,6 +407,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
   }
   float4 ra[TPT], rb[TPT];
   unsigned long long c_near = 0, c_mid = 0, c_far = 0;
+  TileBox box;
   // source j of entry e, staged as X_j = (x_j - c) - shift, gamma_j, k_j = gamma_j x X_j,
   // grouped by class (the self entry in source order)
   auto stage = [&](int bb, int cnt, int img, bool self_entry, int& nf, int& nm) {
@@ -381,7 +421,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       X[q] = (ra[q].x - lc.x) - shx;
       Y[q] = (ra[q].y - lc.y) - shy;
       Z[q] = (ra[q].z - lc.z) - shz;
-      cls[q] = j >= cnt ? -1 : self_entry ? kNear : source_class(X[q], Y[q], Z[q], lc.w, smax, margin0);
+      cls[q] = j >= cnt ? -1 : self_entry ? kNear : source_class(X[q], Y[q], Z[q], box, lc.w, smax, margin0);
     }
     group_slots<TPT>(cls, lane, slot, nf, nm);
 #pragma unroll
@@ -413,6 +453,12 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       t.my[q] = t.z[q] * gi.x - t.x[q] * gi.z;
       t.mz[q] = t.x[q] * gi.y - t.y[q] * gi.x;
       t.a[q] = AccR{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    }
+    {
+      bool valid[TPT];
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) valid[q] = t0 + lane + 32 * q < te;
+      box = tile_box<TPT>(t.x, t.y, t.z, valid);
     }
     const unsigned long long nt = (unsigned long long)min(CH, te - t0);
     int cur_e = rg.x, cur_c0 = rg.x < rg.y ? begin[list[rg.x].x] : 0, cur_cnt = 0, cur_nf = 0, cur_nm = 0;
@@ -671,6 +717,7 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
   const SigK2 K = make_sigk2(K0);
   float4 ra[2], rb[2];
   unsigned long long c_near = 0, c_mid = 0, c_far = 0;
+  TileBox box;
   auto stage = [&](int bb, int cnt, int img, bool self_entry, int& nf, int& nm) {
     const float shx = -(float)(img / 9 - 1) * blen, shy = -(float)((img / 3) % 3 - 1) * blen,
                 shz = -(float)(img % 3 - 1) * blen;
@@ -682,7 +729,7 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       X[q] = (ra[q].x - lc.x) - shx;
       Y[q] = (ra[q].y - lc.y) - shy;
       Z[q] = (ra[q].z - lc.z) - shz;
-      cls[q] = j >= cnt ? -1 : self_entry ? kNear : source_class(X[q], Y[q], Z[q], lc.w, smax, margin0);
+      cls[q] = j >= cnt ? -1 : self_entry ? kNear : source_class(X[q], Y[q], Z[q], box, lc.w, smax, margin0);
     }
     group_slots<2>(cls, lane, slot, nf, nm);
 #pragma unroll
@@ -712,6 +759,10 @@ __global__ void __launch_bounds__(32) k_p2p_x2(const int* __restrict__ leaves, c
       gxs[q] = gi.x;
       gys[q] = gi.y;
       gzs[q] = gi.z;
+    }
+    {
+      const bool valid[2] = {t0 + lane < te, t0 + lane + 32 < te};
+      box = tile_box<2>(xs, ys, zs, valid);
     }
     const float2 tx = make_float2(xs[0], xs[1]), ty = make_float2(ys[0], ys[1]), tz = make_float2(zs[0], zs[1]);
     const float2 gix = make_float2(gxs[0], gxs[1]), giy = make_float2(gys[0], gys[1]),
