@@ -52,7 +52,13 @@ enum { FMM_OUT_VELOCITY = 1, FMM_OUT_STRETCHING = 2, FMM_OUT_STRETCHING_TRANSPOS
 enum {
   FMM_M2L_AUTO = 0,   /* tensor cores (every p) */
   FMM_M2L_SIMT = 1,   /* FP32 CUDA-core GEMM per (target tile, translation) */
-  FMM_M2L_TENSOR = 2  /* tcgen05 BF16x3 split products, FP32 accumulation */
+  FMM_M2L_TENSOR = 2, /* tcgen05 BF16x3 split products, FP32 accumulation */
+  /* Flag, OR'ed with a mode: build the (tile, translation) steps by a radix
+   * sort of the M2L pairs.  Without it the steps come from flag tables over
+   * the translations and (tile, translation) bins whenever those tables are
+   * small (compact keys of <= 22 bits, <= 2^26 bins), else from the sort.
+   * Both give the same steps in the same order. */
+  FMM_M2L_SORT_STEPS = 8
 };
 
 typedef struct fmm_plan_s* fmm_plan;
@@ -75,7 +81,7 @@ typedef struct fmm_plan_s* fmm_plan;
  *   outputs    FMM_OUT_VELOCITY | FMM_OUT_STRETCHING, optionally
  *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
  *              output pointer skips that output.
- *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR.
+ *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR, optionally | FMM_M2L_SORT_STEPS.
  */
 typedef struct {
   int32_t p;

@@ -14,6 +14,7 @@ library_path = os.path.join(HERE, "_lib", "libfmm_vortex.so")
 
 FMM_OK = 0
 FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
+FMM_M2L_SORT_STEPS = 8
 FMM_OUT_VELOCITY, FMM_OUT_STRETCHING, FMM_OUT_STRETCHING_TRANSPOSE = 1, 2, 4
 
 

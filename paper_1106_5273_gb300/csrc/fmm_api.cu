@@ -24,7 +24,7 @@ int check_params(const fmm_params* q) {
   if (q->periodic != 0 && q->periodic != 1) return FMM_E_INVAL;
   if (q->periodic && (q->images < 1 || q->images > 8 || !(q->box_len > 0.0))) return FMM_E_INVAL;
   if (!(q->sigma_sep >= 0.f)) return FMM_E_INVAL;
-  if (q->m2l_mode < FMM_M2L_AUTO || q->m2l_mode > FMM_M2L_TENSOR) return FMM_E_INVAL;
+  if (q->m2l_mode & ~(3 | FMM_M2L_SORT_STEPS) || (q->m2l_mode & 3) > FMM_M2L_TENSOR) return FMM_E_INVAL;
   if (q->outputs & ~(FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE)) return FMM_E_INVAL;
   return FMM_OK;
 }
@@ -37,7 +37,7 @@ std::vector<DBuf*> plan_buffers(fmm_plan p) {
           &p->tile_cells, &p->tile_first, &p->tile_groups, &p->c_ijk, &p->t_pos, &p->t_gam, &p->t_sig, &p->t_vel, &p->leaves, &p->M, &p->L, &p->Mbf, &p->fr0, &p->fr1, &p->tcount, &p->tmask,
           &p->tscan0, &p->tscan1, &p->tscan2, &p->p2p_raw, &p->m2l_raw, &p->lk0, &p->lk1, &p->lv0, &p->lv1,
           &p->p2p_sorted, &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf,
-          &p->tmiss_keys, &p->tmiss_slots, &p->tslot_map, &p->st_tile, &p->st_slot, &p->st_src, &p->st_ckey,
+          &p->tmiss_keys, &p->tmiss_slots, &p->tslot_map, &p->st_tile, &p->st_slot, &p->st_src, &p->bin_flag, &p->bin_scan, &p->bin_flag2, &p->bin_scan2, &p->st_ckey,
           &p->st_fkey, &p->m2l_items, &p->m2l_partial, &p->tile_range, &p->scan_tmp, &p->sort_hist, &p->scal,
           &p->flags, &p->seg_off, &p->seg_box, &p->seg_sig, &p->seg_smax, &p->seg_mac, &p->seg_p2p, &p->c_seg};
 }
@@ -76,8 +76,9 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   if (n == 0) return FMM_OK;
   FMM_CUDA_TRY(cudaSetDevice(p->device));
   FMM_CUDA_TRY(cudaMemsetAsync(p->flags.ptr, 0, sizeof(int) * 4, s));
-  p->last_tc = (p->prm.m2l_mode == FMM_M2L_SIMT) ? 0 : p->tc_ok;
-  if (p->prm.m2l_mode == FMM_M2L_TENSOR && !p->tc_ok) return FMM_E_INVAL;
+  const int m2l_kind = p->prm.m2l_mode & 3;
+  p->last_tc = (m2l_kind == FMM_M2L_SIMT) ? 0 : p->tc_ok;
+  if (m2l_kind == FMM_M2L_TENSOR && !p->tc_ok) return FMM_E_INVAL;
   Timer tm{p, s};
   tm.mark();
   if (sg) FMM_TRY(build_forest(p, n, pos, gam, sig, *sg, s));

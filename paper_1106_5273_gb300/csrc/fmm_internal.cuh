@@ -100,6 +100,7 @@ struct fmm_plan_s {
   std::vector<int> h_map;
   int64_t n_built = 0;                                // operators built by the last evaluation
   fmm::DBuf st_tile, st_slot, st_src, tile_range;     // M2L steps
+  fmm::DBuf bin_flag, bin_scan, bin_flag2, bin_scan2;  // binned step build: key and bin tables
   fmm::DBuf st_ckey, st_fkey;                         // compact / full translation key per step
   fmm::DBuf m2l_items, m2l_partial;                   // M2L work items (+ split list); partial sums
   // scratch

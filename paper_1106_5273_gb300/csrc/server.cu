@@ -393,7 +393,8 @@ int fmm_server_create(const fmm_server_params* prm, fmm_server* out) {
   q.images = prm->images;
   q.m2l_mode = prm->m2l_mode;
   if (!(q.theta > 0.f && q.theta < 1.f) || q.ncrit < 1 || q.ncrit > 4096 || !(q.sigma_sep >= 0.f) ||
-      q.images < 1 || q.images > 8 || q.m2l_mode < FMM_M2L_AUTO || q.m2l_mode > FMM_M2L_TENSOR)
+      q.images < 1 || q.images > 8 || (q.m2l_mode & ~(3 | FMM_M2L_SORT_STEPS)) ||
+      (q.m2l_mode & 3) > FMM_M2L_TENSOR)
     return FMM_E_INVAL;
   fmm_server S = new (std::nothrow) fmm_server_s();
   if (!S) return FMM_E_NOMEM;

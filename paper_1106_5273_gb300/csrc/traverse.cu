@@ -297,9 +297,16 @@ __global__ void k_key_ranges(const uint64_t* __restrict__ keys, int n, int* __re
   }
 }
 
+// Limits of the binned step build: compact keys of at most 22 bits (a 16 MB
+// flag table) and at most 2^26 (tile, translation) bins; beyond either the
+// steps come from the sort.
+constexpr int kBinKeyBits = 22;
+constexpr int64_t kBinMax = 1ll << 26;
+
 struct KeyPack {
   int lo[4];
   int shift[4];  // bit position of each field in the compact key
+  int width[4];  // bits of each field
   int bits;      // total compact key bits
 };
 
@@ -322,6 +329,55 @@ __global__ void k_step_keys2(const int4* __restrict__ raw, const uint64_t* __res
   const uint64_t tile = (uint64_t)(ctile[raw[i].x] / kTile);
   keys[i] = (tile << kp.bits) | compact_key(fkeys[i], kp);
   vals[i] = (uint32_t)i;
+}
+
+// Binned step build.  With K = 2^bits compact keys, the translations present
+// are flagged in a K-table; its scan numbers them in compact-key order (the
+// operator slots).  The (tile, slot) bins present are flagged in a second
+// table, whose scan numbers the steps in (tile, compact key) order: the same
+// steps, slots and order as the sort of k_step_keys2.
+__global__ void k_key_mark(const uint64_t* __restrict__ fkeys, int n, KeyPack kp, uint32_t* __restrict__ kflag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) kflag[compact_key(fkeys[i], kp)] = 1u;
+}
+
+// Slot of every flagged compact key -> its full translation key.
+__global__ void k_key_unpack(const uint32_t* __restrict__ kflag, const uint32_t* __restrict__ kslot, int64_t K,
+                             KeyPack kp, uint64_t* __restrict__ ukeys) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K || !kflag[c]) return;
+  int f[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) f[q] = (int)((c >> kp.shift[q]) & ((1ll << kp.width[q]) - 1)) + kp.lo[q];
+  ukeys[kslot[c]] = m2l_key_encode(f[0], f[1], f[2], f[3]);
+}
+
+// bin of pair i = tile * nkeys + slot; flags the bin and keeps it per pair.
+__global__ void k_bin_mark(const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
+                           const int* __restrict__ ctile, KeyPack kp, const uint32_t* __restrict__ kslot, int nkeys,
+                           uint32_t* __restrict__ bflag, uint32_t* __restrict__ pbin) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t b = (uint32_t)(ctile[raw[i].x] / kTile) * (uint32_t)nkeys + kslot[compact_key(fkeys[i], kp)];
+  bflag[b] = 1u;
+  pbin[i] = b;
+}
+
+__global__ void k_bin_steps(const uint32_t* __restrict__ bflag, const uint32_t* __restrict__ bstep, int64_t nb,
+                            int nkeys, int* __restrict__ st_tile, int* __restrict__ st_slot) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb || !bflag[b]) return;
+  st_tile[bstep[b]] = (int)(b / nkeys);
+  st_slot[bstep[b]] = (int)(b % nkeys);
+}
+
+__global__ void k_bin_fill(const int4* __restrict__ raw, const uint32_t* __restrict__ pbin, int n,
+                           const uint32_t* __restrict__ bstep, const int* __restrict__ ctile,
+                           int* __restrict__ st_src) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 v = raw[i];
+  st_src[(size_t)bstep[pbin[i]] * kTile + (ctile[v.x] % kTile)] = v.y;
 }
 
 __global__ void k_step_write2(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
@@ -665,61 +721,117 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
         int b = 0;
         while ((1ll << b) <= (long long)range) ++b;
         kp.shift[q] = sh;
+        kp.width[q] = b;
         sh += b;
       }
       kp.bits = sh;
       int tb = 1;
       while ((1ll << tb) < (long long)p->ntiles) ++tb;
       if (tb + kp.bits > 63) return FMM_E_DEPTH;
-      // 2. sort pairs by (tile, compact key): consecutive runs are the steps
-      ++g_launches;
-      k_step_keys2<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
-                                   p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
-      int second = 0;
-      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
-                             p->lv1.as<uint32_t>(), n, 0, tb + kp.bits, &second, p->sort_hist, p->scan_tmp, s));
-      uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
-      uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
-      ++g_launches;
-      k_step_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
-      FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
-      FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-      FMM_CUDA_TRY(cudaStreamSynchronize(s));
-      p->n_steps = hc[0];
-      const int64_t ns = p->n_steps;
-      FMM_TRY(p->st_tile.ensure((ns + 1) * sizeof(int)));
-      FMM_TRY(p->st_slot.ensure((ns + 1) * sizeof(int)));
-      FMM_TRY(p->st_src.ensure((ns + 1) * kTile * sizeof(int)));
-      FMM_TRY(p->st_ckey.ensure((ns + 1) * sizeof(uint64_t)));
-      FMM_TRY(p->st_fkey.ensure((ns + 1) * sizeof(uint64_t)));
-      FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (ns + 1) * kTile * sizeof(int), s));
-      ++g_launches;
-      k_step_write2<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
-                                    p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), p->c_tile.as<int>(), kp.bits,
-                                    p->st_tile.as<int>(),
-                                    p->st_ckey.as<uint64_t>(), p->st_fkey.as<uint64_t>(), p->st_src.as<int>());
-      ++g_launches;
-      k_tile_ranges<<<(unsigned)((ns + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)ns, p->tile_range.as<int2>());
-      // 3. distinct translations among the steps -> operator slots
-      FMM_TRY(p->ukeys.ensure((ns + 1) * sizeof(uint64_t)));
-      unsigned gs = (unsigned)((ns + T - 1) / T);
-      ++g_launches;
-      k_copy_u64_iota<<<gs, T, 0, s>>>(p->st_ckey.as<uint64_t>(), (int)ns, p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
-      FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
-                             p->lv1.as<uint32_t>(), ns, 0, std::max(kp.bits, 1), &second, p->sort_hist, p->scan_tmp,
-                             s));
-      sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
-      sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
-      ++g_launches;
-      k_unique_flags<<<gs, T, 0, s>>>(sk, (int)ns, p->tcount.as<uint32_t>());
-      FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ns, dcnt, p->scan_tmp, s));
-      ++g_launches;
-      k_step_slots<<<gs, T, 0, s>>>(sk, sv, (int)ns, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
-                                    p->st_fkey.as<uint64_t>(), p->ukeys.as<uint64_t>(), p->st_slot.as<int>());
-      FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-      FMM_CUDA_TRY(cudaStreamSynchronize(s));
-      p->n_keys = hc[0];
-      FMM_CUDA_TRY(cudaGetLastError());
+      const int64_t K = 1ll << kp.bits;
+      bool binned = false;
+      if (kp.bits <= kBinKeyBits && !(p->prm.m2l_mode & FMM_M2L_SORT_STEPS)) {
+        // 2'. the steps from flag tables (no sort) when the tables are small
+        FMM_TRY(p->bin_flag.ensure((size_t)(K + 1) * sizeof(uint32_t)));
+        FMM_TRY(p->bin_scan.ensure((size_t)(K + 1) * sizeof(uint32_t)));
+        uint32_t* kflag = p->bin_flag.as<uint32_t>();
+        uint32_t* kslot = p->bin_scan.as<uint32_t>();
+        FMM_CUDA_TRY(cudaMemsetAsync(kflag, 0, (size_t)K * sizeof(uint32_t), s));
+        ++g_launches;
+        k_key_mark<<<g, T, 0, s>>>(p->m2l_key.as<uint64_t>(), n, kp, kflag);
+        FMM_TRY(exclusive_scan_u32(kflag, kslot, K, dcnt, p->scan_tmp, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t nkeys = hc[0];
+        const int64_t nb = nkeys * (int64_t)p->ntiles;
+        if (nb <= kBinMax) {
+          binned = true;
+          p->n_keys = nkeys;
+          FMM_TRY(p->ukeys.ensure((size_t)(nkeys + 1) * sizeof(uint64_t)));
+          ++g_launches;
+          k_key_unpack<<<(unsigned)((K + T - 1) / T), T, 0, s>>>(kflag, kslot, K, kp, p->ukeys.as<uint64_t>());
+          // the key tables stay live: bins go to bin_flag2 / bin_scan2
+          FMM_TRY(p->bin_flag2.ensure((size_t)(nb + 1) * sizeof(uint32_t)));
+          FMM_TRY(p->bin_scan2.ensure((size_t)(nb + 1) * sizeof(uint32_t)));
+          uint32_t* bflag = p->bin_flag2.as<uint32_t>();
+          uint32_t* bstep = p->bin_scan2.as<uint32_t>();
+          uint32_t* pbin = p->lv0.as<uint32_t>();
+          FMM_CUDA_TRY(cudaMemsetAsync(bflag, 0, (size_t)nb * sizeof(uint32_t), s));
+          ++g_launches;
+          k_bin_mark<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
+                                     kslot, (int)nkeys, bflag, pbin);
+          FMM_TRY(exclusive_scan_u32(bflag, bstep, nb, dcnt, p->scan_tmp, s));
+          FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+          FMM_CUDA_TRY(cudaStreamSynchronize(s));
+          p->n_steps = hc[0];
+          const int64_t ns = p->n_steps;
+          FMM_TRY(p->st_tile.ensure((ns + 1) * sizeof(int)));
+          FMM_TRY(p->st_slot.ensure((ns + 1) * sizeof(int)));
+          FMM_TRY(p->st_src.ensure((ns + 1) * kTile * sizeof(int)));
+          FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (ns + 1) * kTile * sizeof(int), s));
+          ++g_launches;
+          k_bin_steps<<<(unsigned)((nb + T - 1) / T), T, 0, s>>>(bflag, bstep, nb, (int)nkeys, p->st_tile.as<int>(),
+                                                                 p->st_slot.as<int>());
+          ++g_launches;
+          k_bin_fill<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), pbin, n, bstep, p->c_tile.as<int>(),
+                                     p->st_src.as<int>());
+          ++g_launches;
+          k_tile_ranges<<<(unsigned)((ns + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)ns,
+                                                                  p->tile_range.as<int2>());
+          FMM_CUDA_TRY(cudaGetLastError());
+        }
+      }
+      if (!binned) {
+        // 2. sort pairs by (tile, compact key): consecutive runs are the steps
+        ++g_launches;
+        k_step_keys2<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
+                                     p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
+        int second = 0;
+        FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                               p->lv1.as<uint32_t>(), n, 0, tb + kp.bits, &second, p->sort_hist, p->scan_tmp, s));
+        uint64_t* sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
+        uint32_t* sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+        ++g_launches;
+        k_step_flags<<<g, T, 0, s>>>(sk, n, p->tcount.as<uint32_t>());
+        FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), n, dcnt, p->scan_tmp, s));
+        FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        p->n_steps = hc[0];
+        const int64_t ns = p->n_steps;
+        FMM_TRY(p->st_tile.ensure((ns + 1) * sizeof(int)));
+        FMM_TRY(p->st_slot.ensure((ns + 1) * sizeof(int)));
+        FMM_TRY(p->st_src.ensure((ns + 1) * kTile * sizeof(int)));
+        FMM_TRY(p->st_ckey.ensure((ns + 1) * sizeof(uint64_t)));
+        FMM_TRY(p->st_fkey.ensure((ns + 1) * sizeof(uint64_t)));
+        FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (ns + 1) * kTile * sizeof(int), s));
+        ++g_launches;
+        k_step_write2<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
+                                      p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), p->c_tile.as<int>(), kp.bits,
+                                      p->st_tile.as<int>(),
+                                      p->st_ckey.as<uint64_t>(), p->st_fkey.as<uint64_t>(), p->st_src.as<int>());
+        ++g_launches;
+        k_tile_ranges<<<(unsigned)((ns + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)ns, p->tile_range.as<int2>());
+        // 3. distinct translations among the steps -> operator slots
+        FMM_TRY(p->ukeys.ensure((ns + 1) * sizeof(uint64_t)));
+        unsigned gs = (unsigned)((ns + T - 1) / T);
+        ++g_launches;
+        k_copy_u64_iota<<<gs, T, 0, s>>>(p->st_ckey.as<uint64_t>(), (int)ns, p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
+        FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
+                               p->lv1.as<uint32_t>(), ns, 0, std::max(kp.bits, 1), &second, p->sort_hist, p->scan_tmp,
+                               s));
+        sk = second ? p->lk1.as<uint64_t>() : p->lk0.as<uint64_t>();
+        sv = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
+        ++g_launches;
+        k_unique_flags<<<gs, T, 0, s>>>(sk, (int)ns, p->tcount.as<uint32_t>());
+        FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ns, dcnt, p->scan_tmp, s));
+        ++g_launches;
+        k_step_slots<<<gs, T, 0, s>>>(sk, sv, (int)ns, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
+                                      p->st_fkey.as<uint64_t>(), p->ukeys.as<uint64_t>(), p->st_slot.as<int>());
+        FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        FMM_CUDA_TRY(cudaStreamSynchronize(s));
+        p->n_keys = hc[0];
+        FMM_CUDA_TRY(cudaGetLastError());
+      }
     }
   }
   FMM_CUDA_TRY(cudaStreamSynchronize(s));

@@ -357,6 +357,26 @@ def test_tensor_m2l_matches_simt(p):
     assert rel_l2(u2, u1) < 1e-5 and rel_l2(s2, s1) < 3e-5
 
 
+@pytest.mark.parametrize("case", ["lattice", "taylor_green", "plummer"])
+def test_binned_steps_equal_sorted_steps(case):
+    """M2L steps from the flag tables (translations, then (tile, translation)
+    bins) and from the radix sort of the pairs (FMM_M2L_SORT_STEPS) are the
+    same steps in the same order: bitwise equal outputs and work counts."""
+    from paper_1106_5273_gb300 import FMM_M2L_SORT_STEPS
+    if case == "lattice":
+        w, args = workloads.jittered_lattice(16), (6, 0.5, 32)
+    elif case == "taylor_green":
+        w, args = workloads.taylor_green(32), (10, 0.4, 64)
+    else:
+        w, args = workloads.plummer(20000), (8, 0.5, 32)
+        w["sigma"] = np.float32(0.002)
+    pa, u1, s1 = run_fmm(w, *args, m2l_mode=2)
+    pb, u2, s2 = run_fmm(w, *args, m2l_mode=2 | FMM_M2L_SORT_STEPS)
+    assert np.array_equal(u1, u2) and np.array_equal(s1, s2)
+    a, b = pa.stats(), pb.stats()
+    assert a.m2l_steps > 0 and (a.m2l_steps, a.m2l_keys, a.m2l_pairs) == (b.m2l_steps, b.m2l_keys, b.m2l_pairs)
+
+
 @pytest.mark.parametrize("m2l_mode", [2, 1])
 def test_full_size_taylor_green_128(m2l_mode):
     """2,097,152 blobs, p=10, theta=0.4, ncrit=64, periodic: the accuracy gate
