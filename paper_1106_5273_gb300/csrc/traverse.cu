@@ -435,7 +435,8 @@ __global__ void k_tile_order_keys(const int* __restrict__ level, const uint64_t*
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int oct = (int)(ckey[c] & 7ull);
-  keys[c] = ((uint64_t)level[c] << 40) | ((uint64_t)oct << 32) | (uint64_t)c;
+  // the sort is stable, so cells of a group keep their (Morton) index order
+  keys[c] = ((uint64_t)level[c] << 3) | (uint64_t)oct;
   vals[c] = (uint32_t)c;
   atomicAdd(&gcount[level[c] * 8 + oct], 1);
 }
@@ -661,7 +662,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
                                          p->lv0.as<uint32_t>(), gcount);
       int second = 0;
       FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
-                             p->lv1.as<uint32_t>(), nc, 0, 48, &second, p->sort_hist, p->scan_tmp, s));
+                             p->lv1.as<uint32_t>(), nc, 0, 8, &second, p->sort_hist, p->scan_tmp, s));
       uint32_t* ord = second ? p->lv1.as<uint32_t>() : p->lv0.as<uint32_t>();
       int* hg = reinterpret_cast<int*>(reinterpret_cast<char*>(p->pinned) + 1024);  // counts, then offsets
       FMM_CUDA_TRY(cudaMemcpyAsync(hg, gcount, kGroups * sizeof(int), cudaMemcpyDeviceToHost, s));
