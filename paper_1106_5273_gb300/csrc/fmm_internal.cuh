@@ -15,6 +15,7 @@ constexpr int kScalBox = 0;     // box_min[3], box_len
 constexpr int kScalDipole = 4;  // dipole velocity correction [3] (double)
 constexpr int kScalSigma = 8;   // float bits of max sigma (per-particle sigma)
 constexpr int kScalCount = 16;  // u32 counters area
+constexpr int kScalKeySpan = 40;  // AND and OR of the Morton keys (u64 each)
 constexpr int kBatchBits = 16;  // Morton bits per axis of a batched evaluation (depth cap 16)
 constexpr int kMaxBatch = 1 << (63 - 3 * kBatchBits);  // problems per batched evaluation
 

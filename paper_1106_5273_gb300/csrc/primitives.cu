@@ -306,7 +306,7 @@ int iota_u32(uint32_t* v, int64_t n, cudaStream_t s) {
 // Sort (keys, vals) by key bits [bit_begin, bit_end).  Input in (k0,v0);
 // on return *in_second says whether the result is in (k1,v1).
 int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int bit_begin,
-                   int bit_end, int* in_second, DBuf& hist, DBuf& scan_tmp, cudaStream_t s) {
+                   int bit_end, int* in_second, DBuf& hist, DBuf& scan_tmp, cudaStream_t s, uint64_t vary) {
   *in_second = 0;
   if (n <= 1) return FMM_OK;
   int ntiles = (int)((n + kSortTile - 1) / kSortTile);
@@ -316,6 +316,8 @@ int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64
   uint32_t* va = v0;
   uint32_t* vb = v1;
   for (int shift = bit_begin; shift < bit_end; shift += 8) {
+    const int w = bit_end - shift < 8 ? bit_end - shift : 8;
+    if (((vary >> shift) & ((1ull << w) - 1ull)) == 0ull) continue;  // constant digit: identity pass
     ++g_launches;
     k_sort_hist<<<ntiles, kSortThreads, 0, s>>>(ka, n, shift, ntiles, hist.as<uint32_t>());
     FMM_TRY(exclusive_scan_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), (int64_t)256 * ntiles, nullptr,

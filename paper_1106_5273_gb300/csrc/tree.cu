@@ -170,19 +170,34 @@ __device__ inline uint64_t quantize_axis(float x, double bmin, double blen, doub
 }
 
 // kbits Morton bits per axis; a batch puts the problem index above them.
+// span (if given) gathers the AND and the OR of all keys (one atomic each per
+// warp): their XOR marks the key bits that vary.
 __global__ void k_keys(const float* __restrict__ pos, int64_t n, const double* __restrict__ box,
                        const int* __restrict__ off, int nseg, int kbits, uint64_t* __restrict__ keys,
-                       uint32_t* __restrict__ idx) {
+                       uint32_t* __restrict__ idx, unsigned long long* __restrict__ span) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int sg = off ? seg_of(off, nseg, i) : 0;
-  const double* b = box + 4 * sg;
-  const double blen = b[3], scale = ldexp(1.0, kbits);
-  uint64_t kx = quantize_axis(pos[3 * i + 0], b[0], blen, scale);
-  uint64_t ky = quantize_axis(pos[3 * i + 1], b[1], blen, scale);
-  uint64_t kz = quantize_axis(pos[3 * i + 2], b[2], blen, scale);
-  keys[i] = ((uint64_t)sg << (3 * kbits)) | (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
-  idx[i] = (uint32_t)i;
+  unsigned long long ka = ~0ull, ko = 0ull;
+  if (i < n) {
+    const int sg = off ? seg_of(off, nseg, i) : 0;
+    const double* b = box + 4 * sg;
+    const double blen = b[3], scale = ldexp(1.0, kbits);
+    uint64_t kx = quantize_axis(pos[3 * i + 0], b[0], blen, scale);
+    uint64_t ky = quantize_axis(pos[3 * i + 1], b[1], blen, scale);
+    uint64_t kz = quantize_axis(pos[3 * i + 2], b[2], blen, scale);
+    const uint64_t k = ((uint64_t)sg << (3 * kbits)) | (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
+    keys[i] = k;
+    idx[i] = (uint32_t)i;
+    ka = ko = k;
+  }
+  if (!span) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    ka &= __shfl_xor_sync(0xffffffffu, ka, o);
+    ko |= __shfl_xor_sync(0xffffffffu, ko, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (int64_t)blockIdx.x * blockDim.x + threadIdx.x < n) {
+    atomicAnd(&span[0], ka);
+    atomicOr(&span[1], ko);
+  }
 }
 
 // Sorted position i of a batch lies in its problem's input range.
@@ -492,11 +507,20 @@ int build_tree(fmm_plan p, int64_t n, const float* pos, const float* gam, const 
   uint64_t* k1 = p->keys1.as<uint64_t>();
   uint32_t* v0 = p->vals0.as<uint32_t>();
   uint32_t* v1 = p->vals1.as<uint32_t>();
+  unsigned long long* span = reinterpret_cast<unsigned long long*>(box + kScalKeySpan);
+  FMM_CUDA_TRY(cudaMemsetAsync(span, 0xff, sizeof(unsigned long long), s));
+  FMM_CUDA_TRY(cudaMemsetAsync(span + 1, 0, sizeof(unsigned long long), s));
   ++g_launches;
-  k_keys<<<nb, T, 0, s>>>(pos, n, box, nullptr, 1, kMaxLevel, k0, v0);
+  k_keys<<<nb, T, 0, s>>>(pos, n, box, nullptr, 1, kMaxLevel, k0, v0, span);
   FMM_CUDA_TRY(cudaGetLastError());
+  // sort passes over digits that no key changes are skipped (a lattice leaves
+  // its low bits constant)
+  unsigned long long* hspan = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(p->pinned) + 512);
+  FMM_CUDA_TRY(cudaMemcpyAsync(hspan, span, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint64_t vary = hspan[0] ^ hspan[1];
   int second = 0;
-  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 63, &second, p->sort_hist, p->scan_tmp, s));
+  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 63, &second, p->sort_hist, p->scan_tmp, s, vary));
   p->skeys = second ? k1 : k0;
   p->sidx = second ? v1 : v0;
   ++g_launches;
@@ -570,13 +594,20 @@ int build_forest(fmm_plan p, int64_t n, const float* pos, const float* gam, cons
   uint64_t* k1 = p->keys1.as<uint64_t>();
   uint32_t* v0 = p->vals0.as<uint32_t>();
   uint32_t* v1 = p->vals1.as<uint32_t>();
+  unsigned long long* span = reinterpret_cast<unsigned long long*>(p->scal.as<double>() + kScalKeySpan);
+  FMM_CUDA_TRY(cudaMemsetAsync(span, 0xff, sizeof(unsigned long long), s));
+  FMM_CUDA_TRY(cudaMemsetAsync(span + 1, 0, sizeof(unsigned long long), s));
   ++g_launches;
-  k_keys<<<nb, T, 0, s>>>(pos, n, box, off, S, kBatchBits, k0, v0);
+  k_keys<<<nb, T, 0, s>>>(pos, n, box, off, S, kBatchBits, k0, v0, span);
   FMM_CUDA_TRY(cudaGetLastError());
+  unsigned long long* hspan = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(p->pinned) + 512);
+  FMM_CUDA_TRY(cudaMemcpyAsync(hspan, span, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  FMM_CUDA_TRY(cudaStreamSynchronize(s));
   int sbits = 0;
   while ((1 << sbits) < S) ++sbits;
   int second = 0;
-  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 3 * kBatchBits + sbits, &second, p->sort_hist, p->scan_tmp, s));
+  FMM_TRY(radix_sort_u64(k0, v0, k1, v1, n, 0, 3 * kBatchBits + sbits, &second, p->sort_hist, p->scan_tmp, s,
+                         hspan[0] ^ hspan[1]));
   p->skeys = second ? k1 : k0;
   p->sidx = second ? v1 : v0;
   ++g_launches;
@@ -605,7 +636,7 @@ int morton_keys_raw(int64_t n, const float* pos, int periodic, const double* box
     k_bbox_final<<<1, 32, 0, s>>>(partials, parts, box);
   }
   ++g_launches;
-  k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, box, nullptr, 1, kMaxLevel, keys, idx);
+  k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, box, nullptr, 1, kMaxLevel, keys, idx, nullptr);
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
