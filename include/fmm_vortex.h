@@ -56,7 +56,7 @@ enum {
   /* Flag, OR'ed with a mode: build the (tile, translation) steps by a radix
    * sort of the M2L pairs.  Without it the steps come from flag tables over
    * the translations and (tile, translation) bins whenever those tables are
-   * small (compact keys of <= 22 bits, <= 2^26 bins), else from the sort.
+   * small (compact keys of <= 22 bits, <= 2^28 bins), else from the sort.
    * Both give the same steps in the same order. */
   FMM_M2L_SORT_STEPS = 8
 };

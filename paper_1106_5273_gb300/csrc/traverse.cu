@@ -298,10 +298,10 @@ __global__ void k_key_ranges(const uint64_t* __restrict__ keys, int n, int* __re
 }
 
 // Limits of the binned step build: compact keys of at most 22 bits (a 16 MB
-// flag table) and at most 2^26 (tile, translation) bins; beyond either the
-// steps come from the sort.
+// flag table) and at most 2^28 (tile, translation) bins (two 1 GB tables;
+// 512^3 blobs need ~1.2e8); beyond either the steps come from the sort.
 constexpr int kBinKeyBits = 22;
-constexpr int64_t kBinMax = 1ll << 26;
+constexpr int64_t kBinMax = 1ll << 28;
 
 struct KeyPack {
   int lo[4];
