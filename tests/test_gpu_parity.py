@@ -164,6 +164,24 @@ def test_fmm_periodic_random_matches_fourier():
     assert rel_l2(u, uf) < 1.5 * rel_l2(ref.u, uf) + TOL_U
 
 
+def test_exact_lattice_skips_constant_key_digits():
+    """Blobs on the exact binary lattice (i + 1/2)/8 of the periodic unit cube:
+    every key has its low 51 bits constant, so the Morton sort runs only the
+    passes over digits that vary.  Keys, order, cells and lists stay bit-exact
+    against the oracle, and the FMM matches the oracle FMM on them."""
+    g = (np.arange(8, dtype=np.float64) + 0.5) / 8.0
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    gam = workloads.rng(41).standard_normal(pos.shape).astype(np.float32)
+    gam -= gam.astype(np.float64).mean(0).astype(np.float32)
+    w = dict(pos=pos, gamma=gam, sigma=np.float32(1.5 / 8), periodic=True, box_min=np.zeros(3), box_len=1.0)
+    plan, u, s = run_fmm(w, 6, 0.5, 16, m2l_mode=1)
+    ref = _oracle_fmm(w, 6, 0.5, 16)
+    _check_tree_and_lists(plan, ref, True)
+    _, keys = plan.order()
+    assert np.all((np.asarray(keys, np.uint64) & np.uint64((1 << 48) - 1)) == 0)  # 6 of 8 digits constant
+    assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
+
+
 def _spectrum_check(n, sample=4096):
     """Random-phase spectrum blobs (E ~ k^4 exp(-2 (k/k0)^2), k0 = 4) in the
     periodic cube, p=10, theta=0.4, ncrit=64, 3^3 images + lattice operator,
