@@ -61,6 +61,12 @@ enum {
   FMM_M2L_SORT_STEPS = 8
 };
 
+/* Core width of a pair when every blob carries its own sigma (a sigma array). */
+enum {
+  FMM_SIGMA_SOURCE = 0, /* sigma_j of the source blob (Eq. 2 as written) */
+  FMM_SIGMA_MIXED = 1   /* sigma_ij = sqrt((sigma_i^2 + sigma_j^2) / 2): symmetric in i, j */
+};
+
 typedef struct fmm_plan_s* fmm_plan;
 
 /*
@@ -82,6 +88,10 @@ typedef struct fmm_plan_s* fmm_plan;
  *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
  *              output pointer skips that output.
  *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR, optionally | FMM_M2L_SORT_STEPS.
+ *   sigma_rule FMM_SIGMA_SOURCE (default) or FMM_SIGMA_MIXED: the core width
+ *              of a near-field pair when a sigma array is given (with one
+ *              sigma both rules agree).  The far-field separation and the
+ *              pair classes use the largest sigma, which bounds both.
  */
 typedef struct {
   int32_t p;
@@ -94,6 +104,7 @@ typedef struct {
   float sigma_sep;
   int32_t outputs;
   int32_t m2l_mode;
+  int32_t sigma_rule;
 } fmm_params;
 
 /* Work counts of the last evaluation (for throughput and roofline reports). */
@@ -324,7 +335,8 @@ const char* fmm_strerror(int code);
  * evaluated by the same FMM; a target that coincides with a source gets the
  * regularized field there.  Velocity only.  Per-source core widths: the
  * targets take the largest source width, so the far-field separation and
- * the pair classes are those of the sources.  Same stream and blocking
+ * the pair classes are those of the sources; pairs take the source width
+ * sigma_j whatever the plan's sigma_rule (a point has no width of its own).  Same stream and blocking
  * behaviour as fmm_eval_velocity_stretching; FMM_E_INVAL for bad arguments.
  */
 int fmm_eval_targets(fmm_plan plan, int64_t ns, const float* src_pos, const float* src_gamma,

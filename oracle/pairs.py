@@ -4,7 +4,9 @@ Reading of the paper used here (Sec. 2.1, Eqs. 1-3):
   * G = 1/(4 pi r) and grad G g_sigma means (grad G) times g, with the gradient
     taken so that u_i = (1/4pi) sum_j g(rho)/r^3 (gamma_j x d), d = x_i - x_j,
     the velocity of a Gaussian blob of vorticity.
-  * The cutoff of Eq. (2) uses the SOURCE core width sigma_j.
+  * The cutoff of Eq. (2) uses the SOURCE core width sigma_j.  The mixed
+    rule (an option, for blobs of different widths) uses the symmetric
+    sigma_ij = sqrt((sigma_i^2 + sigma_j^2) / 2) instead.
   * Eq. (3) is the classical scheme (gamma_i . grad) u evaluated at x_i, which
     for one pair gives S (gamma_j x gamma_i) + T (gamma_i . d)(gamma_j x d)
     with S = g/r^3 and T = S'(r)/r.  The transpose scheme (grad u)^T gamma_i
@@ -79,13 +81,15 @@ def S_T(r2, sigma):
     return S, T
 
 
-def pair_sum(xt, gt, xs, gs, sig, shift=None, skip=None, transpose=False):
+def pair_sum(xt, gt, xs, gs, sig, shift=None, skip=None, transpose=False, sig_t=None):
     """Velocity and stretching at targets xt[nt,3] (strengths gt) from sources.
 
     shift: per-source shift [ns,3] added to d = x_i - x_j (exact difference
     first, then the shift), or None.  skip: boolean [nt, ns] mask of pairs to
     leave out (the self pair), or None.  transpose: the transpose stretching
-    scheme.  Returns u[nt,3], s[nt,3] in FP64.
+    scheme.  sig_t: target core widths [nt] for the mixed rule (pair width
+    sqrt((sig_t^2 + sig^2)/2)), or None for the source rule.  Returns u[nt,3],
+    s[nt,3] in FP64.
     """
     xt = np.asarray(xt, np.float64)
     xs = np.asarray(xs, np.float64)
@@ -96,7 +100,12 @@ def pair_sum(xt, gt, xs, gs, sig, shift=None, skip=None, transpose=False):
     if shift is not None:
         d = d + np.asarray(shift, np.float64)[None, :, :]
     r2 = d[..., 0] ** 2 + d[..., 1] ** 2 + d[..., 2] ** 2
-    S, T = S_T(r2, np.broadcast_to(sig[None, :], r2.shape))
+    if sig_t is None:
+        sp = np.broadcast_to(sig[None, :], r2.shape)
+    else:
+        st = np.broadcast_to(np.asarray(sig_t, np.float64), (xt.shape[0],))
+        sp = np.sqrt(0.5 * (st[:, None] ** 2 + sig[None, :] ** 2))
+    S, T = S_T(r2, sp)
     if skip is not None:
         S = np.where(skip, 0.0, S)
         T = np.where(skip, 0.0, T)

@@ -15,6 +15,7 @@ library_path = os.path.join(HERE, "_lib", "libfmm_vortex.so")
 FMM_OK = 0
 FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
 FMM_M2L_SORT_STEPS = 8
+FMM_SIGMA_SOURCE, FMM_SIGMA_MIXED = 0, 1
 FMM_OUT_VELOCITY, FMM_OUT_STRETCHING, FMM_OUT_STRETCHING_TRANSPOSE = 1, 2, 4
 
 
@@ -35,7 +36,7 @@ class Params(ctypes.Structure):
                 ("periodic", ctypes.c_int32), ("images", ctypes.c_int32),
                 ("box_min", ctypes.c_double * 3), ("box_len", ctypes.c_double),
                 ("sigma_sep", ctypes.c_float), ("outputs", ctypes.c_int32),
-                ("m2l_mode", ctypes.c_int32)]
+                ("m2l_mode", ctypes.c_int32), ("sigma_rule", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw):

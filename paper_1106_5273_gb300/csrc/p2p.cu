@@ -98,6 +98,29 @@ __host__ __device__ inline SigK make_sigk(float sigma) {
   return k;
 }
 
+// The constants of make_sigk for the mixed core width of a pair,
+// sigma_ij^2 = (sigma_i^2 + sigma_j^2) / 2, in FP32 (one division and one
+// rsqrt per pair).
+__device__ __forceinline__ SigK sigk_mixed(float si, float sj) {
+  const float s2 = 0.5f * fmaf(si, si, sj * sj);
+  const float iu = 1.f / s2;        // 1 / sigma^2
+  const float is = rsqrtf(s2);      // 1 / sigma
+  const float sg = s2 * is;         // sigma
+  const float is3 = iu * is;        // 1 / sigma^3
+  SigK k;
+  k.kq = -0.72134752044448170f * iu;  // -log2(e) / 2
+  k.kc = -0.26596152026762179f * is3;  // -sqrt(2/pi) / 3
+  k.ku = iu;
+  k.is3 = is3;
+  k.is5 = (-2.f / 3.f) * is3 * iu;
+  k.hn0 = -0.79788456080286535588f * is;
+  k.hn1 = -kE0;
+  k.hn2 = -kE1 * 1.41421356237309515f * sg;
+  k.hn3 = -kE2 * 2.f * s2;
+  k.hn4 = -kE3 * 2.82842712474619030f * s2 * sg;
+  return k;
+}
+
 // S = g/r^3 and T' = -S'(r)/(3r) for one pair (see the file header); ST = 0:
 // S only (velocity without stretching).
 template <int MODE, int ST = 1>
@@ -206,13 +229,15 @@ template <int TPT>
 struct TgtR {
   float x[TPT], y[TPT], z[TPT], gx[TPT], gy[TPT], gz[TPT];  // X_i (leaf-relative) and gamma_i
   float mx[TPT], my[TPT], mz[TPT];                          // m_i = X_i x gamma_i (transpose scheme)
+  float sg[TPT];                                            // sigma_i (mixed core width)
   int self[TPT];
   AccR a[TPT];
 };
 
+// mixed (PS only): the pair's core width is sigma_ij (sigk_mixed), not sigma_j.
 template <bool PS, int MODE, bool SELF, int TPT, int ST>
 __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
-                                              int jb, int je, TgtR<TPT>& t, const SigK& K0) {
+                                              int jb, int je, TgtR<TPT>& t, const SigK& K0, bool mixed) {
 #pragma unroll 4
   for (int j = jb; j < je; ++j) {
     const float4 xj = sA[j];
@@ -222,7 +247,8 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
     for (int q = 0; q < TPT; ++q) {
       if (SELF && j == t.self[q]) continue;
       pair_acc_rel<MODE, ST>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, xj, gj, kj, t.gx[q], t.gy[q], t.gz[q],
-                             t.mx[q], t.my[q], t.mz[q], PS ? sK[j] : K0, t.a[q]);
+                             t.mx[q], t.my[q], t.mz[q],
+                             PS ? (mixed ? sigk_mixed(t.sg[q], xj.w) : sK[j]) : K0, t.a[q]);
     }
   }
 }
@@ -233,14 +259,14 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
 template <bool PS, int TPT, int ST>
 __device__ __forceinline__ void dispatch_rel(bool self, int nf, int nm, const float4* sA, const float4* sB,
                                              const float4* sC, const SigK* sK, int cnt, TgtR<TPT>& t,
-                                             const SigK& K0) {
+                                             const SigK& K0, bool mixed) {
   if (self) {
-    run_chunk_rel<PS, kNear, true, TPT, ST>(sA, sB, sC, sK, 0, cnt, t, K0);
+    run_chunk_rel<PS, kNear, true, TPT, ST>(sA, sB, sC, sK, 0, cnt, t, K0, mixed);
     return;
   }
-  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT, ST>(sA, sB, sC, sK, 0, nf, t, K0);
-  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT, ST>(sA, sB, sC, sK, nf, nf + nm, t, K0);
-  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT, ST>(sA, sB, sC, sK, nf + nm, cnt, t, K0);
+  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT, ST>(sA, sB, sC, sK, 0, nf, t, K0, mixed);
+  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT, ST>(sA, sB, sC, sK, nf, nf + nm, t, K0, mixed);
+  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT, ST>(sA, sB, sC, sK, nf + nm, cnt, t, K0, mixed);
 }
 
 // Axis-aligned bounding box of the targets of one tile, relative to the leaf
@@ -384,7 +410,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
                                             const float* __restrict__ far_u, const float* __restrict__ far_s,
                                             const uint32_t* __restrict__ sidx, float blen, float smax, float margin0,
                                             SigK K0, const double* __restrict__ dip, const int* __restrict__ cseg,
-                                            const SegP2P* __restrict__ sp, float* __restrict__ vel,
+                                            const SegP2P* __restrict__ sp, int mixed, float* __restrict__ vel,
                                             float* __restrict__ dg, unsigned long long* __restrict__ ccount) {
   constexpr int CH = 32 * TPT;
   __shared__ float4 sA[2][CH], sB[2][CH], sC[2][CH];
@@ -449,6 +475,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       t.gx[q] = gi.x;
       t.gy[q] = gi.y;
       t.gz[q] = gi.z;
+      t.sg[q] = xi.w;
       t.mx[q] = t.y[q] * gi.z - t.z[q] * gi.y;
       t.my[q] = t.z[q] * gi.x - t.x[q] * gi.z;
       t.mz[q] = t.x[q] * gi.y - t.y[q] * gi.x;
@@ -499,7 +526,8 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       const bool self = (ent.x == leaf) && ent.y == kImageZero;
 #pragma unroll
       for (int q = 0; q < TPT; ++q) t.self[q] = self ? (t0 + lane + 32 * q) - cur_c0 : -1;
-      dispatch_rel<PS, TPT, ST>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0);
+      dispatch_rel<PS, TPT, ST>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0,
+                                PS && mixed);
       c_far += nt * (unsigned long long)cur_nf;
       c_mid += nt * (unsigned long long)cur_nm;
       c_near += nt * (unsigned long long)(cur_cnt - cur_nf - cur_nm);
@@ -1044,6 +1072,7 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   const float smaxf = (float)smax;
   const float margin0 = (float)p->cf_margin;
   const bool two = p->prm.ncrit > 32;
+  const int mixed = ps && p->prm.sigma_rule == FMM_SIGMA_MIXED;
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
   ++g_launches;
@@ -1059,7 +1088,7 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   }
 #define FMM_P2P_LAUNCH(PS_, TPT_, SEG_, ST_)                                                                 \
   k_p2p<PS_, TPT_, SEG_, ST_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, \
-                                               smaxf, margin0, K0, dip, cseg, sp, vel, dg, cnt)
+                                               smaxf, margin0, K0, dip, cseg, sp, mixed, vel, dg, cnt)
 #define FMM_P2P_X2_LAUNCH(SEG_, ST_)                                                                          \
   k_p2p_x2<SEG_, ST_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf,     \
                                        margin0, K0, dip, cseg, sp, vel, dg, cnt)

@@ -64,7 +64,12 @@ extern "C" int fmm_eval_targets(fmm_plan p, int64_t ns, const float* src_pos, co
     k_sigma_fill<<<1, 1024, 0, s>>>(src_sigma, ns, sig + ns, nt);
     FMM_CUDA_TRY(cudaGetLastError());
   }
-  FMM_TRY(fmm_eval_velocity_stretching(p, n, pos, gam, sig, sigma_uniform, p->t_vel.as<float>(), nullptr, stream));
+  // a point target has no core width of its own: the source rule applies
+  const int rule = p->prm.sigma_rule;
+  p->prm.sigma_rule = FMM_SIGMA_SOURCE;
+  const int rc = fmm_eval_velocity_stretching(p, n, pos, gam, sig, sigma_uniform, p->t_vel.as<float>(), nullptr, stream);
+  p->prm.sigma_rule = rule;
+  FMM_TRY(rc);
   FMM_CUDA_TRY(cudaMemcpyAsync(vel, p->t_vel.as<float>() + 3 * ns, (size_t)nt * 12, cudaMemcpyDeviceToDevice, s));
   return FMM_OK;
 }

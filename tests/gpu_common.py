@@ -13,7 +13,8 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None, outputs=None):
+def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None, outputs=None,
+            sigma_rule=None):
     import torch
     from paper_1106_5273_gb300 import Plan, Params
     pos, gam = w["pos"], w["gamma"]
@@ -24,6 +25,8 @@ def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=N
         kw.update(periodic=1, box_min=w["box_min"], box_len=w["box_len"], images=images or w.get("images", 3))
     if outputs is not None:
         kw.update(outputs=outputs)
+    if sigma_rule is not None:
+        kw.update(sigma_rule=sigma_rule)
     plan = Plan(max(n, 1), Params.default(**kw))
     dp, dg = to_dev(pos), to_dev(gam)
     ds = to_dev(sigma_arr) if sigma_arr is not None else None

@@ -220,6 +220,35 @@ def test_fmm_per_particle_sigma_and_plummer():
     assert rel_l2(u, ud) < 2e-4 and rel_l2(s, sd) < 1e-3
 
 
+@pytest.mark.parametrize("transpose", [False, True])
+def test_fmm_mixed_core_width_rule(transpose):
+    """Per-particle widths with the mixed rule sigma_ij = sqrt((sigma_i^2 +
+    sigma_j^2)/2) (FMM_SIGMA_MIXED) on a Plummer cloud, against the FP64 pair
+    sum with the same rule.  The source rule gives a different field (30% in
+    u here), and with the transpose scheme the mixed rule conserves total
+    vorticity (the source rule misses it by 2%)."""
+    from oracle import pairs
+    from paper_1106_5273_gb300 import FMM_SIGMA_MIXED
+    w = workloads.plummer(3000)
+    n = w["pos"].shape[0]
+    sig = (w["sigma"] * np.linspace(0.7, 1.3, n)).astype(np.float32)
+    outs = 7 if transpose else None  # velocity | stretching | transpose scheme
+    plan, u, s = run_fmm(dict(w, sigma=1.0), 8, 0.5, 16, m2l_mode=1, sigma_arr=sig, outputs=outs,
+                         sigma_rule=FMM_SIGMA_MIXED)
+    x, g, sg = (a.astype(np.float64) for a in (w["pos"], w["gamma"], sig))
+    ud, sd = np.zeros((n, 3)), np.zeros((n, 3))
+    for a in range(0, n, 500):
+        b = min(n, a + 500)
+        skip = np.zeros((b - a, n), bool)
+        skip[np.arange(b - a), np.arange(a, b)] = True
+        ud[a:b], sd[a:b] = pairs.pair_sum(x[a:b], g[a:b], x, g, sg, None, skip, transpose=transpose, sig_t=sg[a:b])
+    assert rel_l2(u, ud) < 2e-4 and rel_l2(s, sd) < 1e-3
+    _, u_src, _ = run_fmm(dict(w, sigma=1.0), 8, 0.5, 16, m2l_mode=1, sigma_arr=sig, outputs=outs)
+    assert rel_l2(u_src, ud) > 0.1
+    if transpose:
+        assert np.abs(s.sum(0)).max() < 1e-3 * np.abs(s).sum(0).max()
+
+
 @pytest.mark.parametrize("case", ["taylor-green-16", "plummer-free", "plummer-free-transpose"])
 def test_packed_p2p_bitwise_equals_scalar_kernel(case):
     """Two targets per lane (ncrit > 32) with one core width run the packed

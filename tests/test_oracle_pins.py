@@ -183,6 +183,36 @@ def test_transpose_scheme_conserves_total_vorticity():
     assert np.abs(sc.sum(0)).max() > 1e-3 * np.abs(sc).sum(0).max()
 
 
+def test_mixed_core_width_rule():
+    # The mixed rule sigma_ij = sqrt((sigma_i^2 + sigma_j^2)/2) (an option for
+    # blobs of different widths).  With one width it is the source rule.  It is
+    # symmetric in i and j, so (a) two equal blobs move with opposite
+    # velocities, and (b) the transpose scheme conserves total vorticity for
+    # any widths; the source rule with different widths does neither.
+    c = workloads.random_cloud(60, seed=23, box=0.5)
+    x, g = c["pos"], c["gamma"]
+    n = x.shape[0]
+    skip = np.eye(n, dtype=bool)
+    u0, s0 = pairs.pair_sum(x, g, x, g, 0.07, None, skip)
+    u1, s1 = pairs.pair_sum(x, g, x, g, 0.07, None, skip, sig_t=np.full(n, 0.07))
+    assert np.allclose(u1, u0, rtol=1e-13, atol=0) and np.allclose(s1, s0, rtol=1e-13, atol=0)
+    # (a) two blobs of the same strength and different widths
+    x2 = np.array([[0.0, 0.0, 0.0], [0.05, 0.02, -0.01]])
+    g2 = np.array([[0.3, -0.2, 0.9], [0.3, -0.2, 0.9]])
+    sg2 = np.array([0.03, 0.08])
+    skip2 = np.eye(2, dtype=bool)
+    um, _ = pairs.pair_sum(x2, g2, x2, g2, sg2, None, skip2, sig_t=sg2)
+    us, _ = pairs.pair_sum(x2, g2, x2, g2, sg2, None, skip2)
+    assert np.allclose(um[0], -um[1], rtol=1e-14, atol=0)
+    assert np.abs(us[0] + us[1]).max() > 1e-2 * np.abs(us).max()
+    # (b) total vorticity under the transpose scheme, widths 0.04 .. 0.1
+    sg = np.linspace(0.04, 0.1, n)
+    _, stm = pairs.pair_sum(x, g, x, g, sg, None, skip, transpose=True, sig_t=sg)
+    _, sts = pairs.pair_sum(x, g, x, g, sg, None, skip, transpose=True)
+    assert np.abs(stm.sum(0)).max() < 1e-12 * np.abs(stm).sum(0).max()
+    assert np.abs(sts.sum(0)).max() > 1e-3 * np.abs(sts).sum(0).max()
+
+
 def test_translation_and_rotation_covariance():
     c = workloads.random_cloud(40, seed=8)
     x = c["pos"].astype(np.float64)
