@@ -234,10 +234,10 @@ struct TgtR {
   AccR a[TPT];
 };
 
-// mixed (PS only): the pair's core width is sigma_ij (sigk_mixed), not sigma_j.
-template <bool PS, int MODE, bool SELF, int TPT, int ST>
+// MIX (PS only): the pair's core width is sigma_ij (sigk_mixed), not sigma_j.
+template <bool PS, int MODE, bool SELF, int TPT, int ST, bool MIX>
 __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB, const float4* sC, const SigK* sK,
-                                              int jb, int je, TgtR<TPT>& t, const SigK& K0, bool mixed) {
+                                              int jb, int je, TgtR<TPT>& t, const SigK& K0) {
 #pragma unroll 4
   for (int j = jb; j < je; ++j) {
     const float4 xj = sA[j];
@@ -248,7 +248,7 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
       if (SELF && j == t.self[q]) continue;
       pair_acc_rel<MODE, ST>(t.x[q] - xj.x, t.y[q] - xj.y, t.z[q] - xj.z, xj, gj, kj, t.gx[q], t.gy[q], t.gz[q],
                              t.mx[q], t.my[q], t.mz[q],
-                             PS ? (mixed ? sigk_mixed(t.sg[q], xj.w) : sK[j]) : K0, t.a[q]);
+                             MIX ? sigk_mixed(t.sg[q], xj.w) : (PS ? sK[j] : K0), t.a[q]);
     }
   }
 }
@@ -256,17 +256,17 @@ __device__ __forceinline__ void run_chunk_rel(const float4* sA, const float4* sB
 // The groups of a staged chunk: sources [0, nf) far, [nf, nf + nm) mid, the
 // rest near; the self entry (not grouped) runs the near form with the self
 // pair skipped.
-template <bool PS, int TPT, int ST>
+template <bool PS, int TPT, int ST, bool MIX>
 __device__ __forceinline__ void dispatch_rel(bool self, int nf, int nm, const float4* sA, const float4* sB,
                                              const float4* sC, const SigK* sK, int cnt, TgtR<TPT>& t,
-                                             const SigK& K0, bool mixed) {
+                                             const SigK& K0) {
   if (self) {
-    run_chunk_rel<PS, kNear, true, TPT, ST>(sA, sB, sC, sK, 0, cnt, t, K0, mixed);
+    run_chunk_rel<PS, kNear, true, TPT, ST, MIX>(sA, sB, sC, sK, 0, cnt, t, K0);
     return;
   }
-  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT, ST>(sA, sB, sC, sK, 0, nf, t, K0, mixed);
-  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT, ST>(sA, sB, sC, sK, nf, nf + nm, t, K0, mixed);
-  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT, ST>(sA, sB, sC, sK, nf + nm, cnt, t, K0, mixed);
+  if (nf > 0) run_chunk_rel<PS, kFar, false, TPT, ST, MIX>(sA, sB, sC, sK, 0, nf, t, K0);
+  if (nm > 0) run_chunk_rel<PS, kMid, false, TPT, ST, MIX>(sA, sB, sC, sK, nf, nf + nm, t, K0);
+  if (nf + nm < cnt) run_chunk_rel<PS, kNear, false, TPT, ST, MIX>(sA, sB, sC, sK, nf + nm, cnt, t, K0);
 }
 
 // Axis-aligned bounding box of the targets of one tile, relative to the leaf
@@ -402,7 +402,7 @@ __device__ __forceinline__ void run_chunk(const float4* sA, const float4* sB, co
 // SEG: a batch of problems; the leaf's problem supplies sigma, the class
 // bounds, the image shift and the dipole correction instead of the arguments.
 // ST: 0 velocity only (dg is not written), 1 classical, 2 transpose stretching.
-template <bool PS, int TPT, bool SEG, int ST>
+template <bool PS, int TPT, bool SEG, int ST, bool MIX>
 __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, const int2* __restrict__ off,
                                             const int2* __restrict__ list, const int* __restrict__ begin,
                                             const int* __restrict__ end, const float4* __restrict__ cf,
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
                                             const float* __restrict__ far_u, const float* __restrict__ far_s,
                                             const uint32_t* __restrict__ sidx, float blen, float smax, float margin0,
                                             SigK K0, const double* __restrict__ dip, const int* __restrict__ cseg,
-                                            const SegP2P* __restrict__ sp, int mixed, float* __restrict__ vel,
+                                            const SegP2P* __restrict__ sp, float* __restrict__ vel,
                                             float* __restrict__ dg, unsigned long long* __restrict__ ccount) {
   constexpr int CH = 32 * TPT;
   __shared__ float4 sA[2][CH], sB[2][CH], sC[2][CH];
@@ -526,8 +526,8 @@ __global__ void __launch_bounds__(32) k_p2p(const int* __restrict__ leaves, cons
       const bool self = (ent.x == leaf) && ent.y == kImageZero;
 #pragma unroll
       for (int q = 0; q < TPT; ++q) t.self[q] = self ? (t0 + lane + 32 * q) - cur_c0 : -1;
-      dispatch_rel<PS, TPT, ST>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t, K0,
-                                PS && mixed);
+      dispatch_rel<PS, TPT, ST, PS && MIX>(self, cur_nf, cur_nm, sA[buf], sB[buf], sC[buf], sK[buf], cur_cnt, t,
+                                           K0);
       c_far += nt * (unsigned long long)cur_nf;
       c_mid += nt * (unsigned long long)cur_nm;
       c_near += nt * (unsigned long long)(cur_cnt - cur_nf - cur_nm);
@@ -1086,9 +1086,15 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
       FMM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     carveout_set = true;
   }
-#define FMM_P2P_LAUNCH(PS_, TPT_, SEG_, ST_)                                                                 \
-  k_p2p<PS_, TPT_, SEG_, ST_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, \
-                                               smaxf, margin0, K0, dip, cseg, sp, mixed, vel, dg, cnt)
+#define FMM_P2P_LAUNCH(PS_, TPT_, SEG_, ST_)                                                                      \
+  do {                                                                                                            \
+    if (mixed)                                                                                                    \
+      k_p2p<true, TPT_, SEG_, ST_, true><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx,    \
+                                                          blen, smaxf, margin0, K0, dip, cseg, sp, vel, dg, cnt); \
+    else                                                                                                          \
+      k_p2p<PS_, TPT_, SEG_, ST_, false><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx,    \
+                                                          blen, smaxf, margin0, K0, dip, cseg, sp, vel, dg, cnt); \
+  } while (0)
 #define FMM_P2P_X2_LAUNCH(SEG_, ST_)                                                                          \
   k_p2p_x2<SEG_, ST_><<<g, 32, 0, s>>>(leaves, off, list, cb, ce, cf, A, B, fu, fs, p->sidx, blen, smaxf,     \
                                        margin0, K0, dip, cseg, sp, vel, dg, cnt)
