@@ -88,6 +88,11 @@ typedef struct fmm_plan_s* fmm_plan;
  *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
  *              output pointer skips that output.
  *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR, optionally | FMM_M2L_SORT_STEPS.
+ *   p2p_pair_max  two leaves whose particle counts multiply to at most this
+ *              do P2P even when the MAC would accept M2L (the cost rule for
+ *              cells of "very few particles", Alg. 2); 0 (default): the MAC
+ *              decides first; >= ncrit^2: every leaf pair does P2P (Alg. 2's
+ *              printed order, leaf test before the MAC).
  *   sigma_rule FMM_SIGMA_SOURCE (default) or FMM_SIGMA_MIXED: the core width
  *              of a near-field pair when a sigma array is given (with one
  *              sigma both rules agree).  The far-field separation and the
@@ -105,6 +110,7 @@ typedef struct {
   int32_t outputs;
   int32_t m2l_mode;
   int32_t sigma_rule;
+  int32_t p2p_pair_max;
 } fmm_params;
 
 /* Work counts of the last evaluation (for throughput and roofline reports). */

@@ -73,9 +73,10 @@ class Result:
 
 
 def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=None,
-        box_len=None, images=3, transpose=False):
+        box_len=None, images=3, transpose=False, p2p_pair_max=0):
     """FP64 FMM.  pos, gamma [n,3] (float32 values), sigma scalar or [n];
-    transpose selects the transpose stretching scheme (grad u)^T gamma.
+    transpose selects the transpose stretching scheme (grad u)^T gamma;
+    p2p_pair_max is the traversal's leaf-pair cost rule (tree.traverse).
 
     Returns a Result with u, s [n,3] in input order and the tree / lists used.
     """
@@ -116,7 +117,7 @@ def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=No
                 acc += cart.m2m(M[ch], t.center[ch] - t.center[c], p)
             M[c] = acc
     # traversal
-    p2p, m2l = tr.traverse(t, blen, theta, ksig, sigma_max, periodic)
+    p2p, m2l = tr.traverse(t, blen, theta, ksig, sigma_max, periodic, p2p_pair_max)
     res.p2p, res.m2l = p2p, m2l
     offs = tr.image_offsets(periodic).astype(np.float64) * blen
     # M2L

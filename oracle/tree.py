@@ -16,7 +16,10 @@ Readings taken where the paper is silent or ambiguous:
   * MAC: M2L iff R_A + R_B < theta |X_A - X_B| and, because the far field uses
     the singular kernel, |X_A - X_B| - (R_A + R_B) >= k_sigma sigma_max.  The
     MAC is tested before the leaf test; two leaves that fail it do P2P; any
-    other pair is pushed.
+    other pair is pushed.  Option (the cost rule for cells of very few
+    particles, Alg. 2): two leaves whose counts multiply to at most
+    p2p_pair_max do P2P before the MAC is tested; p2p_pair_max >= ncrit^2
+    gives Alg. 2's printed order (leaf test first).
   * Algorithm 1 splits the larger cell, read as the larger cube (the coarser
     level; the target A when both cubes are equal); when that cell is a leaf
     the other one is split.  (Comparing tight radii instead would let the
@@ -163,7 +166,7 @@ def image_offsets(periodic):
     return np.stack([ox.ravel(), oy.ravel(), oz.ravel()], 1).astype(np.int64)
 
 
-def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False):
+def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False, p2p_pair_max=0):
     """Algorithms 1-2.  Returns (p2p, m2l) as int64 arrays of (A, B, image)."""
     offs = image_offsets(periodic)
     shifts = offs.astype(np.float64) * float(box_len)
@@ -178,7 +181,12 @@ def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False):
     if len(tree.begin) == 0:
         return np.zeros((0, 3), np.int64), np.zeros((0, 3), np.int64)
 
+    count = tree.end - tree.begin
+
     def interact(a, b, o):
+        if p2p_pair_max > 0 and leaf[a] and leaf[b] and int(count[a]) * int(count[b]) <= p2p_pair_max:
+            p2p.append((a, b, o))
+            return
         cb = C[b] + shifts[o]
         dx = C[a] - cb
         dist = np.sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2])

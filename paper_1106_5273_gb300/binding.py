@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
                 ("periodic", ctypes.c_int32), ("images", ctypes.c_int32),
                 ("box_min", ctypes.c_double * 3), ("box_len", ctypes.c_double),
                 ("sigma_sep", ctypes.c_float), ("outputs", ctypes.c_int32),
-                ("m2l_mode", ctypes.c_int32), ("sigma_rule", ctypes.c_int32)]
+                ("m2l_mode", ctypes.c_int32), ("sigma_rule", ctypes.c_int32),
+                ("p2p_pair_max", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw):

@@ -27,6 +27,7 @@ int check_params(const fmm_params* q) {
   if (q->m2l_mode & ~(3 | FMM_M2L_SORT_STEPS) || (q->m2l_mode & 3) > FMM_M2L_TENSOR) return FMM_E_INVAL;
   if (q->outputs & ~(FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE)) return FMM_E_INVAL;
   if (q->sigma_rule != FMM_SIGMA_SOURCE && q->sigma_rule != FMM_SIGMA_MIXED) return FMM_E_INVAL;
+  if (q->p2p_pair_max < 0) return FMM_E_INVAL;
   return FMM_OK;
 }
 
@@ -196,6 +197,7 @@ void fmm_params_default(fmm_params* q) {
   q->sigma_sep = 5.0f;
   q->outputs = FMM_OUT_VELOCITY | FMM_OUT_STRETCHING;
   q->sigma_rule = FMM_SIGMA_SOURCE;
+  q->p2p_pair_max = 0;
   q->m2l_mode = FMM_M2L_AUTO;
 }
 

@@ -31,6 +31,9 @@ struct TravArgs {
   const int* level;
   const int* cseg;    // batch: problem of each cell (nullptr: one problem, the scalars below)
   const SegMac* sm;   // batch: per-problem shift and MAC constants
+  const int* begin;   // particle range of each cell (the leaf-pair cost rule)
+  const int* end;
+  long long p2p_pair_max;  // leaf pairs with n_A n_B <= this do P2P before the MAC (0: never)
   double theta, ksig, smax, blen;
   float thetaf, ksf, blenf, slack0;  // slack0 = 2e-6 * (largest coordinate magnitude + box length)
 };
@@ -62,6 +65,10 @@ __device__ inline int interact(const TravArgs& t, int a, int b, int o) {
     ksf = m.ksf;
     slack0 = m.slack0;
   }
+  const bool leaves = t.nchild[a] == 0 && t.nchild[b] == 0;
+  if (leaves && t.p2p_pair_max > 0 &&
+      (long long)(t.end[a] - t.begin[a]) * (long long)(t.end[b] - t.begin[b]) <= t.p2p_pair_max)
+    return 1;  // cost rule (Alg. 2): few particles in both, P2P whatever the MAC says
   const float4 A = t.cf[a], B = t.cf[b];
   const float sx = (float)(o / 9 - 1) * blenf, sy = (float)((o / 3) % 3 - 1) * blenf,
               sz = (float)(o % 3 - 1) * blenf;
@@ -76,7 +83,7 @@ __device__ inline int interact(const TravArgs& t, int a, int b, int o) {
   else if (v1 > slack && v2 > slack) m2l = true;
   else m2l = mac_fp64(t, a, b, o, blen, smax);
   if (m2l) return 0;                                          // M2L
-  if (t.nchild[a] == 0 && t.nchild[b] == 0) return 1;        // P2P
+  if (leaves) return 1;                                       // P2P
   return 2;                                                   // push
 }
 
@@ -530,6 +537,9 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   ta.radius = p->c_radius.as<double>();
   ta.cf = p->c_cf.as<float4>();
   ta.nchild = p->c_nchild.as<int>();
+  ta.begin = p->c_begin.as<int>();
+  ta.end = p->c_end.as<int>();
+  ta.p2p_pair_max = p->prm.p2p_pair_max;
   ta.child = p->c_child.as<int>();
   ta.level = p->c_level.as<int>();
   ta.cseg = nullptr;

@@ -14,7 +14,7 @@ def to_dev(a):
 
 
 def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None, outputs=None,
-            sigma_rule=None):
+            sigma_rule=None, p2p_pair_max=None):
     import torch
     from paper_1106_5273_gb300 import Plan, Params
     pos, gam = w["pos"], w["gamma"]
@@ -27,6 +27,8 @@ def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=N
         kw.update(outputs=outputs)
     if sigma_rule is not None:
         kw.update(sigma_rule=sigma_rule)
+    if p2p_pair_max is not None:
+        kw.update(p2p_pair_max=p2p_pair_max)
     plan = Plan(max(n, 1), Params.default(**kw))
     dp, dg = to_dev(pos), to_dev(gam)
     ds = to_dev(sigma_arr) if sigma_arr is not None else None

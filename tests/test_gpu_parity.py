@@ -27,11 +27,11 @@ def _built():
     __graft_entry__.build()
 
 
-def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3, transpose=False):
+def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3, transpose=False, p2p_pair_max=0):
     from oracle import fmm as ofmm
-    kw = {}
+    kw = dict(p2p_pair_max=p2p_pair_max)
     if w.get("periodic"):
-        kw = dict(periodic=True, box_min=w["box_min"], box_len=w["box_len"], images=images)
+        kw.update(periodic=True, box_min=w["box_min"], box_len=w["box_len"], images=images)
     return ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), p, theta, ncrit, ksig=ksig, transpose=transpose, **kw)
 
 
@@ -162,6 +162,31 @@ def test_fmm_periodic_random_matches_fourier():
     assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
     uf, sf = op.fourier(w["pos"], g, w["pos"], g, 0.45, L, 14)
     assert rel_l2(u, uf) < 1.5 * rel_l2(ref.u, uf) + TOL_U
+
+
+@pytest.mark.parametrize("case", ["free-space", "periodic"])
+def test_leaf_pair_cost_rule(case):
+    """Leaf pairs whose counts multiply to at most p2p_pair_max do P2P before
+    the MAC (ncrit^2: Alg. 2's printed order).  The lists stay bit-exact
+    against the oracle traversal with the same rule, no M2L pair joins two
+    such leaves, and the FMM matches the oracle FMM on them."""
+    if case == "free-space":
+        w, args, pmax = workloads.jittered_lattice(16), (6, 0.5, 32), 32 * 32
+    else:
+        c = workloads.random_cloud(600, seed=21, box=2 * math.pi, zero_net=True)
+        g = c["gamma"] - c["gamma"].astype(np.float64).mean(0).astype(np.float32)
+        w = dict(pos=c["pos"], gamma=g, sigma=np.float32(0.45), periodic=True, box_min=np.zeros(3),
+                 box_len=2 * math.pi)
+        args, pmax = (6, 0.5, 16), 100
+    plan, u, s = run_fmm(w, *args, m2l_mode=1, p2p_pair_max=pmax)
+    ref = _oracle_fmm(w, *args, p2p_pair_max=pmax)
+    _check_tree_and_lists(plan, ref, case == "periodic")
+    cnt = ref.tree.end - ref.tree.begin
+    leaf = ref.tree.nchild == 0
+    assert all(not (leaf[A] and leaf[B]) or cnt[A] * cnt[B] > pmax for A, B, _ in ref.m2l)
+    assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
+    base, _, _ = run_fmm(w, *args, m2l_mode=1)
+    assert plan.stats().p2p_pairs > base.stats().p2p_pairs
 
 
 def test_exact_lattice_skips_constant_key_digits():

@@ -416,14 +416,22 @@ def test_tree_invariants():
 
 
 @pytest.mark.parametrize("periodic_case", [False, True])
-def test_traversal_covers_every_pair_once(periodic_case):
+@pytest.mark.parametrize("pair_max", [0, 20, 64])
+def test_traversal_covers_every_pair_once(periodic_case, pair_max):
     # Every (target particle, source particle, image) is reached exactly once,
-    # either by P2P of their leaves or by M2L of an ancestor pair.
+    # either by P2P of their leaves or by M2L of an ancestor pair; with the
+    # leaf-pair cost rule no M2L pair joins two leaves whose counts multiply to
+    # at most pair_max (64 = ncrit^2: Alg. 2's printed order, no leaf-leaf M2L).
     c = workloads.random_cloud(300, seed=11, box=1.0)
     pos = c["pos"]
     kw = dict(box_min=np.zeros(3), box_len=1.0) if periodic_case else {}
     order, skeys, t, bmin, blen = tr.build(pos, 8, **kw)
-    p2p, m2l = tr.traverse(t, blen, 0.6, 2.0, 0.01, periodic_case)
+    p2p, m2l = tr.traverse(t, blen, 0.6, 2.0, 0.01, periodic_case, p2p_pair_max=pair_max)
+    cnt = t.end - t.begin
+    ll = [(A, B) for A, B, o in m2l if t.nchild[A] == 0 and t.nchild[B] == 0]
+    if pair_max == 0:
+        assert len(ll) > 0  # the default lets the MAC join leaves by M2L
+    assert all(cnt[A] * cnt[B] > pair_max for A, B in ll)
     n = pos.shape[0]
     nimg = 27 if periodic_case else 1
     leaf_of = np.zeros(n, int)
