@@ -510,6 +510,19 @@ def main():
             traffic = json.load(open(prof)).get("bytes_per_launch_full_workload")
         except Exception:
             traffic = None
+    # second roofline: the tensor-core M2L phase.  Useful flops: a P x P operator
+    # on 3 components per M2L pair, 2 P^2 x 3 each, times the 3 BF16 products of
+    # the split-precision scheme; peak = the measured dense BF16 rate.
+    P = int(w["p"]) ** 2
+    m2l_flops = 3 * 2.0 * P * P * 3 * st.m2l_pairs
+    bf16_peak, bf16_src = 1900.0, "fallback (no MEASURED_PEAKS.json)"
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        try:
+            bf16_peak, bf16_src = float(json.load(open(mp))["bf16_tflops"]), "measured (MEASURED_PEAKS.json, burst)"
+        except Exception:
+            pass
+    m2l_ach = m2l_flops / (st.ms_m2l * 1e-3) / 1e12 if st.ms_m2l > 0 and st.m2l_tensor else None
     if rank == 0:
         cpu, acc = (None, None)
         if not args.no_cpu_baseline and world == 1:
@@ -535,6 +548,10 @@ def main():
                          "fp32_pipe_slot_frac": slots / p2p_t / (SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6),
                          "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
             "paper_convention_tflops": 174 * pairs / p2p_t / 1e12,
+            "roofline_m2l": None if m2l_ach is None else {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": m2l_ach, "peak": bf16_peak,
+                             "unit": "TFLOP/s", "frac": (m2l_ach / bf16_peak) if m2l_ach else None,
+                             "peak_source": bf16_src, "ms": st.ms_m2l,
+                             "flops": "3 BF16 products x 2 P^2 x 3 components per M2L pair (useful rows only)"},
             "velocity_only": velocity_only,
             "phases_ms": {k: getattr(st, k) for k in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
                                                        "ms_downward", "ms_p2p", "ms_total")},
