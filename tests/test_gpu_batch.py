@@ -148,6 +148,29 @@ def test_batch_per_particle_sigma():
         assert rel_l2(u[off[k]:off[k + 1]], ud) < 2e-4 and rel_l2(s[off[k]:off[k + 1]], sd) < 1e-3
 
 
+def test_batch_mixed_core_width_alone_and_in_the_mix():
+    """Per-particle widths with the mixed rule (FMM_SIGMA_MIXED) in a batch:
+    each problem against the FP64 pair sum with the same rule, and bit-identical
+    alone and in the mix."""
+    from oracle import pairs
+    from paper_1106_5273_gb300 import FMM_SIGMA_MIXED, Plan, Params
+    probs = []
+    for k, n in enumerate([700, 1800]):
+        w = workloads.plummer(n, seed=950 + k)
+        w["sigma_arr"] = (w["sigma"] * np.linspace(1.3, 0.7, n)).astype(np.float32)
+        probs.append(w)
+    off, pos, gam, _, sarr = _concat(probs, per_particle_sigma=True)
+    plan = Plan(int(off[-1]), Params.default(p=8, theta=0.5, ncrit=16, sigma_rule=FMM_SIGMA_MIXED))
+    u, s = _run_batch(plan, off, pos, gam, sarr=sarr)
+    for k, w in enumerate(probs):
+        n = w["pos"].shape[0]
+        x, g, sg = (a.astype(np.float64) for a in (w["pos"], w["gamma"], w["sigma_arr"]))
+        ud, sd = pairs.pair_sum(x, g, x, g, sg, None, np.eye(n, dtype=bool), sig_t=sg)
+        assert rel_l2(u[off[k]:off[k + 1]], ud) < 2e-4 and rel_l2(s[off[k]:off[k + 1]], sd) < 1e-3
+        ua, sa = _run_batch(plan, np.array([0, n]), w["pos"], w["gamma"], sarr=w["sigma_arr"])
+        assert np.array_equal(ua, u[off[k]:off[k + 1]]) and np.array_equal(sa, s[off[k]:off[k + 1]])
+
+
 def test_autotune_ncrit_picks_the_fastest_candidate():
     """fmm_autotune_ncrit times each candidate leaf size on the sample batch and
     returns the fastest; the batch evaluated with it matches the direct sum."""
