@@ -60,17 +60,38 @@ __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, cons
                                             int transpose, float* __restrict__ far_u, float* __restrict__ far_s) {
   extern __shared__ float sm[];
   const int P = p * p;
-  float* sL = sm;           // [3][P]
-  float* sW = sL + 3 * P;   // [5][P]
+  float2* sD = reinterpret_cast<float2*>(sm);  // [3][5][P] complex, see below
+  float* sL = sm + 2 * 15 * P;                 // [3][P]
+  float* sW = sL + 3 * P;                      // [5][P]
   const int leaf = leaves[blockIdx.x];
   for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) sL[i] = L[(size_t)leaf * 3 * P + i];
   for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) sW[i] = Wg[i];
+  __syncthreads();
+  const int on[5] = {1, 1, 2, 2, 2}, om[5] = {0, 1, 0, 1, 2};
+  // The leaf's coefficients of the derivative expansions, once per leaf:
+  // D[q][o][k^2+k+mm] = W_o(k, mm) L~_q(on_o + k, om_o + mm) for mm >= 0 and
+  // (-1)^m W_o(k, -m) L~_q(on_o + k, om_o - m) for mm = -m < 0, so that the
+  // derivative o of potential q is sum_k,m D(+m) R~_k^m + D(-m) conj(R~_k^m).
+  for (int i = threadIdx.x; i < 15 * P; i += blockDim.x) {
+    const int qo = i / P, kk = i % P, q = qo / 5, o = qo % 5;
+    int k = 0;
+    while ((k + 1) * (k + 1) <= kk) ++k;
+    const int mm = kk - k * k - k, m = mm < 0 ? -mm : mm;
+    const int N = on[o] + k;
+    float2 d = make_float2(0.f, 0.f);
+    if (N <= p - 1) {
+      const float w = sW[o * P + kk];
+      const float2 lt = lget(sL + q * P, N, om[o] + mm);
+      const float sg = (mm < 0 && (m & 1)) ? -w : w;
+      d = make_float2(sg * lt.x, sg * lt.y);
+    }
+    sD[i] = d;
+  }
   __syncthreads();
   const int b = begin[leaf], e = end[leaf];
   const double a = box[4 * (cseg ? cseg[leaf] : 0) + 3] * ldexp(1.0, -level[leaf]);
   const float inv_a = (float)(1.0 / a);
   const double cx = center[3 * leaf], cy = center[3 * leaf + 1], cz = center[3 * leaf + 2];
-  const int on[5] = {1, 1, 2, 2, 2}, om[5] = {0, 1, 0, 1, 2};
   for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
     float4 x = A[j];
     float4 g = B[j];
@@ -110,27 +131,19 @@ __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, cons
         // contributions of R~_k^{+m} and R~_k^{-m}
 #pragma unroll
         for (int o = 0; o < 5; ++o) {
-          const int N = on[o] + k;
-          if (N > p - 1) continue;
-          const float wp = sW[o * P + k * k + k + m];
+          if (on[o] + k > p - 1) continue;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            float2 lt = lget(sL + q * P, N, om[o] + m);
-            acc[q][o][0] += wp * (lt.x * r0r - lt.y * r0i);
-            acc[q][o][1] += wp * (lt.x * r0i + lt.y * r0r);
+            const float2 d = sD[(q * 5 + o) * P + k * k + k + m];
+            acc[q][o][0] = fmaf(d.x, r0r, fmaf(-d.y, r0i, acc[q][o][0]));
+            acc[q][o][1] = fmaf(d.x, r0i, fmaf(d.y, r0r, acc[q][o][1]));
           }
           if (m > 0) {
-            const float wm = sW[o * P + k * k + k - m];
-            float rr = r0r, ri = -r0i;  // (-1)^m conj(R)
-            if (m & 1) {
-              rr = -rr;
-              ri = -ri;
-            }
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              float2 lt = lget(sL + q * P, N, om[o] - m);
-              acc[q][o][0] += wm * (lt.x * rr - lt.y * ri);
-              acc[q][o][1] += wm * (lt.x * ri + lt.y * rr);
+            for (int q = 0; q < 3; ++q) {  // conj(R~_k^m)
+              const float2 d = sD[(q * 5 + o) * P + k * k + k - m];
+              acc[q][o][0] = fmaf(d.x, r0r, fmaf(d.y, r0i, acc[q][o][0]));
+              acc[q][o][1] = fmaf(-d.x, r0i, fmaf(d.y, r0r, acc[q][o][1]));
             }
           }
         }
@@ -197,7 +210,7 @@ int downward_pass(fmm_plan p, int64_t n, cudaStream_t s) {
   FMM_TRY(p->far_u.ensure((size_t)n * 3 * sizeof(float)));
   FMM_TRY(p->far_s.ensure((size_t)n * 3 * sizeof(float)));
   ++g_launches;
-  k_l2p<<<(unsigned)p->nleaves, 64, 8 * P * sizeof(float), s>>>(
+  k_l2p<<<(unsigned)p->nleaves, 64, (2 * 15 + 8) * P * sizeof(float), s>>>(
       p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(), p->c_center.as<double>(),
       p->batched ? p->seg_box.as<double>() : p->scal.as<double>(), p->batched ? p->c_seg.as<int>() : nullptr,
       p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_w.as<float>(),
