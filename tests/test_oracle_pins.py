@@ -478,6 +478,12 @@ def test_fmm_matches_direct_sum_and_converges():
     terr = [np.linalg.norm(fmm.fmm(x, g, sig, p, 0.5, 8, ksig=3.0, transpose=True).s - sdt) / np.linalg.norm(sdt)
             for p in (3, 7)]
     assert terr[1] < 3e-4 and terr[1] < 0.3 * terr[0]
+    # the leaf-pair cost rule moves MAC-accepted leaf pairs to P2P: fewer M2L
+    # pairs and an error no larger than without it (a dropped pair would blow it up)
+    r0 = fmm.fmm(x, g, sig, 3, 0.5, 8, ksig=3.0)
+    rc = fmm.fmm(x, g, sig, 3, 0.5, 8, ksig=3.0, p2p_pair_max=64)
+    assert len(rc.m2l) < len(r0.m2l) and len(rc.p2p) > len(r0.p2p)
+    assert np.linalg.norm(rc.u - ud) <= np.linalg.norm(r0.u - ud)
     # the near field alone (no M2L accepted) is the direct sum
     r = fmm.fmm(x, g, sig, 3, 1e-6, 8)
     assert len(r.m2l) == 0
