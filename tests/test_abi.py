@@ -38,11 +38,12 @@ def test_params_and_errors_without_gpu(lib):
     from paper_1106_5273_gb300 import binding
     q = binding.Params.default()
     assert (q.p, round(q.theta, 6), q.ncrit, q.periodic, q.images) == (10, 0.4, 64, 0, 3)
+    assert (q.sigma_rule, q.p2p_pair_max, q.m2l_mode) == (0, 0, 0)
     assert binding._strerror(0) == "ok" and "invalid" in binding._strerror(-1)
     # parameter validation happens before any CUDA call
     h = ctypes.c_void_p()
     for bad in (dict(p=0), dict(p=17), dict(theta=1.5), dict(ncrit=0), dict(periodic=1, box_len=0.0),
-                dict(periodic=1, images=0), dict(m2l_mode=7), dict(sigma_rule=2)):
+                dict(periodic=1, images=0), dict(m2l_mode=7), dict(sigma_rule=2), dict(p2p_pair_max=-1)):
         qq = binding.Params.default(**bad)
         assert lib.fmm_plan_create(ctypes.byref(qq), 100, ctypes.byref(h)) == -1
     assert lib.fmm_plan_create(ctypes.byref(q), -1, ctypes.byref(h)) == -1
