@@ -193,8 +193,8 @@ int fmm_eval_velocity_stretching_host(fmm_plan plan, int64_t n, const float* pos
  *                     be NULL) for a free-space plan, where every problem gets
  *                     its own bounding cube as in fmm_eval_velocity_stretching
  *   vel, dgamma       device [n][3] float32 outputs (either may be NULL)
- * The plan supplies p, theta, ncrit, images, sigma_sep and m2l_mode for all
- * problems.  The tree of each problem stops at level FMM_BATCH_DEPTH (16)
+ * The plan supplies p, theta, ncrit, images, sigma_sep, m2l_mode, sigma_rule
+ * and p2p_pair_max for all problems.  The tree of each problem stops at level FMM_BATCH_DEPTH (16)
  * instead of 21.  The result of each problem does not depend on the other
  * problems of the batch: every sum runs in a fixed order and every constant
  * (cube, sigma, class bounds, dipole term) is the problem's own, so a problem
@@ -270,7 +270,7 @@ typedef struct {
                                    first batch (fmm_autotune_ncrit over 32 ... 256) */
   float sigma_sep;
   int32_t images;
-  int32_t m2l_mode;
+  int32_t m2l_mode;             /* the plans' other parameters take fmm_params_default's values */
 } fmm_server_params;
 
 /* One request.  Host arrays; the caller keeps them valid (and does not read
