@@ -328,7 +328,7 @@ void fmm_plan_destroy(fmm_plan plan);
 const char* fmm_strerror(int code);
 
 /*
- * Velocity at nt target points from ns source blobs (Sec. 5.2 compares the
+ * Velocity at nt target points from ns source blobs (Sec. 4.3 compares the
  * kinetic energy spectrum of the vortex-method field with the spectral
  * method's, which needs the velocity on grid points that are not particles).
  *   src_pos[ns][3], src_gamma[ns][3]   device float32 sources
@@ -379,7 +379,8 @@ int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gam
  * the library until the process exits.  n must be <= FMM_NOALLOC_MAX_N;
  * larger n returns FMM_E_CAPACITY and launches nothing.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress, with the device current); make that
- * first call before any stream capture.  All calls share the array and it
+ * first call before any stream capture.  Host threads may make that first
+ * call at the same time (the cached address is atomic).  All calls share the array and it
  * keeps the last call's contents; calls whose GPU work overlaps (other
  * streams, other threads) race on it and give undefined results.  Nothing in
  * the array needs to start at zero.  Asynchronous on cuda_stream.

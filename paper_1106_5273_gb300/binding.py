@@ -266,7 +266,17 @@ def morton_order_noalloc(pos, keys_out, order_out, periodic=False, box_min=None,
     pos: float32 CUDA tensor [n,3]; keys_out: int64 CUDA tensor [n] (holds the
     uint64 keys); order_out: int32 CUDA tensor [n] (holds uint32 indices).
     """
+    import torch
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError("pos must have shape [n, 3]")
     n = pos.shape[0]
+    for t, dt, name in ((keys_out, torch.int64, "keys_out"), (order_out, torch.int32, "order_out")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.dtype != dt:
+            raise TypeError("%s must be a contiguous %s CUDA tensor" % (name, dt))
+        if t.device != pos.device:
+            raise ValueError("%s must be on the device of pos (%s)" % (name, pos.device))
+        if t.numel() < n:
+            raise ValueError("%s holds %d elements, fewer than n = %d" % (name, t.numel(), n))
     bm = (ctypes.c_double * 3)(*(box_min if box_min is not None else (0.0, 0.0, 0.0)))
     _check(lib.fmm_morton_order_noalloc(n, _dptr(pos, name="pos"), 1 if periodic else 0, bm, float(box_len),
                                         ctypes.c_void_p(keys_out.data_ptr()), ctypes.c_void_p(order_out.data_ptr()),

@@ -4,8 +4,9 @@ For x = rho/sqrt(2) >= 1 the P2P kernel writes
     g(rho) = 1 - exp(-x^2) * (erfcx(x) + 2x/sqrt(pi)),
 sharing exp(-x^2) with the Gaussian term of the stretching kernel, and
 approximates erfcx(x) = exp(x^2) erfc(x) by a degree-3 polynomial in
-y = 1/x on [1/XMAX, 1] (y comes from the rsqrt the kernel computes anyway;
-beyond XMAX = 4.6, exp(-x^2) F < 4e-9 and y is clamped).  The fit minimises
+y = 1/x on [1/XMAX, 1] (y comes from the rsqrt the kernel computes anyway).
+The kernel does not clamp y: beyond XMAX = 4.6 the polynomial stays bounded
+(y < 1/XMAX) and exp(-x^2) < 8e-10 multiplies it, so g = 1 to FP32 precision.  The fit minimises
 the relative error of g (weight exp(-x^2)/g) by iteratively reweighted least
 squares.  Below x = 1 the kernel uses the Taylor series of g/rho^3 instead.
 Run:  python gen_cutoff_fit.py   (prints the coefficients, low order first).

@@ -13,6 +13,8 @@
 // life of the process.  In host code its name is only a host-side stand-in,
 // not a device address: the device address is obtained once per device with
 // cudaGetSymbolAddress (with that device current) and passed to the kernels.
+#include <atomic>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -41,7 +43,10 @@ constexpr size_t kScratchBytes = align256(kOffScan + kScanWords * sizeof(uint32_
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+// Device address of the scratch array, per device.  Atomic so that two host
+// threads making their first call on one device at once do not race: both
+// look the same address up and store it (release), readers load it (acquire).
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
 
 }  // namespace
 
@@ -57,13 +62,14 @@ extern "C" int fmm_morton_order_noalloc(int64_t n, const float* pos, int periodi
   int dev = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return FMM_E_INVAL;
-  if (!g_scratch_addr[dev]) {
+  unsigned char* base = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!base) {
     // set-up, once per device, with that device current
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return FMM_E_CUDA;
-    g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+    base = static_cast<unsigned char*>(ptr);
+    g_scratch_addr[dev].store(base, std::memory_order_release);
   }
-  unsigned char* base = g_scratch_addr[dev];
   cudaStream_t s = (cudaStream_t)stream;
   double* box = reinterpret_cast<double*>(base + kOffBox);
   double* part = reinterpret_cast<double*>(base + kOffPart);

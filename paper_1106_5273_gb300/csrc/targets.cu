@@ -1,4 +1,4 @@
-// Velocity at separate target points (Sec. 5.2 compares the kinetic energy
+// Velocity at separate target points (Sec. 4.3 compares the kinetic energy
 // spectrum of the vortex-method field with the spectral method's, which needs
 // the velocity on grid points that are not particles).  The targets enter the
 // plan's tree as blobs of zero strength behind the sources, so the FMM of

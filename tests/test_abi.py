@@ -79,3 +79,19 @@ def test_server_params_validated_without_gpu(lib):
         q = b.ServerParams.default(**bad)
         assert lib.fmm_server_create(ctypes.byref(q), ctypes.byref(h)) == -1
     assert lib.fmm_server_submit(None, None, None) == -1
+
+
+def test_noalloc_binding_rejects_bad_outputs_before_the_call(lib):
+    """morton_order_noalloc checks shapes, devices and dtypes in Python, so a
+    wrong output never reaches the kernels (checked here with CPU tensors)."""
+    import torch
+    from paper_1106_5273_gb300 import binding as b
+    pos = torch.zeros((8, 3), dtype=torch.float32)
+    keys = torch.zeros(8, dtype=torch.int64)
+    order = torch.zeros(8, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        b.morton_order_noalloc(torch.zeros((8, 2), dtype=torch.float32), keys, order)
+    with pytest.raises(ValueError):
+        b.morton_order_noalloc(torch.zeros(24, dtype=torch.float32), keys, order)
+    with pytest.raises(TypeError):  # CPU outputs
+        b.morton_order_noalloc(pos, keys, order)

@@ -51,6 +51,18 @@ def test_noalloc_ordering_matches_plan_on_consecutive_calls():
             assert np.array_equal(keys.cpu().numpy().view(np.uint64), keys_ref)
             assert np.array_equal(order.cpu().numpy().view(np.uint32), order_ref)
 
+    # outputs of the wrong dtype or size are refused before the library is called
+    pos = torch.zeros((1000, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        morton_order_noalloc(pos, torch.empty(999, dtype=torch.int64, device="cuda"),
+                             torch.empty(1000, dtype=torch.int32, device="cuda"))
+    with pytest.raises(TypeError):
+        morton_order_noalloc(pos, torch.empty(1000, dtype=torch.int32, device="cuda"),
+                             torch.empty(1000, dtype=torch.int32, device="cuda"))
+    with pytest.raises(TypeError):
+        morton_order_noalloc(pos, torch.empty(1000, dtype=torch.int64, device="cuda"),
+                             torch.empty(2000, dtype=torch.int32, device="cuda")[::2])
+
     big = torch.zeros((NOALLOC_MAX_N + 1, 3), dtype=torch.float32, device="cuda")
     kb = torch.empty(NOALLOC_MAX_N + 1, dtype=torch.int64, device="cuda")
     ob = torch.empty(NOALLOC_MAX_N + 1, dtype=torch.int32, device="cuda")
