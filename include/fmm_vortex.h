@@ -61,6 +61,14 @@ enum {
   FMM_M2L_SORT_STEPS = 8
 };
 
+/* fmm_params.split_tie: the cell Algorithm 1 splits when the pair's cells are
+ * cubes of one size (its radius test "radius of A > radius of B" is read on
+ * the cube size, so a tie goes to the ELSE branch). */
+enum {
+  FMM_SPLIT_SOURCE = 0, /* split B, the source cell (Alg. 1 as printed; default) */
+  FMM_SPLIT_TARGET = 1  /* split A, the target cell (an alternative, not the printed rule) */
+};
+
 /* Core width of a pair when every blob carries its own sigma (a sigma array). */
 enum {
   FMM_SIGMA_SOURCE = 0, /* sigma_j of the source blob (Eq. 2 as written) */
@@ -97,6 +105,10 @@ typedef struct fmm_plan_s* fmm_plan;
  *              of a near-field pair when a sigma array is given (with one
  *              sigma both rules agree).  The far-field separation and the
  *              pair classes use the largest sigma, which bounds both.
+ *   split_tie  FMM_SPLIT_SOURCE (default: Alg. 1's ELSE branch splits B when
+ *              A and B are cubes of one size) or FMM_SPLIT_TARGET (split A
+ *              then).  Alg. 1 always splits the larger cube; when that cell
+ *              is a leaf the other one is split.
  */
 typedef struct {
   int32_t p;
@@ -111,6 +123,7 @@ typedef struct {
   int32_t m2l_mode;
   int32_t sigma_rule;
   int32_t p2p_pair_max;
+  int32_t split_tie;
 } fmm_params;
 
 /* Work counts of the last evaluation (for throughput and roofline reports). */
@@ -139,7 +152,8 @@ typedef struct {
 } fmm_stats;
 
 /* Fill *prm with defaults: p=10, theta=0.4, ncrit=64, free space, images=3,
- * box [0,1)^3, sigma_sep=5, both outputs, FMM_M2L_AUTO. */
+ * box [0,1)^3, sigma_sep=5, both outputs, FMM_M2L_AUTO, FMM_SIGMA_SOURCE,
+ * p2p_pair_max=0, FMM_SPLIT_SOURCE. */
 void fmm_params_default(fmm_params* prm);
 
 /*

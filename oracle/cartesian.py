@@ -136,11 +136,23 @@ def l2l(L, h, p):
 
 
 def m2l_batch(M, t, p):
-    """Locals [q,3,P] from multipoles M [q,3,P] across translations t [q,3]."""
+    """Locals [q,3,P] from multipoles M [q,3,P] across translations t [q,3].
+
+    Each translation is independent: the rows are processed in blocks only to
+    bound memory (the Python loop of taylor_inv_r runs once per block, and
+    the [block, P, P] operators are formed a few at a time)."""
     _, _, _, _, IDX, F, _, _, _ = _tables(p)
-    b = taylor_inv_r(t, 2 * (p - 1))
-    K = b[:, IDX] * F[None]
-    return np.einsum("qab,qcb->qca", K, M)
+    t = np.asarray(t, np.float64).reshape(-1, 3)
+    M = np.asarray(M)
+    P = IDX.shape[0]
+    out = np.zeros((t.shape[0], M.shape[1], P))
+    sub = max(1, 4000000 // (P * P))
+    for r0 in range(0, t.shape[0], 4096):
+        b = taylor_inv_r(t[r0:r0 + 4096], 2 * (p - 1))
+        for s0 in range(0, b.shape[0], sub):
+            K = b[s0:s0 + sub][:, IDX] * F[None]
+            out[r0 + s0:r0 + s0 + K.shape[0]] = np.einsum("qab,qcb->qca", K, M[r0 + s0:r0 + s0 + K.shape[0]])
+    return out
 
 
 def multipole_field(M, y, p):

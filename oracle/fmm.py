@@ -73,10 +73,11 @@ class Result:
 
 
 def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=None,
-        box_len=None, images=3, transpose=False, p2p_pair_max=0):
+        box_len=None, images=3, transpose=False, p2p_pair_max=0, split_tie="source"):
     """FP64 FMM.  pos, gamma [n,3] (float32 values), sigma scalar or [n];
     transpose selects the transpose stretching scheme (grad u)^T gamma;
-    p2p_pair_max is the traversal's leaf-pair cost rule (tree.traverse).
+    p2p_pair_max is the traversal's leaf-pair cost rule and split_tie the cell
+    Algorithm 1 splits on equal cubes (tree.traverse).
 
     Returns a Result with u, s [n,3] in input order and the tree / lists used.
     """
@@ -117,13 +118,13 @@ def fmm(pos, gamma, sigma, p, theta, ncrit, ksig=5.0, periodic=False, box_min=No
                 acc += cart.m2m(M[ch], t.center[ch] - t.center[c], p)
             M[c] = acc
     # traversal
-    p2p, m2l = tr.traverse(t, blen, theta, ksig, sigma_max, periodic, p2p_pair_max)
+    p2p, m2l = tr.traverse(t, blen, theta, ksig, sigma_max, periodic, p2p_pair_max, split_tie)
     res.p2p, res.m2l = p2p, m2l
     offs = tr.image_offsets(periodic).astype(np.float64) * blen
     # M2L
     if len(m2l):
         tvec = t.center[m2l[:, 0]] - (t.center[m2l[:, 1]] + offs[m2l[:, 2]])
-        chunk = max(1, 200000 // (P * P))
+        chunk = 65536
         for c0 in range(0, len(m2l), chunk):
             sl = slice(c0, c0 + chunk)
             contrib = cart.m2l_batch(M[m2l[sl, 1]], tvec[sl], p)

@@ -20,10 +20,14 @@ Readings taken where the paper is silent or ambiguous:
     particles, Alg. 2): two leaves whose counts multiply to at most
     p2p_pair_max do P2P before the MAC is tested; p2p_pair_max >= ncrit^2
     gives Alg. 2's printed order (leaf test first).
-  * Algorithm 1 splits the larger cell, read as the larger cube (the coarser
-    level; the target A when both cubes are equal); when that cell is a leaf
-    the other one is split.  (Comparing tight radii instead would let the
-    rounding of the inputs decide between cells of equal cubes.)
+  * Algorithm 1 splits A when its radius exceeds B's and B otherwise (the
+    ELSE branch, so B on a tie).  "Radius" is read as the cube's size (the
+    coarser level is the larger cell): comparing tight particle radii instead
+    would let the rounding of the inputs decide between cells of equal
+    cubes.  When the cell to split is a leaf, the other one is split (the
+    pair was pushed because one of them has children).  Option
+    split_tie="target" splits A instead on equal cubes (not the printed
+    rule; kept to compare the two).
   * Periodic: the traversal starts from (root, root + o L) for the 27 shifts
     o in {-1,0,1}^3 (targets stay in the original cube).
 All FP64 expressions are written in a fixed order with no fused operations so
@@ -166,8 +170,15 @@ def image_offsets(periodic):
     return np.stack([ox.ravel(), oy.ravel(), oz.ravel()], 1).astype(np.int64)
 
 
-def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False, p2p_pair_max=0):
-    """Algorithms 1-2.  Returns (p2p, m2l) as int64 arrays of (A, B, image)."""
+def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False, p2p_pair_max=0, split_tie="source"):
+    """Algorithms 1-2.  Returns (p2p, m2l) as int64 arrays of (A, B, image).
+
+    split_tie: which cell Algorithm 1 splits when A and B are cubes of one
+    size: "source" (B, the printed ELSE branch; default) or "target" (A).
+    """
+    if split_tie not in ("source", "target"):
+        raise ValueError("split_tie must be 'source' or 'target'")
+    tie_a = split_tie == "target"
     offs = image_offsets(periodic)
     shifts = offs.astype(np.float64) * float(box_len)
     theta = float(theta)
@@ -202,7 +213,8 @@ def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False, p2p_pair_max
         interact(0, 0, o)
     while stack:
         a, b, o = stack.pop()
-        split_a = lev[a] <= lev[b]
+        # radius of A > radius of B  <=>  A is the coarser cube
+        split_a = lev[a] < lev[b] or (tie_a and lev[a] == lev[b])
         if split_a and leaf[a]:
             split_a = False
         elif (not split_a) and leaf[b]:

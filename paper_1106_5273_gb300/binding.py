@@ -16,6 +16,7 @@ FMM_OK = 0
 FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
 FMM_M2L_SORT_STEPS = 8
 FMM_SIGMA_SOURCE, FMM_SIGMA_MIXED = 0, 1
+FMM_SPLIT_SOURCE, FMM_SPLIT_TARGET = 0, 1
 FMM_OUT_VELOCITY, FMM_OUT_STRETCHING, FMM_OUT_STRETCHING_TRANSPOSE = 1, 2, 4
 
 
@@ -37,7 +38,7 @@ class Params(ctypes.Structure):
                 ("box_min", ctypes.c_double * 3), ("box_len", ctypes.c_double),
                 ("sigma_sep", ctypes.c_float), ("outputs", ctypes.c_int32),
                 ("m2l_mode", ctypes.c_int32), ("sigma_rule", ctypes.c_int32),
-                ("p2p_pair_max", ctypes.c_int32)]
+                ("p2p_pair_max", ctypes.c_int32), ("split_tie", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw):

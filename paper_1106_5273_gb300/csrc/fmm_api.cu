@@ -28,6 +28,7 @@ int check_params(const fmm_params* q) {
   if (q->outputs & ~(FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE)) return FMM_E_INVAL;
   if (q->sigma_rule != FMM_SIGMA_SOURCE && q->sigma_rule != FMM_SIGMA_MIXED) return FMM_E_INVAL;
   if (q->p2p_pair_max < 0) return FMM_E_INVAL;
+  if (q->split_tie != FMM_SPLIT_SOURCE && q->split_tie != FMM_SPLIT_TARGET) return FMM_E_INVAL;
   return FMM_OK;
 }
 
@@ -198,6 +199,7 @@ void fmm_params_default(fmm_params* q) {
   q->outputs = FMM_OUT_VELOCITY | FMM_OUT_STRETCHING;
   q->sigma_rule = FMM_SIGMA_SOURCE;
   q->p2p_pair_max = 0;
+  q->split_tie = FMM_SPLIT_SOURCE;
   q->m2l_mode = FMM_M2L_AUTO;
 }
 

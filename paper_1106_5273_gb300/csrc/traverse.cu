@@ -1,8 +1,9 @@
 // Dual-tree traversal (Sec. 3.3, Algorithms 1-2) and list grouping.
 //
 // Algorithm 1 pops a pair (A, B), splits the larger cell -- the larger cube,
-// i.e. the coarser level (the target A when both are equal; the other one when
-// that cell is a leaf) -- and calls Algorithm 2
+// i.e. the coarser level; on equal cubes its ELSE branch, the source B
+// (fmm_params.split_tie = FMM_SPLIT_TARGET takes A instead); the other cell
+// when that one is a leaf -- and calls Algorithm 2
 // on every child pair: M2L if the FMM MAC holds (R_A + R_B < theta |X_A-X_B|)
 // and the pair is at least k_sigma sigma_max apart (the far field uses the
 // singular kernel), else P2P if both are leaves, else push.  Here the stack
@@ -34,6 +35,7 @@ struct TravArgs {
   const int* begin;   // particle range of each cell (the leaf-pair cost rule)
   const int* end;
   long long p2p_pair_max;  // leaf pairs with n_A n_B <= this do P2P before the MAC (0: never)
+  int split_tie;           // FMM_SPLIT_SOURCE / FMM_SPLIT_TARGET: the cell split on equal cubes
   double theta, ksig, smax, blen;
   float thetaf, ksf, blenf, slack0;  // slack0 = 2e-6 * (largest coordinate magnitude + box length)
 };
@@ -133,7 +135,8 @@ __global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int n
 }
 
 __device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, int& c0, int& nc) {
-  split_a = t.level[a] <= t.level[b];
+  // radius of A > radius of B  <=>  A is the coarser cube (a tie: split_tie)
+  split_a = t.level[a] < t.level[b] || (t.split_tie == FMM_SPLIT_TARGET && t.level[a] == t.level[b]);
   if (split_a && t.nchild[a] == 0) split_a = false;
   else if (!split_a && t.nchild[b] == 0) split_a = true;
   int s = split_a ? a : b;
@@ -540,6 +543,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   ta.begin = p->c_begin.as<int>();
   ta.end = p->c_end.as<int>();
   ta.p2p_pair_max = p->prm.p2p_pair_max;
+  ta.split_tie = p->prm.split_tie;
   ta.child = p->c_child.as<int>();
   ta.level = p->c_level.as<int>();
   ta.cseg = nullptr;

@@ -14,7 +14,7 @@ def to_dev(a):
 
 
 def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None, outputs=None,
-            sigma_rule=None, p2p_pair_max=None):
+            sigma_rule=None, p2p_pair_max=None, split_tie=None):
     import torch
     from paper_1106_5273_gb300 import Plan, Params
     pos, gam = w["pos"], w["gamma"]
@@ -29,9 +29,22 @@ def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=N
         kw.update(sigma_rule=sigma_rule)
     if p2p_pair_max is not None:
         kw.update(p2p_pair_max=p2p_pair_max)
+    if split_tie is not None:
+        kw.update(split_tie=split_tie)
     plan = Plan(max(n, 1), Params.default(**kw))
     dp, dg = to_dev(pos), to_dev(gam)
     ds = to_dev(sigma_arr) if sigma_arr is not None else None
     u, s = plan.eval(dp, dg, sigma=ds, sigma_uniform=float(w["sigma"]))
     torch.cuda.synchronize()
     return plan, u.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+
+
+def per_target_error(a, ref, floor=0.1):
+    """max_i |a_i - ref_i| / (|ref_i| + floor * rms(ref)): the error of the worst
+    target relative to its own magnitude, floored at a fraction of the rms
+    magnitude so that targets where the field nearly vanishes do not divide
+    by zero."""
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    rms = np.linalg.norm(ref) / np.sqrt(max(ref.shape[0], 1))
+    return float((np.linalg.norm(a - ref, axis=1) / (np.linalg.norm(ref, axis=1) + floor * rms)).max())

@@ -27,9 +27,9 @@ def _built():
     __graft_entry__.build()
 
 
-def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3, transpose=False, p2p_pair_max=0):
+def _oracle_fmm(w, p, theta, ncrit, ksig=5.0, images=3, transpose=False, p2p_pair_max=0, split_tie="source"):
     from oracle import fmm as ofmm
-    kw = dict(p2p_pair_max=p2p_pair_max)
+    kw = dict(p2p_pair_max=p2p_pair_max, split_tie=split_tie)
     if w.get("periodic"):
         kw.update(periodic=True, box_min=w["box_min"], box_len=w["box_len"], images=images)
     return ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), p, theta, ncrit, ksig=ksig, transpose=transpose, **kw)

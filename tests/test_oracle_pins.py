@@ -416,8 +416,35 @@ def test_tree_invariants():
 
 
 @pytest.mark.parametrize("periodic_case", [False, True])
+def test_algorithm1_splits_the_larger_cube_and_the_source_on_a_tie(periodic_case):
+    # Alg. 1: "IF radius of A > radius of B split A ELSE split B".  On a
+    # complete octree (every leaf on one level) no leaf forces the other
+    # split, so from (root, root) the printed rule alternates B, A, B, ...:
+    # every emitted pair has its target on the source's level or one above
+    # (level(A) - level(B) in {0, -1}).  Splitting A on ties mirrors that
+    # ({0, +1}).  A reversed comparison or a tie sent to the wrong branch
+    # fails here.  Both settings cover every pair once (next test).
+    w = workloads.taylor_green(16)  # 4096 lattice blobs: ncrit 8 gives leaves on level 3 only
+    kw = dict(box_min=w["box_min"], box_len=w["box_len"]) if periodic_case else {}
+    order, skeys, t, bmin, blen = tr.build(w["pos"], 8, **kw)
+    leaf = t.nchild == 0
+    assert np.all(t.level[leaf] == 3)
+    seen = {}
+    for tie, allowed in (("source", {0, -1}), ("target", {0, 1})):
+        p2p, m2l = tr.traverse(t, blen, 0.7, 0.0, 0.0, periodic_case, split_tie=tie)
+        both = np.concatenate([p2p, m2l])
+        dl = set((t.level[both[:, 0]] - t.level[both[:, 1]]).tolist())
+        assert dl <= allowed and len(dl) == 2, (tie, dl)
+        seen[tie] = m2l
+    assert len(seen["source"]) != len(seen["target"]) or not np.array_equal(seen["source"], seen["target"])
+    with pytest.raises(ValueError):
+        tr.traverse(t, blen, 0.5, 0.0, 0.0, periodic_case, split_tie="larger")
+
+
+@pytest.mark.parametrize("periodic_case", [False, True])
 @pytest.mark.parametrize("pair_max", [0, 20, 64])
-def test_traversal_covers_every_pair_once(periodic_case, pair_max):
+@pytest.mark.parametrize("split_tie", ["source", "target"])
+def test_traversal_covers_every_pair_once(periodic_case, pair_max, split_tie):
     # Every (target particle, source particle, image) is reached exactly once,
     # either by P2P of their leaves or by M2L of an ancestor pair; with the
     # leaf-pair cost rule no M2L pair joins two leaves whose counts multiply to
@@ -426,7 +453,7 @@ def test_traversal_covers_every_pair_once(periodic_case, pair_max):
     pos = c["pos"]
     kw = dict(box_min=np.zeros(3), box_len=1.0) if periodic_case else {}
     order, skeys, t, bmin, blen = tr.build(pos, 8, **kw)
-    p2p, m2l = tr.traverse(t, blen, 0.6, 2.0, 0.01, periodic_case, p2p_pair_max=pair_max)
+    p2p, m2l = tr.traverse(t, blen, 0.6, 2.0, 0.01, periodic_case, p2p_pair_max=pair_max, split_tie=split_tie)
     cnt = t.end - t.begin
     ll = [(A, B) for A, B, o in m2l if t.nchild[A] == 0 and t.nchild[B] == 0]
     if pair_max == 0:
