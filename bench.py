@@ -56,6 +56,9 @@ def parse():
                     help="taylor-green: the 128^3 periodic evaluation (default); batched: 512 independent "
                          "free-space problems; serving: a Poisson request stream")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving run of the default line")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 512^3 spectrum run of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched run of the default line")
+    ap.add_argument("--no-reuse", action="store_true", help="skip the tree-reuse / graph-replay run")
     ap.add_argument("--serving-seconds", type=float, default=1.0, help="arrival horizon of the serving run")
     ap.add_argument("--serving-rate", type=float, default=200.0, help="mean arrivals per second")
     return ap.parse_args()
@@ -131,6 +134,55 @@ def job_value(n_per_rank, world, t_step_ms):
     return world * n_per_rank / (t_step_ms * 1e-3)
 
 
+def bf16_peak():
+    """Dense BF16 tensor rate: the measured burst figure, else the recipe's fallback."""
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        try:
+            return float(json.load(open(mp))["bf16_tflops"]), "measured (MEASURED_PEAKS.json, burst)"
+        except Exception:
+            pass
+    return 1900.0, "fallback (no MEASURED_PEAKS.json)"
+
+
+def p2p_roofline(st, p2p_ms, traffic=None):
+    """FP32-pipe roofline of the P2P kernel from its CUDA-event time (ms per launch)."""
+    p2p_t = p2p_ms * 1e-3
+    flops = (P2P_FLOPS["near"] * st.p2p_pairs_near + P2P_FLOPS["mid"] * st.p2p_pairs_mid
+             + P2P_FLOPS["far"] * st.p2p_pairs_far)
+    slots = (P2P_SLOTS["near"] * st.p2p_pairs_near + P2P_SLOTS["mid"] * st.p2p_pairs_mid
+             + P2P_SLOTS["far"] * st.p2p_pairs_far)
+    clk_mhz = 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+    achieved = flops / p2p_t / 1e12
+    return {"bound": "alu", "kernel": "k_p2p_x2", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "flops_per_pair": P2P_FLOPS, "pairs_per_launch": st.p2p_pairs,
+            "pairs_by_class": {"near": st.p2p_pairs_near, "mid": st.p2p_pairs_mid, "far": st.p2p_pairs_far},
+            "ms_per_launch": p2p_ms,
+            "fp32_pipe_slot_frac": slots / p2p_t / (SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6),
+            "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz (derived from unit counts and the "
+                         "maximum clock)"}
+
+
+def m2l_roofline(st, p):
+    """Tensor roofline of the M2L phase: useful flops = 3 BF16 products x 2 P^2 x 3 components
+    per M2L pair; peak = the dense BF16 rate."""
+    P = int(p) ** 2
+    if not (st.ms_m2l > 0 and st.m2l_tensor):
+        return None
+    peak, src = bf16_peak()
+    ach = 3 * 2.0 * P * P * 3 * st.m2l_pairs / (st.ms_m2l * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "peak_source": src, "ms": st.ms_m2l,
+            "flops": "3 BF16 products x 2 P^2 x 3 components per M2L pair (useful rows only)"}
+
+
+PHASES = ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l", "ms_downward", "ms_p2p", "ms_total")
+WORK = ("ncells", "nleaves", "nlevels", "p2p_cell_pairs", "p2p_pairs", "m2l_pairs", "m2l_steps", "m2l_keys",
+        "m2l_built", "m2l_tensor")
+
+
 def workload(n_side):
     import workloads
     return workloads.taylor_green(n_side)
@@ -159,6 +211,28 @@ def cpu_baseline(w, vel_gpu, n_targets):
         d = vel_gpu.astype(np.float64) - u_ref
         acc = float(np.linalg.norm(d) / np.linalg.norm(u_ref))
     return out, acc
+
+
+def cpu_fmm_baseline():
+    """The oracle's plain FP64 FMM (Cartesian Taylor expansions, numpy) timed on the host:
+    the 4096-blob jittered lattice in full (p=6, theta 0.5, ncrit 32, free space), and a
+    4096-blob Taylor-Green lattice (16^3) with the benchmark's parameters (p=10, theta 0.4,
+    ncrit 64, periodic, 3 image levels) -- the 128^3 evaluation would take hours in it."""
+    import workloads
+    from oracle import fmm as ofmm
+    out = {}
+    for key, w, args, kw in (
+            ("jittered_lattice_16", workloads.jittered_lattice(16), (6, 0.5, 32), {}),
+            ("taylor_green_16_p10", workloads.taylor_green(16), (10, 0.4, 64), None)):
+        if kw is None:
+            kw = dict(periodic=True, box_min=w["box_min"], box_len=w["box_len"], images=3)
+        t0 = time.perf_counter()
+        ofmm.fmm(w["pos"], w["gamma"], float(w["sigma"]), *args, **kw)
+        dt = time.perf_counter() - t0
+        n = w["pos"].shape[0]
+        out[key] = {"particles_per_s": n / dt, "seconds": dt, "n": n, "p": args[0], "theta": args[1],
+                    "ncrit": args[2], "threads": "numpy (BLAS calls may use several cores)"}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -226,9 +300,10 @@ def serving_inputs(specs):
     return out
 
 
-def serve_stream(specs, inputs, workers, batching, budget, ncrit=64):
+def serve_stream(specs, inputs, workers, batching, budget, ncrit=64, keep=()):
     """Submit every request at its arrival time; per-request latency = completion - arrival.
-    ncrit = 0: the server autotunes the leaf size per class on the warm-up requests."""
+    ncrit = 0: the server autotunes the leaf size per class on the warm-up requests.
+    keep: indices of requests whose velocity is returned (for the accuracy check)."""
     import numpy as np
     from paper_1106_5273_gb300 import Server
     srv = Server(workers=workers, batching=batching, theta=0.5, ncrit=ncrit, hbm_budget_bytes=budget,
@@ -250,9 +325,11 @@ def serve_stream(specs, inputs, workers, batching, budget, ncrit=64):
                 break
             time.sleep(min(dt, 0.001))
         tickets.append(srv.submit(x["pos"], x["gamma"], r["p"], x["sigma"], periodic=r["periodic"], box=x["box"]))
-    lat, done, bsz, status = [], [], [], []
-    for r, t in zip(specs, tickets):
-        res, _, _ = srv.wait(t, 3600.0)
+    lat, done, bsz, status, kept = [], [], [], [], {}
+    for k, (r, t) in enumerate(zip(specs, tickets)):
+        res, u, _ = srv.wait(t, 3600.0)
+        if k in keep:
+            kept[k] = u
         lat.append(res["t_done"] - (t0 + r["t"]))
         done.append(res["t_done"])
         bsz.append(res["batch_problems"])
@@ -267,32 +344,80 @@ def serve_stream(specs, inputs, workers, batching, budget, ncrit=64):
                 "max": float(lat.max())},
             "requests": len(specs), "particles": parts, "failed": int(sum(1 for s_ in status if s_ != 0)),
             "batches": c1["batches"] - c0["batches"], "mean_batch_problems": float(np.mean(bsz)),
-            "peak_device_bytes": c1["peak_bytes"], "memory_waits": c1["memory_waits"] - c0["memory_waits"],
-            "workers": workers, "batching": bool(batching)}
+            "peak_device_bytes": c1["peak_bytes"], "hbm_budget_bytes": budget,
+            "memory_waits": c1["memory_waits"] - c0["memory_waits"],
+            "workers": workers, "batching": bool(batching), "ncrit": ncrit or "autotuned per class", "_kept": kept}
+
+
+def serving_accuracy(specs, inputs, kept, ntargets=256):
+    """rel-L2 of the velocity of sampled requests: Plummer requests against the FP64 direct sum
+    (C, OpenMP) on sampled targets, periodic spectrum requests against the exact blob field of
+    their generating modes."""
+    import numpy as np
+    import workloads
+    from oracle import direct as od
+    from oracle import periodic as op
+    od.build()
+    out = []
+    for k, u in sorted(kept.items()):
+        r, x = specs[k], inputs[k]
+        n = r["n"]
+        idx = np.random.default_rng(k).choice(n, size=min(ntargets, n), replace=False)
+        if r["periodic"]:
+            m = int(round(n ** (1.0 / 3.0)))
+            w = workloads.random_spectrum(m, seed=r["seed"])
+            ref, _ = op.spectral_field(w["modes"], w["uhat"], w["pos"][idx].astype(np.float64),
+                                       w["gamma"][idx].astype(np.float64), float(w["sigma"]))
+        else:
+            ref, _ = od.direct(x["pos"][idx], x["gamma"][idx], x["pos"], x["gamma"], float(x["sigma"]),
+                               skip_self=True)
+        e = float(np.linalg.norm(u[idx].astype(np.float64) - ref) / np.linalg.norm(ref))
+        out.append({"request": k, "n": n, "p": r["p"], "kind": r["kind"], "rel_l2_u": e})
+    return out
+
+
+def _pick_checked(specs):
+    """The smallest periodic and the two smallest free-space requests of each order."""
+    keep = []
+    for p in SERVING_ORDERS:
+        for per, cnt in ((True, 1), (False, 2)):
+            c = sorted((r["n"], k) for k, r in enumerate(specs) if r["p"] == p and r["periodic"] == per)
+            keep += [k for _, k in c[:cnt]]
+    return tuple(sorted(keep))
 
 
 def run_serving(args, horizon=None):
     """Poisson request stream (N log-uniform in [1e4, 4e6], p in {4, 8, 12}, 30% periodic
-    random-spectrum lattices, 70% Plummer clusters, theta 0.5, ncrit 64): continuous batching
-    with two workers against one request per call on one worker."""
+    random-spectrum lattices, 70% Plummer clusters, theta 0.5): continuous batching against one
+    request per call, both with two workers and the leaf size autotuned per class, at the
+    configured rate (above what one GPU evaluates: queueing) and at 20 requests/s (below
+    saturation: service time); velocity accuracy of sampled requests for both arms."""
     import workloads
     horizon = args.serving_seconds if horizon is None else horizon
-    specs = workloads.request_specs(rate=args.serving_rate, horizon_s=horizon, orders=SERVING_ORDERS)
-    inputs = serving_inputs(specs)
     budget = 200 << 30
-    served = serve_stream(specs, inputs, 2, 1, budget, ncrit=0)
-    plain = serve_stream(specs, inputs, 1, 0, budget, ncrit=64)
-    return {"stream": "Poisson %.0f req/s for %.1f s (%d requests, %d particles), N log-uniform [1e4, 4e6], "
-                      "p in {4,8,12}, 30%% periodic spectrum / 70%% Plummer, host arrays in and out"
-                      % (args.serving_rate, horizon, len(specs), served["particles"]),
-            "continuous_batching": served, "one_request_per_call": plain,
-            "ncrit": "continuous batching: autotuned per (p, periodic) class on the warm-up requests; "
-                     "one request per call: 64",
-            "speedup_particles_per_s": served["particles_per_s"] / plain["particles_per_s"],
-            "p99_ratio": plain["latency_ms"]["p99"] / served["latency_ms"]["p99"]}
+    out = {"hbm_budget_bytes": budget}
+    for key, rate, hz in (("saturated", args.serving_rate, horizon), ("below_saturation", 20.0, 2.0)):
+        specs = workloads.request_specs(rate=rate, horizon_s=hz, orders=SERVING_ORDERS)
+        inputs = serving_inputs(specs)
+        keep = _pick_checked(specs) if key == "saturated" else ()
+        served = serve_stream(specs, inputs, 2, 1, budget, ncrit=0, keep=keep)
+        plain = serve_stream(specs, inputs, 2, 0, budget, ncrit=0, keep=keep)
+        ks, kp = served.pop("_kept"), plain.pop("_kept")
+        entry = {"stream": "Poisson %.0f req/s for %.1f s (%d requests, %d particles), N log-uniform [1e4, 4e6], "
+                           "p in {4,8,12}, 30%% periodic spectrum / 70%% Plummer, host arrays in and out"
+                           % (rate, hz, len(specs), served["particles"]),
+                 "continuous_batching": served, "one_request_per_call": plain,
+                 "speedup_particles_per_s": served["particles_per_s"] / plain["particles_per_s"],
+                 "p99_ratio": plain["latency_ms"]["p99"] / served["latency_ms"]["p99"]}
+        if keep:
+            entry["accuracy"] = {"continuous_batching": serving_accuracy(specs, inputs, ks),
+                                 "one_request_per_call": serving_accuracy(specs, inputs, kp)}
+        out[key] = entry
+    out["arms"] = "both arms: 2 workers, leaf size autotuned per (p, periodic) class on the warm-up requests"
+    return out
 
 
-def run_batched(args):
+def run_batched(args, compact=False):
     """512 independent free-space problems (N log-uniform [1e3, 1e6], ball or Plummer, p in
     {4, 8, 12}, theta 0.5): one fmm_eval_batch per order, leaf size autotuned per order on a
     sample of its problems (untimed), against one fmm_eval_velocity_stretching per problem
@@ -310,7 +435,7 @@ def run_batched(args):
         groups.setdefault(sp["p"], []).append(sp)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    steps, warm = max(1, min(args.steps, 5)), max(3, args.warmup)
+    steps, warm = (2, 3) if compact else (max(1, min(args.steps, 5)), max(3, args.warmup))
 
     def timed(fn, nsteps, nwarm):
         for _ in range(nwarm):
@@ -387,6 +512,121 @@ def run_batched(args):
             "gpu_launches": l_b, "groups": per_group,
             "one_problem_per_call": {"value": ntot / (t_p * 1e-3), "ms_per_step": t_p, "gpu_launches": l_p},
             "speedup": t_p / t_b, "clocks": clk}
+
+
+def timed_evals(fn, steps, warmup, flush, stream, stats=None):
+    """CUDA-event times (ms) of fn() after warm-up, L2 flushed before each; also the phase
+    stats of each step when stats (a plan) is given."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms, st = [], []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        if stats is not None:
+            st.append(stats.stats())
+    return ms, st
+
+
+def run_tree_reuse(plan, pos, gam, sig, vel, dg, flush, stream, steps, w):
+    """Strength-only re-evaluation on the kept tree (fmm_eval_strengths) and its captured CUDA
+    graph (fmm_graph_launch), against the full evaluation: the vortex method puts its particles
+    back on the same lattice every step and keeps the tree (Sec. 3.4)."""
+    import numpy as np
+    import torch
+    from paper_1106_5273_gb300 import kernel_launch_count
+    plan.eval(pos, gam, sigma_uniform=sig, vel=vel, dgamma=dg)
+    torch.cuda.synchronize()
+    ref_u = vel.clone()
+    gbuf = gam.clone()
+    ms_s, _ = timed_evals(lambda: plan.eval_strengths(gbuf, vel, dg), steps, 3, flush, stream)
+    graph = plan.capture_graph(gbuf, vel, dg)
+    l0 = kernel_launch_count()
+    ms_g, _ = timed_evals(graph.launch, steps, 3, flush, stream)
+    launches = (kernel_launch_count() - l0) // (steps + 3)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(vel, ref_u)) and plan.status() == 0
+    graph.close()
+    n = pos.shape[0]
+    t_s, t_g = sum(ms_s) / len(ms_s), sum(ms_g) / len(ms_g)
+    return {"eval_strengths": {"ms_per_step": t_s, "particles_per_s": n / (t_s * 1e-3)},
+            "graph_replay": {"ms_per_step": t_g, "particles_per_s": n / (t_g * 1e-3), "gpu_launches": launches,
+                             "graph_launches_per_step": 1},
+            "bit_identical_to_full_evaluation": same, "steps": steps,
+            "note": "same positions and core widths, new strengths: tree, lists and M2L operators kept"}
+
+
+def run_config3(args, steps=3, warmup=1):
+    """The 512^3 random-phase spectrum workload (E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4, u_rms = 1,
+    sigma = 1.2h) in the periodic cube: p=10, theta 0.4, ncrit 64, tensor-core M2L, with its own
+    clocks, phases, rooflines and rel-L2 on 4096 sampled targets against the exact blob field
+    of the generating modes."""
+    import numpy as np
+    import torch
+    import workloads
+    from oracle import periodic as op
+    from paper_1106_5273_gb300 import Params, Plan, kernel_launch_count
+    t0 = time.perf_counter()
+    w = workloads.random_spectrum(512)
+    gen_s = time.perf_counter() - t0
+    n = w["pos"].shape[0]
+    idx = np.random.default_rng(7).choice(n, size=4096, replace=False)
+    us, ss = op.spectral_field(w["modes"], w["uhat"], w["pos"][idx].astype(np.float64),
+                               w["gamma"][idx].astype(np.float64), float(w["sigma"]))
+    prm = Params.default(p=10, theta=0.4, ncrit=64, periodic=1, box_min=w["box_min"], box_len=w["box_len"],
+                         images=5)
+    plan = Plan(n, prm)
+    pos = torch.from_numpy(w["pos"]).cuda()
+    gam = torch.from_numpy(w["gamma"]).cuda()
+    sig = float(w["sigma"])
+    del w["pos"], w["gamma"]
+    vel = torch.empty((n, 3), device="cuda")
+    dg = torch.empty((n, 3), device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    plan.set_timing(True)
+    fn = lambda: plan.eval(pos, gam, sigma_uniform=sig, vel=vel, dgamma=dg)
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = kernel_launch_count()
+    ms, sts = timed_evals(fn, steps, 0, flush, stream, stats=plan)
+    launches = (kernel_launch_count() - l0) // steps
+    clk = clocks.stop()
+    st = sts[-1]
+    t = sum(ms) / len(ms)
+    ti = torch.from_numpy(idx).cuda()
+    u = vel[ti].cpu().numpy().astype(np.float64)
+    s_ = dg[ti].cpu().numpy().astype(np.float64)
+    eu = float(np.linalg.norm(u - us) / np.linalg.norm(us))
+    es = float(np.linalg.norm(s_ - ss) / np.linalg.norm(ss))
+    out = {"workload": "random-spectrum-512^3", "n": n, "p": 10, "theta": 0.4, "ncrit": 64, "images": 5,
+           "images_note": "27 explicit images + 4 lattice levels (3^5 cells per axis): with 3 levels the truncated "
+                          "lattice sum of this field leaves rel-L2(u) 1.04e-4",
+           "split_tie": "source (Alg. 1 as printed)", "steps": steps, "warmup": warmup, "ms_per_step": t,
+           "particles_per_s": n / (t * 1e-3), "gpu_launches": launches,
+           "phases_ms": {k: float(np.mean([getattr(x, k) for x in sts])) for k in PHASES},
+           "work": {k: getattr(st, k) for k in WORK},
+           "roofline": p2p_roofline(st, float(np.mean([x.ms_p2p for x in sts]))),
+           "roofline_m2l": m2l_roofline(st, 10),
+           "accuracy": {"rel_l2_u": eu, "rel_l2_s": es, "targets": 4096,
+                        "reference": "exact blob field of the generating Fourier modes (oracle)"},
+           "device_bytes": plan.device_bytes(), "input_generation_s": gen_s, "clocks": clk,
+           "l2": "inputs (4.3 GB) larger than L2; also flushed before every timed step"}
+    plan.close()
+    del pos, gam, vel, dg, flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -494,15 +734,6 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_t = sum(e2e_ms) / len(e2e_ms) if e2e_ms else float("nan")
     # roofline of the dominant kernel (P2P), from its CUDA-event time inside the step
-    pairs = st.p2p_pairs
-    p2p_t = sum(p2p_ms) / len(p2p_ms) * 1e-3
-    flops = (P2P_FLOPS["near"] * st.p2p_pairs_near + P2P_FLOPS["mid"] * st.p2p_pairs_mid
-             + P2P_FLOPS["far"] * st.p2p_pairs_far)
-    achieved = flops / p2p_t / 1e12
-    slots = (P2P_SLOTS["near"] * st.p2p_pairs_near + P2P_SLOTS["mid"] * st.p2p_pairs_mid
-             + P2P_SLOTS["far"] * st.p2p_pairs_far)
-    clk_mhz = 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "p2p_traffic.json")
     if os.path.exists(prof):
@@ -510,23 +741,16 @@ def main():
             traffic = json.load(open(prof)).get("bytes_per_launch_full_workload")
         except Exception:
             traffic = None
-    # second roofline: the tensor-core M2L phase.  Useful flops: a P x P operator
-    # on 3 components per M2L pair, 2 P^2 x 3 each, times the 3 BF16 products of
-    # the split-precision scheme; peak = the measured dense BF16 rate.
-    P = int(w["p"]) ** 2
-    m2l_flops = 3 * 2.0 * P * P * 3 * st.m2l_pairs
-    bf16_peak, bf16_src = 1900.0, "fallback (no MEASURED_PEAKS.json)"
-    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(mp):
-        try:
-            bf16_peak, bf16_src = float(json.load(open(mp))["bf16_tflops"]), "measured (MEASURED_PEAKS.json, burst)"
-        except Exception:
-            pass
-    m2l_ach = m2l_flops / (st.ms_m2l * 1e-3) / 1e12 if st.ms_m2l > 0 and st.m2l_tensor else None
+    roof = p2p_roofline(st, sum(p2p_ms) / len(p2p_ms), traffic)
+    roof_m2l = m2l_roofline(st, w["p"])
+    reuse = None
+    if rank == 0 and not args.no_reuse:
+        reuse = run_tree_reuse(plan, pos, gam, sig, vel, dg, flush, stream, max(3, args.steps // 2), w)
     if rank == 0:
         cpu, acc = (None, None)
         if not args.no_cpu_baseline and world == 1:
             cpu, acc = cpu_baseline(w, vel.cpu().numpy(), args.cpu_targets)
+            cpu["fmm"] = cpu_fmm_baseline()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -539,30 +763,26 @@ def main():
             "e2e": {"value": job_value(n, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": int(2 * n * 12), "d2h_bytes_per_step": int(2 * n * 12)},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": "k_p2p_x2", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                         "flops_per_pair": P2P_FLOPS, "pairs_per_launch": pairs,
-                         "pairs_by_class": {"near": st.p2p_pairs_near, "mid": st.p2p_pairs_mid,
-                                            "far": st.p2p_pairs_far},
-                         "ms_per_launch": p2p_t * 1e3,
-                         "fp32_pipe_slot_frac": slots / p2p_t / (SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6),
-                         "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
-            "paper_convention_tflops": 174 * pairs / p2p_t / 1e12,
-            "roofline_m2l": None if m2l_ach is None else {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": m2l_ach, "peak": bf16_peak,
-                             "unit": "TFLOP/s", "frac": (m2l_ach / bf16_peak) if m2l_ach else None,
-                             "peak_source": bf16_src, "ms": st.ms_m2l,
-                             "flops": "3 BF16 products x 2 P^2 x 3 components per M2L pair (useful rows only)"},
+            "roofline": roof,
+            "paper_convention_tflops": 174 * st.p2p_pairs / (roof["ms_per_launch"] * 1e-3) / 1e12,
+            "roofline_m2l": roof_m2l,
             "velocity_only": velocity_only,
-            "phases_ms": {k: getattr(st, k) for k in ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l",
-                                                       "ms_downward", "ms_p2p", "ms_total")},
-            "work": {k: getattr(st, k) for k in ("ncells", "nleaves", "nlevels", "p2p_cell_pairs", "p2p_pairs",
-                                                  "m2l_pairs", "m2l_steps", "m2l_keys", "m2l_built", "m2l_tensor")},
+            "phases_ms": {k: getattr(st, k) for k in PHASES},
+            "work": {k: getattr(st, k) for k in WORK},
             "clocks": clk,
             "cpu_baseline": cpu,
+            "tree_reuse": reuse,
         }
-        if not args.no_serving and world == 1:
+        if world == 1:
             plan.close()
-            line["serving"] = run_serving(args)
+            del pos, gam, vel, dg
+            torch.cuda.empty_cache()
+            if not args.no_config3:
+                line["config3"] = run_config3(args)
+            if not args.no_batched:
+                line["batched"] = run_batched(args, compact=True)
+            if not args.no_serving:
+                line["serving"] = run_serving(args)
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:

@@ -265,6 +265,13 @@ int64_t fmm_plan_device_bytes(fmm_plan plan);
  * the worker first frees idle plans, then takes fewer requests, then waits
  * for other workers (which free their idle plans while anyone waits).  A
  * request that does not fit the budget on its own completes with FMM_E_NOMEM.
+ * The budget is also enforced on what the plans actually allocate: every
+ * device allocation of a worker is charged to it first and refused if the
+ * server's bytes would exceed hbm_budget_bytes.  A batch refused that way
+ * (its class's need was underestimated) goes back to the front of the queue
+ * with the class's per-particle need raised; a request refused more than 8
+ * times completes with FMM_E_NOMEM.  So the device bytes the server holds
+ * never exceed the budget (fmm_server_counters.peak_bytes).
  *
  * batching = 0 gives the one-problem-per-call path for comparison: every
  * request is evaluated alone through fmm_eval_velocity_stretching.
@@ -285,6 +292,9 @@ typedef struct {
   float sigma_sep;
   int32_t images;
   int32_t m2l_mode;             /* the plans' other parameters take fmm_params_default's values */
+  int32_t pad;
+  int64_t model_bytes_per_particle; /* first estimate of a class's workspace per particle
+                                       (0: 2048 bytes) until its evaluations measure it */
 } fmm_server_params;
 
 /* One request.  Host arrays; the caller keeps them valid (and does not read
@@ -314,7 +324,8 @@ typedef struct {
 } fmm_request_result;
 
 /* Server counters: batches run, requests done, particles done, the largest
- * number of device bytes held at once, and the batches that waited for memory. */
+ * number of device bytes the server had allocated at once, and the batches
+ * that waited for memory (or were refused by the budget and re-queued). */
 typedef struct {
   int64_t batches, requests, particles, peak_bytes, memory_waits;
 } fmm_server_counters;
@@ -362,6 +373,52 @@ const char* fmm_strerror(int code);
 int fmm_eval_targets(fmm_plan plan, int64_t ns, const float* src_pos, const float* src_gamma,
                      const float* src_sigma, float sigma_uniform, int64_t nt, const float* tgt_pos,
                      float* vel, void* cuda_stream);
+
+/*
+ * Re-evaluation with new strengths on the plan's last tree.  The vortex
+ * method re-initialises its particles onto the same positions every step, so
+ * the tree structure is built once and reused (Sec. 3.4).  After a full
+ * evaluation (fmm_eval_velocity_stretching or fmm_eval_batch) of n particles,
+ * this call evaluates velocity and stretching for the SAME positions and core
+ * widths and new strengths:
+ *   gamma[n][3]            device float32, in the caller's particle order
+ *   vel[n][3], dgamma[n][3] device float32 outputs (either may be NULL)
+ * It keeps the sorted positions, octree, interaction lists and M2L operators
+ * of that evaluation and runs only the strength-dependent steps (gather of
+ * the strengths into the sorted order, P2M/M2M, M2L, periodic lattice
+ * operator and dipole term, L2L/L2P, P2P and the combine), with the same
+ * kernels in the same order, so the result is bit-identical to a full
+ * evaluation of the same input.  Fully asynchronous on cuda_stream: no host
+ * synchronization, no allocation; errors raised by kernels (FMM_E_TIMEOUT)
+ * are kept on the device and read by fmm_plan_status.  FMM_E_INVAL if the
+ * plan's last call was not a successful full evaluation (or was
+ * fmm_eval_targets, whose tree also holds the targets).
+ */
+int fmm_eval_strengths(fmm_plan plan, const float* gamma, float* vel, float* dgamma,
+                       void* cuda_stream);
+
+/*
+ * The error status raised on the device by the plan's last evaluation
+ * (FMM_OK or FMM_E_TIMEOUT): waits for cuda_stream, then reads one int.
+ */
+int fmm_plan_status(fmm_plan plan, void* cuda_stream);
+
+/*
+ * A CUDA graph of fmm_eval_strengths for fixed buffers: the call's kernel
+ * launches are recorded once (stream capture) and replayed by
+ * fmm_graph_launch, one graph launch per evaluation, nothing on the host in
+ * between.  gamma, vel and dgamma are the device arrays every replay reads
+ * and writes: write the next strengths into gamma (stream-ordered), launch,
+ * read vel/dgamma.  The graph is tied to the plan's current tree: a later
+ * full evaluation on the plan makes fmm_graph_launch return FMM_E_INVAL
+ * (capture again).  Destroy graphs before their plan.
+ */
+typedef struct fmm_graph_s* fmm_graph;
+int fmm_graph_capture(fmm_plan plan, const float* gamma, float* vel, float* dgamma, fmm_graph* out);
+int fmm_graph_launch(fmm_graph graph, void* cuda_stream);
+/* Kernel launches one replay performs (counted in fmm_kernel_launch_count). */
+int64_t fmm_graph_kernel_count(fmm_graph graph);
+void fmm_graph_destroy(fmm_graph graph);
 
 /*
  * All-pairs direct sum of Eqs. (1)-(3) on the device, free space, without

@@ -90,6 +90,14 @@ lib.fmm_eval_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp
 lib.fmm_plan_device_bytes.argtypes = [_vp]
 lib.fmm_plan_device_bytes.restype = _i64
 lib.fmm_morton_order_noalloc.argtypes = [_i64, _vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
+lib.fmm_eval_strengths.argtypes = [_vp, _vp, _vp, _vp, _vp]
+lib.fmm_plan_status.argtypes = [_vp, _vp]
+lib.fmm_graph_capture.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]
+lib.fmm_graph_launch.argtypes = [_vp, _vp]
+lib.fmm_graph_kernel_count.argtypes = [_vp]
+lib.fmm_graph_kernel_count.restype = _i64
+lib.fmm_graph_destroy.argtypes = [_vp]
+lib.fmm_graph_destroy.restype = None
 lib.fmm_kernel_launch_count.argtypes = []
 lib.fmm_kernel_launch_count.restype = ctypes.c_int64
 lib.fmm_plan_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
@@ -216,6 +224,31 @@ class Plan:
             _stream_ptr(stream)), "fmm_eval_batch")
         return vel, dgamma
 
+    def eval_strengths(self, gamma, vel=None, dgamma=None, stream=None, stretching=True):
+        """fmm_eval_strengths: new strengths (torch CUDA [n, 3], the caller's order) on the
+        positions, core widths and tree of the last full evaluation; returns (vel, dgamma)."""
+        import torch
+        n = gamma.shape[0]
+        if n != self.stats().n:
+            raise ValueError("gamma has %d rows, the plan's last evaluation %d" % (n, self.stats().n))
+        if vel is None:
+            vel = torch.empty((n, 3), dtype=torch.float32, device=gamma.device)
+        if dgamma is None and stretching:
+            dgamma = torch.empty((n, 3), dtype=torch.float32, device=gamma.device)
+        if not stretching:
+            dgamma = None
+        _check(lib.fmm_eval_strengths(self._h, _dptr(gamma, name="gamma"), _dptr(vel, name="vel"),
+                                      _dptr(dgamma, name="dgamma"), _stream_ptr(stream)), "fmm_eval_strengths")
+        return vel, dgamma
+
+    def status(self, stream=None):
+        """fmm_plan_status: 0 or the FMM_E_* raised on the device (waits for the stream)."""
+        return int(lib.fmm_plan_status(self._h, _stream_ptr(stream)))
+
+    def capture_graph(self, gamma, vel, dgamma=None):
+        """fmm_graph_capture: a Graph replaying fmm_eval_strengths on these fixed tensors."""
+        return Graph(self, gamma, vel, dgamma)
+
     def device_bytes(self):
         """Device memory the plan holds (fmm_plan_device_bytes)."""
         return int(lib.fmm_plan_device_bytes(self._h))
@@ -254,6 +287,39 @@ class Plan:
         m2l = np.zeros((s.m2l_pairs, 3), np.int32)
         _check(lib.fmm_plan_get_lists(self._h, p2p.ctypes.data, m2l.ctypes.data), "fmm_plan_get_lists")
         return p2p, m2l
+
+
+class Graph:
+    """A captured CUDA graph of fmm_eval_strengths (fmm_graph_*).  Keeps the plan and the
+    tensors it reads and writes alive."""
+
+    def __init__(self, plan, gamma, vel, dgamma=None):
+        n = plan.stats().n
+        for t, name in ((gamma, "gamma"), (vel, "vel")) + (((dgamma, "dgamma"),) if dgamma is not None else ()):
+            if t.dim() != 2 or t.shape[0] != n or t.shape[1] != 3:
+                raise ValueError("%s must have shape [%d, 3]" % (name, n))
+        h = _vp()
+        _check(lib.fmm_graph_capture(plan._h, _dptr(gamma, name="gamma"), _dptr(vel, name="vel"),
+                                     _dptr(dgamma, name="dgamma"), ctypes.byref(h)), "fmm_graph_capture")
+        self._h = h
+        self._keep = (plan, gamma, vel, dgamma)
+
+    def launch(self, stream=None):
+        _check(lib.fmm_graph_launch(self._h, _stream_ptr(stream)), "fmm_graph_launch")
+
+    def kernel_count(self):
+        return int(lib.fmm_graph_kernel_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fmm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_N = 1 << 20
@@ -335,7 +401,8 @@ class ServerParams(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("batching", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("max_batch_particles", ctypes.c_int64), ("max_batch_problems", ctypes.c_int32),
                 ("theta", ctypes.c_float), ("ncrit", ctypes.c_int32), ("sigma_sep", ctypes.c_float),
-                ("images", ctypes.c_int32), ("m2l_mode", ctypes.c_int32)]
+                ("images", ctypes.c_int32), ("m2l_mode", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("model_bytes_per_particle", ctypes.c_int64)]
 
     @classmethod
     def default(cls, **kw):

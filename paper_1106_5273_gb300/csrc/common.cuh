@@ -32,18 +32,56 @@ constexpr int kImageZero = 13;     // image index of the zero shift, (ox+1)*9+(o
     if (r_ != FMM_OK) return r_;                   \
   } while (0)
 
+// A device-byte budget shared by a group of host threads (the serving loop
+// installs one on its worker threads with set_thread_budget).  Every DBuf
+// allocation made by such a thread is charged to it before cudaMalloc is
+// called and refused (FMM_E_NOMEM) if the charge would take the bytes held
+// past the limit; the buffer returns its bytes to the same budget when it is
+// released, whichever thread releases it.
+struct ByteBudget {
+  std::atomic<int64_t> held{0};
+  std::atomic<int64_t> peak{0};
+  std::atomic<int64_t> refusals{0};
+  int64_t limit = 0;
+  bool charge(int64_t b) {
+    int64_t cur = held.load();
+    do {
+      if (cur + b > limit) {
+        ++refusals;
+        return false;
+      }
+    } while (!held.compare_exchange_weak(cur, cur + b));
+    int64_t pk = peak.load();
+    while (cur + b > pk && !peak.compare_exchange_weak(pk, cur + b)) {
+    }
+    return true;
+  }
+  void credit(int64_t b) { held -= b; }
+};
+inline ByteBudget*& thread_budget() {
+  static thread_local ByteBudget* b = nullptr;
+  return b;
+}
+inline void set_thread_budget(ByteBudget* b) { thread_budget() = b; }
+
 // Device buffer that only grows.
 struct DBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  ByteBudget* owner = nullptr;  // budget charged with `bytes` (nullptr: none)
   int ensure(size_t need) {
     if (need <= bytes) return FMM_OK;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    bytes = 0;
     size_t nb = need + need / 4 + 256;
-    if (cudaMalloc(&ptr, nb) != cudaSuccess) return FMM_E_NOMEM;
+    ByteBudget* bb = thread_budget();
+    if (bb && !bb->charge((int64_t)nb)) return FMM_E_NOMEM;  // the old buffer stays
+    release();
+    if (cudaMalloc(&ptr, nb) != cudaSuccess) {
+      ptr = nullptr;
+      if (bb) bb->credit((int64_t)nb);
+      return FMM_E_NOMEM;
+    }
     bytes = nb;
+    owner = bb;
     return FMM_OK;
   }
   // Grow to at least `need` bytes keeping the current contents.
@@ -51,20 +89,32 @@ struct DBuf {
     if (need <= bytes) return FMM_OK;
     void* np = nullptr;
     size_t nb = need + need / 4 + 256;
-    if (cudaMalloc(&np, nb) != cudaSuccess) return FMM_E_NOMEM;
-    if (ptr) {
-      if (cudaMemcpyAsync(np, ptr, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return FMM_E_CUDA;
-      if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_E_CUDA;
-      cudaFree(ptr);
+    ByteBudget* bb = thread_budget();
+    if (bb && !bb->charge((int64_t)nb)) return FMM_E_NOMEM;
+    if (cudaMalloc(&np, nb) != cudaSuccess) {
+      if (bb) bb->credit((int64_t)nb);
+      return FMM_E_NOMEM;
     }
+    if (ptr) {
+      if (cudaMemcpyAsync(np, ptr, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaFree(np);
+        if (bb) bb->credit((int64_t)nb);
+        return FMM_E_CUDA;
+      }
+    }
+    release();
     ptr = np;
     bytes = nb;
+    owner = bb;
     return FMM_OK;
   }
   void release() {
     if (ptr) cudaFree(ptr);
+    if (owner) owner->credit((int64_t)bytes);
     ptr = nullptr;
     bytes = 0;
+    owner = nullptr;
   }
   template <class T>
   T* as() const { return reinterpret_cast<T*>(ptr); }

@@ -73,6 +73,8 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   if (!sg && !sig && !(sig_u > 0.f)) return FMM_E_INVAL;
   memset(&p->stats, 0, sizeof(p->stats));
   p->last_n = n;
+  p->reuse_ok = 0;
+  ++p->epoch;
   p->ncells = p->nleaves = 0;
   p->n_p2p = p->n_m2l = p->n_keys = p->n_steps = p->p2p_pairs = 0;
   p->level_begin.clear();
@@ -148,6 +150,10 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   unsigned long long cls[3];
   memcpy(cls, reinterpret_cast<char*>(p->pinned) + 128, sizeof(cls));
   if (hf != 0) return hf;
+  p->reuse_ok = 1;
+  p->reuse_ps = sig ? 1 : 0;
+  p->reuse_sig_u = sig_u;
+  p->reuse_smax = smax;
   fmm_stats& st = p->stats;
   st.n = n;
   st.ncells = p->ncells;

@@ -117,6 +117,14 @@ struct fmm_plan_s {
   int64_t n_p2p = 0, n_m2l = 0, n_keys = 0, n_steps = 0, p2p_pairs = 0;
   int64_t last_n = 0;
   int last_tc = 0;
+  // tree reuse (fmm_eval_strengths): set by a successful full evaluation of
+  // the plan's own particles; epoch counts full evaluations (a captured graph
+  // is valid only within the epoch it was captured in)
+  int reuse_ok = 0;
+  int reuse_ps = 0;         // the last evaluation had a per-particle sigma array
+  float reuse_sig_u = 0.f;  // its uniform sigma
+  double reuse_smax = 0.0;  // its largest sigma
+  int64_t epoch = 0;
   fmm_stats stats;
   cudaEvent_t ev[8];
   int have_events = 0;
@@ -149,6 +157,8 @@ int m2l_simt(fmm_plan p, cudaStream_t s);
 int m2l_tensor(fmm_plan p, cudaStream_t s);
 // downward.cu
 int downward_pass(fmm_plan p, int64_t n, cudaStream_t s);
+// reuse.cu
+int eval_strengths(fmm_plan p, const float* gam, float* vel, float* dg, cudaStream_t s);
 // p2p.cu
 int p2p_near(fmm_plan p, int64_t n, float sig_u, int per_particle_sigma, double smax, float* vel, float* dg,
              cudaStream_t s);

@@ -37,7 +37,10 @@ struct Req {
   fmm_request r;
   fmm_request_result res;
   bool done = false;
+  int retries = 0;  // batches of this request refused by the byte budget
 };
+
+constexpr int kMaxRetries = 8;
 
 struct PlanRec {
   fmm_plan plan = nullptr;
@@ -77,6 +80,9 @@ struct fmm_server_s {
   int mem_waiters = 0;
   int probing = 0;  // a first batch of a class is running
   fmm_server_counters ctr{};
+  // every device byte the workers allocate is charged here first; an
+  // allocation past hbm_budget_bytes fails (FMM_E_NOMEM) instead of happening
+  fmm::ByteBudget budget;
   std::chrono::steady_clock::time_point t0;
 
   double now() const {
@@ -93,8 +99,14 @@ int64_t new_plan_capacity(fmm_server S, int64_t n) { return std::max<int64_t>(n,
 // Bytes a worker will hold after running a batch of `n` particles of class c:
 // its other plans, this class's plan (creation bytes + the workspace model)
 // and the staging buffers.
+Model initial_model(fmm_server S) {
+  Model m;
+  if (S->prm.model_bytes_per_particle > 0) m.per = (double)S->prm.model_bytes_per_particle;
+  return m;
+}
+
 int64_t projected(fmm_server S, Worker* W, int c, int64_t n) {
-  const Model m = S->model.count(c) ? S->model[c] : Model();
+  const Model m = S->model.count(c) ? S->model[c] : initial_model(S);
   int64_t other_plans = 0, cur = 0, base = kPlanBytesPerCapacity * new_plan_capacity(S, n);
   for (auto& kv : W->plans) {
     if (kv.first == c) {
@@ -215,6 +227,7 @@ int run_batch(fmm_server S, Worker* W, std::vector<fmm_request>& rs, int64_t nto
 
 void worker_loop(fmm_server S, Worker* W) {
   cudaSetDevice(S->device);
+  fmm::set_thread_budget(&S->budget);
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
     S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
@@ -309,9 +322,48 @@ void worker_loop(fmm_server S, Worker* W) {
     PlanRec rec = W->plans.count(c) ? W->plans[c] : PlanRec();
     const int ncrit = S->prm.ncrit > 0 ? S->prm.ncrit : (S->tuned.count(c) ? S->tuned[c] : 0);
     int ncrit_used = ncrit;
+    const int64_t others_at_start = S->held_total - W->held;
     lk.unlock();
     int rc = run_batch(S, W, rs, ntot, &rec, ncrit, &ncrit_used);
     lk.lock();
+    if (rc == FMM_E_NOMEM && ntot > 0) {
+      // An allocation of this batch was refused by the byte budget (or the
+      // device is out of memory): the class's footprint was underestimated.
+      // Raise its per-particle need to at least what the batch could not fit
+      // in, free this worker's plans, and return the requests to the front of
+      // the queue, where the next batch is formed with the larger need (fewer
+      // requests, or a wait for the other workers).  After kMaxRetries refusals
+      // a request completes with FMM_E_NOMEM.
+      W->busy = false;
+      if (probe) S->probing = 0;
+      if (rec.plan) W->plans[c] = rec;
+      else W->plans.erase(c);
+      Model& m = S->model.count(c) ? S->model[c] : (S->model[c] = initial_model(S));
+      const double avail = (double)std::max<int64_t>(budget - others_at_start, 0);
+      m.per = std::max(m.per * 2.0, avail / (double)ntot);
+      m.have_big = true;
+      drop_plans(S, W, -1);
+      std::vector<int64_t> again;
+      const double td = S->now();
+      for (int64_t t : batch) {
+        Req& rq = S->reqs[t];
+        if (++rq.retries <= kMaxRetries) {
+          again.push_back(t);
+          continue;
+        }
+        rq.res.status = FMM_E_NOMEM;
+        rq.res.batch_problems = (int32_t)batch.size();
+        rq.res.batch_particles = ntot;
+        rq.res.worker = W->id;
+        rq.res.t_done = td;
+        rq.done = true;
+      }
+      S->queue.insert(S->queue.begin(), again.begin(), again.end());
+      ++S->ctr.memory_waits;
+      S->cv_done.notify_all();
+      S->cv_work.notify_all();
+      continue;
+    }
     if (rc == FMM_OK && ncrit_used > 0 && !S->tuned.count(c)) S->tuned[c] = ncrit_used;
     W->busy = false;
     if (probe) S->probing = 0;
@@ -396,9 +448,11 @@ int fmm_server_create(const fmm_server_params* prm, fmm_server* out) {
       q.images < 1 || q.images > 8 || (q.m2l_mode & ~(3 | FMM_M2L_SORT_STEPS)) ||
       (q.m2l_mode & 3) > FMM_M2L_TENSOR)
     return FMM_E_INVAL;
+  if (prm->model_bytes_per_particle < 0) return FMM_E_INVAL;
   fmm_server S = new (std::nothrow) fmm_server_s();
   if (!S) return FMM_E_NOMEM;
   S->prm = *prm;
+  S->budget.limit = prm->hbm_budget_bytes;
   S->t0 = std::chrono::steady_clock::now();
   if (cudaGetDevice(&S->device) != cudaSuccess) {
     delete S;
@@ -454,6 +508,7 @@ int fmm_server_get_counters(fmm_server S, fmm_server_counters* out) {
   if (!S || !out) return FMM_E_INVAL;
   std::lock_guard<std::mutex> g(S->mu);
   *out = S->ctr;
+  out->peak_bytes = S->budget.peak.load();  // allocated bytes, never above the budget
   return FMM_OK;
 }
 

@@ -69,6 +69,7 @@ extern "C" int fmm_eval_targets(fmm_plan p, int64_t ns, const float* src_pos, co
   p->prm.sigma_rule = FMM_SIGMA_SOURCE;
   const int rc = fmm_eval_velocity_stretching(p, n, pos, gam, sig, sigma_uniform, p->t_vel.as<float>(), nullptr, stream);
   p->prm.sigma_rule = rule;
+  p->reuse_ok = 0;  // the tree holds the targets too: no strength-only re-evaluation
   FMM_TRY(rc);
   FMM_CUDA_TRY(cudaMemcpyAsync(vel, p->t_vel.as<float>() + 3 * ns, (size_t)nt * 12, cudaMemcpyDeviceToDevice, s));
   return FMM_OK;

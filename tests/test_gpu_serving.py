@@ -158,6 +158,31 @@ def test_serving_memory_budget():
     srv.close()
 
 
+def test_serving_budget_holds_when_the_footprint_model_underestimates():
+    """The class footprint model starts at 1 byte per particle, so the first
+    batch (all twelve 200k-blob requests) is admitted far beyond what the 3 GiB
+    budget holds.  The budget refuses the plan's allocations, the batch goes
+    back to the queue with a larger per-particle need, and every request still
+    completes, bit-identical to its evaluation alone, while the bytes the
+    server allocated never exceed the budget."""
+    from paper_1106_5273_gb300 import Server
+    budget = 3 << 30
+    srv = Server(workers=2, batching=1, theta=THETA, ncrit=NCRIT, hbm_budget_bytes=budget,
+                 max_batch_particles=4000000, model_bytes_per_particle=1)
+    reqs = [dict(w=workloads.plummer(200000, seed=300 + k, sigma_rule="halfmass"), p=4, periodic=False, box=None)
+            for k in range(12)]
+    tickets = _submit_all(srv, reqs)
+    results = [srv.wait(t, 600.0) for t in tickets]
+    c = srv.counters()
+    assert all(res["status"] == 0 for res, _, _ in results), [res["status"] for res, _, _ in results]
+    assert 0 < c["peak_bytes"] <= budget, c
+    assert c["memory_waits"] >= 1  # at least one batch was refused and re-queued
+    for r, (res, u, s) in list(zip(reqs, results))[::5]:
+        ua, sa = _alone(r)
+        assert np.array_equal(u, ua) and np.array_equal(s, sa)
+    srv.close()
+
+
 def test_serving_bad_requests():
     from paper_1106_5273_gb300 import Server, FmmError
     srv = Server(workers=1)
