@@ -369,8 +369,8 @@ def serving_accuracy(specs, inputs, kept, ntargets=256):
             ref, _ = op.spectral_field(w["modes"], w["uhat"], w["pos"][idx].astype(np.float64),
                                        w["gamma"][idx].astype(np.float64), float(w["sigma"]))
         else:
-            ref, _ = od.direct(x["pos"][idx], x["gamma"][idx], x["pos"], x["gamma"], float(x["sigma"]),
-                               skip_self=True)
+            # all sources, the target's own blob included: its pair adds exactly zero to u (d = 0)
+            ref, _ = od.direct(x["pos"][idx], x["gamma"][idx], x["pos"], x["gamma"], float(x["sigma"]))
         e = float(np.linalg.norm(u[idx].astype(np.float64) - ref) / np.linalg.norm(ref))
         out.append({"request": k, "n": n, "p": r["p"], "kind": r["kind"], "rel_l2_u": e})
     return out

@@ -53,6 +53,9 @@ enum {
   FMM_M2L_AUTO = 0,   /* tensor cores (every p) */
   FMM_M2L_SIMT = 1,   /* FP32 CUDA-core GEMM per (target tile, translation) */
   FMM_M2L_TENSOR = 2, /* tcgen05 BF16x3 split products, FP32 accumulation */
+  FMM_M2L_TENSOR_TF32 = 3, /* tcgen05 TF32x3 split products (hi/lo TF32 halves, 22 bits
+                              per operand), FP32 accumulation: ~16x smaller product error
+                              than BF16x3 at about twice its tensor work */
   /* Flag, OR'ed with a mode: build the (tile, translation) steps by a radix
    * sort of the M2L pairs.  Without it the steps come from flag tables over
    * the translations and (tile, translation) bins whenever those tables are
@@ -62,8 +65,8 @@ enum {
 };
 
 /* fmm_params.split_tie: the cell Algorithm 1 splits when the pair's cells are
- * cubes of one size (its radius test "radius of A > radius of B" is read on
- * the cube size, so a tie goes to the ELSE branch). */
+ * cubes of one size (Alg. 1 compares the two cells' radii, read here as their
+ * cube sizes, and splits B unless A is the larger). */
 enum {
   FMM_SPLIT_SOURCE = 0, /* split B, the source cell (Alg. 1 as printed; default) */
   FMM_SPLIT_TARGET = 1  /* split A, the target cell (an alternative, not the printed rule) */
@@ -95,7 +98,8 @@ typedef struct fmm_plan_s* fmm_plan;
  *   outputs    FMM_OUT_VELOCITY | FMM_OUT_STRETCHING, optionally
  *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
  *              output pointer skips that output.
- *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR, optionally | FMM_M2L_SORT_STEPS.
+ *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR / _TENSOR_TF32, optionally
+ *              | FMM_M2L_SORT_STEPS.
  *   p2p_pair_max  two leaves whose particle counts multiply to at most this
  *              do P2P even when the MAC would accept M2L (the cost rule for
  *              cells of "very few particles", Alg. 2); 0 (default): the MAC
@@ -269,8 +273,8 @@ int64_t fmm_plan_device_bytes(fmm_plan plan);
  * device allocation of a worker is charged to it first and refused if the
  * server's bytes would exceed hbm_budget_bytes.  A batch refused that way
  * (its class's need was underestimated) goes back to the front of the queue
- * with the class's per-particle need raised; a request refused more than 8
- * times completes with FMM_E_NOMEM.  So the device bytes the server holds
+ * with the class's per-particle need raised; a request refused more than 4
+ * times while no other worker was running completes with FMM_E_NOMEM.  So the device bytes the server holds
  * never exceed the budget (fmm_server_counters.peak_bytes).
  *
  * batching = 0 gives the one-problem-per-call path for comparison: every

@@ -213,7 +213,7 @@ def traverse(tree, box_len, theta, ksig, sigma_max, periodic=False, p2p_pair_max
         interact(0, 0, o)
     while stack:
         a, b, o = stack.pop()
-        # radius of A > radius of B  <=>  A is the coarser cube
+        # A larger than B  <=>  A is on the coarser level (the cube size)
         split_a = lev[a] < lev[b] or (tie_a and lev[a] == lev[b])
         if split_a and leaf[a]:
             split_a = False

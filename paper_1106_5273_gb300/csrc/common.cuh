@@ -48,6 +48,7 @@ struct ByteBudget {
     do {
       if (cur + b > limit) {
         ++refusals;
+        last_refused() = b;
         return false;
       }
     } while (!held.compare_exchange_weak(cur, cur + b));
@@ -57,6 +58,11 @@ struct ByteBudget {
     return true;
   }
   void credit(int64_t b) { held -= b; }
+  // size of the last allocation this host thread had refused
+  static int64_t& last_refused() {
+    static thread_local int64_t v = 0;
+    return v;
+  }
 };
 inline ByteBudget*& thread_budget() {
   static thread_local ByteBudget* b = nullptr;

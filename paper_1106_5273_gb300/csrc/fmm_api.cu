@@ -24,7 +24,7 @@ int check_params(const fmm_params* q) {
   if (q->periodic != 0 && q->periodic != 1) return FMM_E_INVAL;
   if (q->periodic && (q->images < 1 || q->images > 8 || !(q->box_len > 0.0))) return FMM_E_INVAL;
   if (!(q->sigma_sep >= 0.f)) return FMM_E_INVAL;
-  if (q->m2l_mode & ~(3 | FMM_M2L_SORT_STEPS) || (q->m2l_mode & 3) > FMM_M2L_TENSOR) return FMM_E_INVAL;
+  if (q->m2l_mode & ~(3 | FMM_M2L_SORT_STEPS)) return FMM_E_INVAL;
   if (q->outputs & ~(FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE)) return FMM_E_INVAL;
   if (q->sigma_rule != FMM_SIGMA_SOURCE && q->sigma_rule != FMM_SIGMA_MIXED) return FMM_E_INVAL;
   if (q->p2p_pair_max < 0) return FMM_E_INVAL;
@@ -83,7 +83,7 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   FMM_CUDA_TRY(cudaMemsetAsync(p->flags.ptr, 0, sizeof(int) * 4, s));
   const int m2l_kind = p->prm.m2l_mode & 3;
   p->last_tc = (m2l_kind == FMM_M2L_SIMT) ? 0 : p->tc_ok;
-  if (m2l_kind == FMM_M2L_TENSOR && !p->tc_ok) return FMM_E_INVAL;
+  if ((m2l_kind == FMM_M2L_TENSOR || m2l_kind == FMM_M2L_TENSOR_TF32) && !p->tc_ok) return FMM_E_INVAL;
   Timer tm{p, s};
   tm.mark();
   if (sg) FMM_TRY(build_forest(p, n, pos, gam, sig, *sg, s));
@@ -232,6 +232,7 @@ int fmm_plan_create(const fmm_params* prm, int64_t n_max, fmm_plan* out) {
   p->P = prm->p * prm->p;
   p->Kpad = 128;
   p->tc_ok = 1;  // tcgen05 M2L: one CTA per 128 output rows (two for p > 11)
+  p->tc_kind = (prm->m2l_mode & 3) == FMM_M2L_TENSOR_TF32 ? 1 : 0;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
     return FMM_E_CUDA;

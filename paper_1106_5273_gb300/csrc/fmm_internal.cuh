@@ -46,6 +46,7 @@ struct fmm_plan_s {
   int device = 0;
   int timing = 0;
   int tc_ok = 0;  // tensor-core M2L usable for this p
+  int tc_kind = 0;  // tensor-core element kind: 0 BF16x3, 1 TF32x3 (FMM_M2L_TENSOR_TF32)
   // batched evaluation (several independent problems in one tree forest)
   int batched = 0;         // 1 while the last evaluation was a batch
   int nseg = 1;            // problems (non-empty) of the last evaluation
@@ -85,7 +86,7 @@ struct fmm_plan_s {
   fmm::DBuf tile_groups; // int32 (level, octant) cell counts, then cell and tile offsets of the groups
   fmm::DBuf leaves;                                                 // leaf cell ids
   fmm::DBuf M, L;                                                   // [cells][3][P] FP32
-  fmm::DBuf Mbf;                                                    // [cells][2][3][64 x K chunks] BF16 hi/lo
+  fmm::DBuf Mbf;  // [cells][hi/lo][3][K chunks x 128 bytes] BF16 or TF32 hi/lo
   // traversal
   fmm::DBuf fr0, fr1;                                 // frontier int4 (a,b,o,0)
   fmm::DBuf tcount, tmask, tscan0, tscan1, tscan2;    // per-item scratch
@@ -197,7 +198,13 @@ __host__ __device__ inline void m2l_key_decode(uint64_t key, int* delta, double 
 }
 
 // K chunks of 64 coefficients (4 MMA K-steps of 16) covering P inputs.
-__host__ __device__ inline int m2l_kchunks(int P) { return ((P + 15) / 16 + 3) / 4; }
+// Tensor-core M2L element kinds: 0 = BF16 (kind::f16, K step 16), 1 = TF32
+// (kind::tf32, K step 8).  A K chunk is one 128-byte row of either: 64 BF16 or
+// 32 TF32 values, 4 K steps.
+__host__ __device__ inline int m2l_kstep(int kind) { return kind ? 8 : 16; }
+__host__ __device__ inline int m2l_kchunks(int P, int kind = 0) {
+  return ((P + m2l_kstep(kind) - 1) / m2l_kstep(kind) + 3) / 4;
+}
 // Blocks of 128 output rows (one MMA M) covering P outputs.
 __host__ __device__ inline int m2l_rowblocks(int P) { return (P + 127) / 128; }
 

@@ -98,15 +98,25 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
-// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N = 192, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptors: D f32, both operands K-major, N = 192, M = 128;
+// kind::f16 with A and B BF16 (format 1), kind::tf32 with A and B TF32 (format 2).
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) | ((128u >> 4) << 24);
 
+template <int KIND>
 __device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-          tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-      : "memory");
+  if (KIND == 0)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(kIdescBf16), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(kIdescTf32), "r"(acc)
+        : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -124,11 +134,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// KIND 0: BF16 operands (64 per 128-byte row, K step 16); KIND 1: TF32 (32
+// per row, K step 8).  Tb / Mb hold 128-byte rows: a K chunk of one operator
+// row or one (cell, hi/lo, component) multipole row.
+template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2)
     k_m2l_tc(const int2* __restrict__ tile_range, const int* __restrict__ tfirst, const int* __restrict__ st_slot,
-             const int* __restrict__ st_src, const __nv_bfloat16* __restrict__ Tbf,
-             const __nv_bfloat16* __restrict__ Mbf, int P, int nkc, int ksteps_last, int kpad, int nrh,
-             const int* __restrict__ tcell, float* __restrict__ L, int* __restrict__ flag) {
+             const int* __restrict__ st_src, const uint8_t* __restrict__ Tb, const uint8_t* __restrict__ Mb, int P,
+             int nkc, int ksteps_last, int nrh, const int* __restrict__ tcell, float* __restrict__ L,
+             int* __restrict__ flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tile = blockIdx.x;
@@ -186,7 +200,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int src = (k & 1) ? srcB : srcA;
         v[q] = make_uint4(0u, 0u, 0u, 0u);
         if (src >= 0)
-          v[q] = __ldg(reinterpret_cast<const uint4*>(Mbf + (((size_t)src * 2 + h) * 3 + (k >> 1)) * kpad + kc * 64) + j);
+          v[q] = __ldg(reinterpret_cast<const uint4*>(Mb + ((((size_t)src * 2 + h) * 3 + (k >> 1)) * nkc + kc) * 128) +
+                       j);
       }
       if (!mbar_wait(empty(stage), ph ^ 1u, abort)) break;
 #pragma unroll
@@ -211,9 +226,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (!mbar_wait(empty(stage), ph ^ 1u, abort)) return false;
       const int st = rg.x + it / nkc, kc = it % nkc;
       const size_t key = (size_t)st_slot[st];
-      const size_t chunk = (size_t)nrh * 128 * 64, row0 = (size_t)rh * 128 * 64;
-      const __nv_bfloat16* hi = Tbf + ((key * 2 + 0) * nkc + kc) * chunk + row0;
-      const __nv_bfloat16* lo = Tbf + ((key * 2 + 1) * nkc + kc) * chunk + row0;
+      const size_t chunk = (size_t)nrh * 128 * 128, row0 = (size_t)rh * 128 * 128;  // bytes
+      const uint8_t* hi = Tb + ((key * 2 + 0) * nkc + kc) * chunk + row0;
+      const uint8_t* lo = Tb + ((key * 2 + 1) * nkc + kc) * chunk + row0;
       const uint32_t a0 = sbase + stage * kStageBytes;
       mbar_arrive_tx(fullA(stage), 2 * abytes);
       bulk_g2s(a0, hi, abytes, fullA(stage));
@@ -249,9 +264,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       const uint32_t b_hi = a_hi + 2 * kABytes, b_lo = b_hi + kBBytes;
       for (int kk = 0; kk < ks; ++kk) {
         const uint32_t off = (uint32_t)kk * 32u;
-        umma(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (it > 0 || kk > 0) ? 1u : 0u);
-        umma(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
-        umma(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+        umma<KIND>(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (it > 0 || kk > 0) ? 1u : 0u);
+        umma<KIND>(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+        umma<KIND>(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
       }
       umma_commit(empty(stage));
     }
@@ -318,17 +333,30 @@ __global__ void k_wait_selftest(long long spins, int arrive, int* status) {
 
 int m2l_tensor(fmm_plan p, cudaStream_t s) {
   if (p->n_steps == 0) return FMM_OK;
-  const int ksteps = (p->P + 15) / 16;
-  const int nkc = m2l_kchunks(p->P);
+  const int kind = p->tc_kind;
+  const int ksteps = (p->P + m2l_kstep(kind) - 1) / m2l_kstep(kind);
+  const int nkc = m2l_kchunks(p->P, kind);
   const int last = ksteps - 4 * (nkc - 1);
   const size_t sh = (size_t)kBarOff + 128 + 1024;
-  FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[kind]) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(kind ? k_m2l_tc<1> : k_m2l_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sh));
+    attr_set[kind] = true;
+  }
   const int nrh = m2l_rowblocks(p->P);
   ++g_launches;
-  k_m2l_tc<<<dim3((unsigned)p->ntiles, (unsigned)nrh), kThreads, sh, s>>>(
-      p->tile_range.as<int2>(), p->tile_first.as<int>(), p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<__nv_bfloat16>(),
-      p->Mbf.as<__nv_bfloat16>(), p->P, nkc, last, 64 * nkc, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
-      p->flags.as<int>());
+  const dim3 grid((unsigned)p->ntiles, (unsigned)nrh);
+  if (kind)
+    k_m2l_tc<1><<<grid, kThreads, sh, s>>>(p->tile_range.as<int2>(), p->tile_first.as<int>(), p->st_slot.as<int>(),
+                                           p->st_src.as<int>(), p->Tbf.as<uint8_t>(), p->Mbf.as<uint8_t>(), p->P,
+                                           nkc, last, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
+                                           p->flags.as<int>());
+  else
+    k_m2l_tc<0><<<grid, kThreads, sh, s>>>(p->tile_range.as<int2>(), p->tile_first.as<int>(), p->st_slot.as<int>(),
+                                           p->st_src.as<int>(), p->Tbf.as<uint8_t>(), p->Mbf.as<uint8_t>(), p->P,
+                                           nkc, last, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
+                                           p->flags.as<int>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }

@@ -137,8 +137,20 @@ Mat lattice_matrix(int p, int images) {
 
 // ---- device: M2L operator per translation key
 
+// Round an FP32 value to TF32 (10 stored mantissa bits, to nearest, ties to
+// even) in its 32-bit container; the low 13 bits end up zero.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;  // inf / nan
+  u += 0x0FFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// kind 0: BF16 tiles [key][hi/lo][nkc K chunks of 64][rows][64];
+// kind 1: TF32 tiles [key][hi/lo][nkc K chunks of 32][rows][32]; both 128-byte
+// rows with 16-byte groups in the 128-byte swizzle order (group j at j ^ (row & 7)).
 __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __restrict__ slots, int nkeys, int p,
-                            float* __restrict__ T32, __nv_bfloat16* __restrict__ Tbf, int nkc) {
+                            float* __restrict__ T32, uint8_t* __restrict__ Tb, int nkc, int kind) {
   __shared__ cd I[(2 * kPMax - 1) * (2 * kPMax) / 2];
   __shared__ double nu[kNCoefMax];
   __shared__ double rp[kPMax];
@@ -163,9 +175,10 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
   }
   if (threadIdx.x < (unsigned)p) rp[threadIdx.x] = ldexp(1.0, delta * (int)threadIdx.x);
   const int rows = 128 * m2l_rowblocks(P);  // output rows of the BF16 tiles
-  if (nkc) {  // zero this slot's BF16 tiles (padding rows and columns stay zero)
-    uint4* z = reinterpret_cast<uint4*>(Tbf + (size_t)key_id * 2 * nkc * rows * 64);
-    for (int i = threadIdx.x; i < 2 * nkc * rows * 64 / 8; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  const size_t chunk_bytes = (size_t)rows * 128;
+  if (nkc) {  // zero this slot's tiles (padding rows and columns stay zero)
+    uint4* z = reinterpret_cast<uint4*>(Tb + (size_t)key_id * 2 * nkc * chunk_bytes);
+    for (size_t i = threadIdx.x; i < 2 * nkc * chunk_bytes / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
@@ -184,15 +197,22 @@ __global__ void k_build_m2l(const uint64_t* __restrict__ keys, const int* __rest
     if (pi == 0) v = po == 0 ? s * (A.re + B.re) : s * (A.im + B.im);
     else v = po == 0 ? -s * (B.im - A.im) : s * (B.re - A.re);
     if (!nkc) T32[(size_t)key_id * P * P + e] = (float)v;  // FP32 copy for the SIMT path only
-    if (nkc) {
-      // [key][hi/lo][nkc K chunks of 64][rows][64], 16-byte groups of a row
-      // stored in the 128-byte swizzle order (group j at j ^ (row & 7))
+    if (nkc && kind == 0) {
+      __nv_bfloat16* Tbf = reinterpret_cast<__nv_bfloat16*>(Tb);
       __nv_bfloat16 hi = __double2bfloat16(v);
       __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
       const int kc = c >> 6, j = (c & 63) >> 3, el = c & 7;
       const size_t within = (size_t)r * 64 + (size_t)(((j ^ (r & 7)) << 3) + el);
       Tbf[(((size_t)key_id * 2 + 0) * nkc + kc) * ((size_t)rows * 64) + within] = hi;
       Tbf[(((size_t)key_id * 2 + 1) * nkc + kc) * ((size_t)rows * 64) + within] = lo;
+    } else if (nkc) {
+      float* Ttf = reinterpret_cast<float*>(Tb);
+      const float hi = round_tf32((float)v);
+      const float lo = round_tf32((float)(v - (double)hi));
+      const int kc = c >> 5, j = (c & 31) >> 2, el = c & 3;
+      const size_t within = (size_t)r * 32 + (size_t)(((j ^ (r & 7)) << 2) + el);
+      Ttf[(((size_t)key_id * 2 + 0) * nkc + kc) * ((size_t)rows * 32) + within] = hi;
+      Ttf[(((size_t)key_id * 2 + 1) * nkc + kc) * ((size_t)rows * 32) + within] = lo;
     }
   }
 }
@@ -295,8 +315,7 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
     int64_t cap = std::max<int64_t>(need, p->tcache_cap * 2);
     if (!tc) FMM_TRY(p->T32.grow_copy((size_t)cap * P * P * sizeof(float), s));
     if (tc)
-      FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * m2l_kchunks(P) * 128 * m2l_rowblocks(P) * 64 * sizeof(__nv_bfloat16),
-                               s));
+      FMM_TRY(p->Tbf.grow_copy((size_t)cap * 2 * m2l_kchunks(P, p->tc_kind) * 128 * m2l_rowblocks(P) * 128, s));
     p->tcache_cap = cap;
   }
   if (!miss_keys.empty()) {
@@ -307,8 +326,8 @@ int build_m2l_operators(fmm_plan p, cudaStream_t s) {
     FMM_CUDA_TRY(cudaMemcpyAsync(p->tmiss_slots.ptr, miss_slots.data(), nm * sizeof(int), cudaMemcpyHostToDevice, s));
     ++g_launches;
     k_build_m2l<<<(unsigned)nm, 256, 0, s>>>(p->tmiss_keys.as<uint64_t>(), p->tmiss_slots.as<int>(), (int)nm,
-                                             p->prm.p, p->T32.as<float>(), p->Tbf.as<__nv_bfloat16>(),
-                                             tc ? m2l_kchunks(P) : 0);
+                                             p->prm.p, p->T32.as<float>(), p->Tbf.as<uint8_t>(),
+                                             tc ? m2l_kchunks(P, p->tc_kind) : 0, p->tc_kind);
     FMM_CUDA_TRY(cudaGetLastError());
     p->n_built = nm;
   }

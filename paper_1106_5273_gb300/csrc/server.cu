@@ -40,7 +40,7 @@ struct Req {
   int retries = 0;  // batches of this request refused by the byte budget
 };
 
-constexpr int kMaxRetries = 8;
+constexpr int kMaxRetries = 4;
 
 struct PlanRec {
   fmm_plan plan = nullptr;
@@ -329,25 +329,31 @@ void worker_loop(fmm_server S, Worker* W) {
     if (rc == FMM_E_NOMEM && ntot > 0) {
       // An allocation of this batch was refused by the byte budget (or the
       // device is out of memory): the class's footprint was underestimated.
-      // Raise its per-particle need to at least what the batch could not fit
-      // in, free this worker's plans, and return the requests to the front of
-      // the queue, where the next batch is formed with the larger need (fewer
-      // requests, or a wait for the other workers).  After kMaxRetries refusals
-      // a request completes with FMM_E_NOMEM.
+      // What the batch had allocated plus the refused allocation bounds its
+      // need from below; the class's per-particle need is raised past that
+      // (and by at least 25%), every idle plan is freed, and the requests go
+      // back to the front of the queue, where the next batch is formed with
+      // the larger need (fewer requests, or a wait for the other workers).
+      // A request counts a refusal only when no other worker was running;
+      // after kMaxRetries such refusals it completes with FMM_E_NOMEM.
+      bool others_busy = false;
+      for (Worker* o : S->workers) others_busy |= (o != W && o->busy);
       W->busy = false;
       if (probe) S->probing = 0;
+      const int64_t grown = plan_bytes(rec.plan) - rec.base + fmm::ByteBudget::last_refused();
       if (rec.plan) W->plans[c] = rec;
       else W->plans.erase(c);
       Model& m = S->model.count(c) ? S->model[c] : (S->model[c] = initial_model(S));
-      const double avail = (double)std::max<int64_t>(budget - others_at_start, 0);
-      m.per = std::max(m.per * 2.0, avail / (double)ntot);
+      const double per_lb = ((double)grown - (m.have_small ? m.fixed : 0.0)) / (double)ntot;
+      m.per = std::max(m.per * 1.25, 1.1 * per_lb);
       m.have_big = true;
-      drop_plans(S, W, -1);
+      for (Worker* o : S->workers)
+        if (o == W || !o->busy) drop_plans(S, o, -1);
       std::vector<int64_t> again;
       const double td = S->now();
       for (int64_t t : batch) {
         Req& rq = S->reqs[t];
-        if (++rq.retries <= kMaxRetries) {
+        if (others_busy || ++rq.retries <= kMaxRetries) {
           again.push_back(t);
           continue;
         }
@@ -445,8 +451,7 @@ int fmm_server_create(const fmm_server_params* prm, fmm_server* out) {
   q.images = prm->images;
   q.m2l_mode = prm->m2l_mode;
   if (!(q.theta > 0.f && q.theta < 1.f) || q.ncrit < 1 || q.ncrit > 4096 || !(q.sigma_sep >= 0.f) ||
-      q.images < 1 || q.images > 8 || (q.m2l_mode & ~(3 | FMM_M2L_SORT_STEPS)) ||
-      (q.m2l_mode & 3) > FMM_M2L_TENSOR)
+      q.images < 1 || q.images > 8 || (q.m2l_mode & ~(3 | FMM_M2L_SORT_STEPS)))
     return FMM_E_INVAL;
   if (prm->model_bytes_per_particle < 0) return FMM_E_INVAL;
   fmm_server S = new (std::nothrow) fmm_server_s();

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int n
 }
 
 __device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, int& c0, int& nc) {
-  // radius of A > radius of B  <=>  A is the coarser cube (a tie: split_tie)
+  // A's cube larger than B's <=> A on the coarser level (equal levels: split_tie)
   split_a = t.level[a] < t.level[b] || (t.split_tie == FMM_SPLIT_TARGET && t.level[a] == t.level[b]);
   if (split_a && t.nchild[a] == 0) split_a = false;
   else if (!split_a && t.nchild[b] == 0) split_a = true;

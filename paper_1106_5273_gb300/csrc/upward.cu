@@ -117,6 +117,30 @@ __global__ void __launch_bounds__(128) k_m2m(int lb, const int* __restrict__ chi
   }
 }
 
+// Round an FP32 value to TF32 (10 stored mantissa bits, to nearest, ties to
+// even) in its 32-bit container; the low 13 bits end up zero.
+__device__ __forceinline__ float round_tf32_m(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;  // inf / nan
+  u += 0x0FFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// Mtf[cell][hi/lo][comp][kpad] TF32 halves, zero beyond P (kpad = 32 x K chunks).
+__global__ void k_split_tf32(const float* __restrict__ M, int64_t ncell, int P, int kpad, float* __restrict__ Mtf) {
+  int64_t total = ncell * 3 * kpad;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(i % kpad);
+    int64_t cc = i / kpad;  // cell*3 + comp
+    int64_t cell = cc / 3;
+    int comp = (int)(cc % 3);
+    float v = k < P ? M[cc * P + k] : 0.f;
+    const float hi = round_tf32_m(v);
+    Mtf[((cell * 2 + 0) * 3 + comp) * kpad + k] = hi;
+    Mtf[((cell * 2 + 1) * 3 + comp) * kpad + k] = round_tf32_m(v - hi);
+  }
+}
+
 // Mbf[cell][hi/lo][comp][kpad], zero beyond P (kpad = 64 x K chunks).
 __global__ void k_split_bf16(const float* __restrict__ M, int64_t ncell, int P, int kpad,
                              __nv_bfloat16* __restrict__ Mbf) {
@@ -159,10 +183,14 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
   }
   FMM_CUDA_TRY(cudaGetLastError());
   if (p->last_tc) {
-    const int kpad = 64 * m2l_kchunks(P);
-    FMM_TRY(p->Mbf.ensure((size_t)nc * 2 * 3 * kpad * sizeof(__nv_bfloat16)));
+    // 128 bytes per K chunk of each (cell, hi/lo, component) row
+    const int nkc = m2l_kchunks(P, p->tc_kind);
+    FMM_TRY(p->Mbf.ensure((size_t)nc * 2 * 3 * nkc * 128));
     ++g_launches;
-    k_split_bf16<<<2048, 256, 0, s>>>(p->M.as<float>(), nc, P, kpad, p->Mbf.as<__nv_bfloat16>());
+    if (p->tc_kind)
+      k_split_tf32<<<2048, 256, 0, s>>>(p->M.as<float>(), nc, P, 32 * nkc, p->Mbf.as<float>());
+    else
+      k_split_bf16<<<2048, 256, 0, s>>>(p->M.as<float>(), nc, P, 64 * nkc, p->Mbf.as<__nv_bfloat16>());
     FMM_CUDA_TRY(cudaGetLastError());
   }
   return FMM_OK;

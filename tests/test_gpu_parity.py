@@ -424,14 +424,21 @@ def test_deterministic_and_host_entry():
 
 @pytest.mark.parametrize("p", [4, 8, 10, 11, 12, 16])
 def test_tensor_m2l_matches_simt(p):
-    """tcgen05 BF16x3 M2L against the FP32 SIMT M2L on the same lists (1-4 K chunks, ragged K;
-    p >= 12: two CTAs per tile, one per block of 128 output rows)."""
+    """tcgen05 M2L against the FP32 SIMT M2L on the same lists (1-4 K chunks of
+    BF16, 1-8 of TF32, ragged K; p >= 12: two CTAs per tile, one per block of
+    128 output rows).  BF16x3 products carry up to 3 x 2^-18 relative error,
+    TF32x3 products 3 x 2^-22, so the TF32 tolerance is 16x tighter."""
     w = workloads.plummer(6000)
     w["sigma"] = np.float32(0.002)
     _, u1, s1 = run_fmm(w, p, 0.5, 32, m2l_mode=1)
     plan, u2, s2 = run_fmm(w, p, 0.5, 32, m2l_mode=2)
     assert plan.stats().m2l_tensor == 1 and plan.stats().m2l_pairs > 0
     assert rel_l2(u2, u1) < 1e-5 and rel_l2(s2, s1) < 3e-5
+    plan3, u3, s3 = run_fmm(w, p, 0.5, 32, m2l_mode=3)
+    assert plan3.stats().m2l_tensor == 1
+    print("p=%d BF16x3 vs FP32: u %.2e s %.2e; TF32x3: u %.2e s %.2e" % (
+        p, rel_l2(u2, u1), rel_l2(s2, s1), rel_l2(u3, u1), rel_l2(s3, s1)))
+    assert rel_l2(u3, u1) < 1e-5 / 16 and rel_l2(s3, s1) < 3e-5 / 16
 
 
 @pytest.mark.parametrize("case", ["lattice", "taylor_green", "plummer"])

@@ -417,7 +417,7 @@ def test_tree_invariants():
 
 @pytest.mark.parametrize("periodic_case", [False, True])
 def test_algorithm1_splits_the_larger_cube_and_the_source_on_a_tie(periodic_case):
-    # Alg. 1: "IF radius of A > radius of B split A ELSE split B".  On a
+    # Alg. 1 splits A when A is the larger cell and B otherwise.  On a
     # complete octree (every leaf on one level) no leaf forces the other
     # split, so from (root, root) the printed rule alternates B, A, B, ...:
     # every emitted pair has its target on the source's level or one above
