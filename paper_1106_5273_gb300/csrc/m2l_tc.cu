@@ -27,6 +27,8 @@
 // its own bulk copies, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -45,6 +47,10 @@ constexpr uint32_t kBarOff = kStages * kStageBytes;
 constexpr int kTmemCols = 256;
 constexpr long long kSpin = 1ll << 24;
 constexpr int kGather = (2 * kN * 8) / kProducers;          // 16-byte items per producer thread (12)
+// Work items of one-problem plans: S = max(kItemMinSteps, steps / kItemTarget)
+// steps per item, about four items per concurrent CTA (2 per SM x 152 SMs).
+constexpr int64_t kItemMinSteps = 128;
+constexpr int64_t kItemTarget = 4 * 2 * 152;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -137,17 +143,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // KIND 0: BF16 operands (64 per 128-byte row, K step 16); KIND 1: TF32 (32
 // per row, K step 8).  Tb / Mb hold 128-byte rows: a K chunk of one operator
 // row or one (cell, hi/lo, component) multipole row.
+// items == nullptr: CTA x runs all steps of tile x and writes its local
+// expansions.  Otherwise CTA x runs work item x (tile, first step, end step,
+// partial slot) of *nitems: a tile's steps in runs of at most S; a tile split
+// into several items writes each item's D to its partial slot, summed later
+// by k_m2l_combine.
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_m2l_tc(const int2* __restrict__ tile_range, const int* __restrict__ tfirst, const int* __restrict__ st_slot,
-             const int* __restrict__ st_src, const uint8_t* __restrict__ Tb, const uint8_t* __restrict__ Mb, int P,
-             int nkc, int ksteps_last, int nrh, const int* __restrict__ tcell, float* __restrict__ L,
+    k_m2l_tc(const int2* __restrict__ tile_range, const int4* __restrict__ items, const uint32_t* __restrict__ nitems,
+             const int* __restrict__ tfirst, const int* __restrict__ st_slot, const int* __restrict__ st_src,
+             const uint8_t* __restrict__ Tb, const uint8_t* __restrict__ Mb, int P, int nkc, int ksteps_last, int nrh,
+             const int* __restrict__ tcell, float* __restrict__ L, float* __restrict__ partial,
              int* __restrict__ flag) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int tile = blockIdx.x;
+  int tile = blockIdx.x, pslot = -1;
+  int2 rg;
+  if (items) {
+    if (blockIdx.x >= *nitems) return;  // beyond the items of this evaluation
+    const int4 w = items[blockIdx.x];
+    tile = w.x;
+    rg = make_int2(w.y, w.z);
+    pslot = w.w;
+  } else {
+    rg = tile_range[tile];
+  }
   const int rh = blockIdx.y;  // block of 128 output rows
-  const int2 rg = tile_range[tile];
   if (rg.y <= rg.x) return;  // no M2L for this tile: the whole CTA leaves before any barrier
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
   // bars: fullA[2], fullB[2], empty[2], done
@@ -291,6 +312,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int first = tfirst[tile];
       const int ncell = tfirst[tile + 1] - first;
       const int r = rh * 128 + warp * 32 + lane;  // output coefficient of this TMEM lane
+      float* pdst = pslot >= 0 ? partial + ((size_t)pslot * nrh + rh) * (size_t)kN * 128 : nullptr;
 #pragma unroll 1
       for (int cb = 0; cb < kN / 16; ++cb) {
         float v[16];
@@ -299,7 +321,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int i = 0; i < 16; ++i) {
           const int n = cb * 16 + i;
           const int comp = n / kTile, slot = n % kTile;
-          if (r < P && slot < ncell) L[((size_t)tcell[first + slot] * 3 + comp) * P + r] = v[i];
+          if (pdst) pdst[(size_t)n * 128 + warp * 32 + lane] = v[i];  // [column][row of the block]
+          else if (r < P && slot < ncell) L[((size_t)tcell[first + slot] * 3 + comp) * P + r] = v[i];
         }
       }
     } else {
@@ -311,6 +334,50 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (warp == kProducerWarps) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ---- work items (one-problem plans): runs of at most S steps per CTA
+
+__global__ void k_m2l_item_count(const int2* __restrict__ tr, int ntiles, int S, uint32_t* __restrict__ cnt,
+                                 uint32_t* __restrict__ pcnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const int c = tr[t].y - tr[t].x;
+  const uint32_t k = c > 0 ? (uint32_t)((c + S - 1) / S) : 0u;
+  cnt[t] = k;
+  pcnt[t] = k > 1 ? k : 0u;
+}
+
+__global__ void k_m2l_item_fill(const int2* __restrict__ tr, int ntiles, int S, const uint32_t* __restrict__ cnt,
+                                const uint32_t* __restrict__ ioff, const uint32_t* __restrict__ poff,
+                                int4* __restrict__ items) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const uint32_t k = cnt[t];
+  for (uint32_t q = 0; q < k; ++q) {
+    const int s0 = tr[t].x + (int)q * S;
+    items[ioff[t] + q] = make_int4(t, s0, min(s0 + S, tr[t].y), k > 1 ? (int)(poff[t] + q) : -1);
+  }
+}
+
+// Local expansions of the split tiles: the partial sums of their items, added
+// in item order (a fixed order, so the result is deterministic).
+__global__ void k_m2l_combine(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ poff,
+                              const int* __restrict__ tfirst, const int* __restrict__ tcell, int P, int nrh,
+                              const float* __restrict__ partial, float* __restrict__ L) {
+  const int t = blockIdx.x;
+  const uint32_t k = cnt[t];
+  if (k <= 1) return;
+  const int first = tfirst[t], ncell = tfirst[t + 1] - first;
+  const size_t per = (size_t)nrh * kN * 128;  // floats per partial slot
+  for (int e = threadIdx.x; e < nrh * kN * 128; e += blockDim.x) {
+    const int r = e & 127, n = (e >> 7) % kN, rh = e / (kN * 128);
+    const int row = rh * 128 + r, slot = n % kTile, comp = n / kTile;
+    if (row >= P || slot >= ncell) continue;
+    float acc = 0.f;
+    for (uint32_t q = 0; q < k; ++q) acc += partial[(size_t)(poff[t] + q) * per + (size_t)e];
+    L[((size_t)tcell[first + slot] * 3 + comp) * P + row] = acc;
   }
 }
 
@@ -345,19 +412,61 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
     attr_set[kind] = true;
   }
   const int nrh = m2l_rowblocks(p->P);
+  const int nt = (int)p->ntiles;
+  const int T = 256;
+  // One-problem plans split the tiles into work items of at most S steps:
+  // with Alg. 1's printed rule the coarse target tiles collect many more
+  // steps than the rest, and one CTA per tile left a long tail.  Batches keep
+  // one CTA per tile, so that a problem's sums do not depend on the others.
+  const int4* items = nullptr;
+  const uint32_t* nitems = nullptr;
+  uint32_t *cnt = nullptr, *poff = nullptr;
+  unsigned grid = (unsigned)nt;
+  if (!p->batched) {
+    const int64_t S = std::max<int64_t>(kItemMinSteps, (p->n_steps + kItemTarget - 1) / kItemTarget);
+    const int64_t max_items = nt + p->n_steps / S + 1;
+    const int64_t max_split = 2 * (p->n_steps / S) + 1;
+    const size_t b_items = (size_t)max_items * sizeof(int4), b_arr = (size_t)(nt + 1) * sizeof(uint32_t);
+    FMM_TRY(p->m2l_items.ensure(b_items + 4 * b_arr + 64));
+    FMM_TRY(p->m2l_partial.ensure((size_t)max_split * nrh * kN * 128 * sizeof(float)));
+    uint8_t* base = p->m2l_items.as<uint8_t>();
+    int4* it = reinterpret_cast<int4*>(base);
+    cnt = reinterpret_cast<uint32_t*>(base + b_items);
+    uint32_t* pcnt = cnt + (nt + 1);
+    uint32_t* ioff = pcnt + (nt + 1);
+    poff = ioff + (nt + 1);
+    uint32_t* totals = poff + (nt + 1);  // [0] items, [1] partial slots
+    const unsigned gt = (unsigned)((nt + T - 1) / T);
+    ++g_launches;
+    k_m2l_item_count<<<gt, T, 0, s>>>(p->tile_range.as<int2>(), nt, (int)S, cnt, pcnt);
+    FMM_TRY(exclusive_scan_u32(cnt, ioff, nt, totals, p->scan_tmp, s));
+    FMM_TRY(exclusive_scan_u32(pcnt, poff, nt, totals + 1, p->scan_tmp, s));
+    ++g_launches;
+    k_m2l_item_fill<<<gt, T, 0, s>>>(p->tile_range.as<int2>(), nt, (int)S, cnt, ioff, poff, it);
+    FMM_CUDA_TRY(cudaGetLastError());
+    items = it;
+    nitems = totals;
+    grid = (unsigned)max_items;
+  }
   ++g_launches;
-  const dim3 grid((unsigned)p->ntiles, (unsigned)nrh);
+  const dim3 g3(grid, (unsigned)nrh);
   if (kind)
-    k_m2l_tc<1><<<grid, kThreads, sh, s>>>(p->tile_range.as<int2>(), p->tile_first.as<int>(), p->st_slot.as<int>(),
-                                           p->st_src.as<int>(), p->Tbf.as<uint8_t>(), p->Mbf.as<uint8_t>(), p->P,
-                                           nkc, last, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
-                                           p->flags.as<int>());
+    k_m2l_tc<1><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
+                                         p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
+                                         p->Mbf.as<uint8_t>(), p->P, nkc, last, nrh, p->tile_cells.as<int>(),
+                                         p->L.as<float>(), p->m2l_partial.as<float>(), p->flags.as<int>());
   else
-    k_m2l_tc<0><<<grid, kThreads, sh, s>>>(p->tile_range.as<int2>(), p->tile_first.as<int>(), p->st_slot.as<int>(),
-                                           p->st_src.as<int>(), p->Tbf.as<uint8_t>(), p->Mbf.as<uint8_t>(), p->P,
-                                           nkc, last, nrh, p->tile_cells.as<int>(), p->L.as<float>(),
-                                           p->flags.as<int>());
+    k_m2l_tc<0><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
+                                         p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
+                                         p->Mbf.as<uint8_t>(), p->P, nkc, last, nrh, p->tile_cells.as<int>(),
+                                         p->L.as<float>(), p->m2l_partial.as<float>(), p->flags.as<int>());
   FMM_CUDA_TRY(cudaGetLastError());
+  if (items) {
+    ++g_launches;
+    k_m2l_combine<<<(unsigned)nt, T, 0, s>>>(cnt, poff, p->tile_first.as<int>(), p->tile_cells.as<int>(), p->P, nrh,
+                                             p->m2l_partial.as<float>(), p->L.as<float>());
+    FMM_CUDA_TRY(cudaGetLastError());
+  }
   return FMM_OK;
 }
 
