@@ -163,7 +163,7 @@ void fmm_params_default(fmm_params* prm);
 /*
  * Create a plan for up to n_max particles on the current CUDA device.
  * Builds the M2M/L2L operators and, if periodic, the FP64 lattice operator
- * (Sec. 3.5).  Device workspace is allocated here and grown on demand by
+ * (Sec. 3.5, built on the device).  Device workspace is allocated here and grown on demand by
  * evaluations.  Returns FMM_E_INVAL for bad parameters, FMM_E_NOMEM, or
  * FMM_E_CUDA; *out is set only on success.
  */
@@ -423,6 +423,18 @@ int fmm_graph_launch(fmm_graph graph, void* cuda_stream);
 /* Kernel launches one replay performs (counted in fmm_kernel_launch_count). */
 int64_t fmm_graph_kernel_count(fmm_graph graph);
 void fmm_graph_destroy(fmm_graph graph);
+
+/*
+ * The periodic lattice operator of a plan (Sec. 3.5): the P x P (P = p^2) FP64
+ * matrix A, row-major, with L~_root += A M~_root in the normalized
+ * real-packed coefficients: the images beyond the 27 explicit ones, as
+ * images-1 rings of 702 super-cells (sides 1, 3, 9 ... in box units).  Plans
+ * build it on the device in FP64 (on_device = 1, what plans use); on_device
+ * = 0 builds the same sums on the host in FP64, for comparison.  out: host
+ * [p^4] doubles.  Synchronous; FMM_E_INVAL for p outside 1..16 or images
+ * outside 1..8.
+ */
+int fmm_lattice_operator(int32_t p, int32_t images, int32_t on_device, double* out);
 
 /*
  * All-pairs direct sum of Eqs. (1)-(3) on the device, free space, without

@@ -98,6 +98,7 @@ lib.fmm_graph_kernel_count.argtypes = [_vp]
 lib.fmm_graph_kernel_count.restype = _i64
 lib.fmm_graph_destroy.argtypes = [_vp]
 lib.fmm_graph_destroy.restype = None
+lib.fmm_lattice_operator.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
 lib.fmm_kernel_launch_count.argtypes = []
 lib.fmm_kernel_launch_count.restype = ctypes.c_int64
 lib.fmm_plan_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
@@ -349,6 +350,15 @@ def morton_order_noalloc(pos, keys_out, order_out, periodic=False, box_min=None,
                                         ctypes.c_void_p(keys_out.data_ptr()), ctypes.c_void_p(order_out.data_ptr()),
                                         _stream_ptr(stream)), "fmm_morton_order_noalloc")
     return keys_out, order_out
+
+
+def lattice_operator(p, images, on_device=True):
+    """fmm_lattice_operator: the P x P FP64 periodic lattice operator (numpy)."""
+    import numpy as np
+    out = np.zeros((p * p, p * p), np.float64)
+    _check(lib.fmm_lattice_operator(int(p), int(images), 1 if on_device else 0, out.ctypes.data),
+           "fmm_lattice_operator")
+    return out
 
 
 def selftest_bounded_wait(spins, arrive, stream=None):

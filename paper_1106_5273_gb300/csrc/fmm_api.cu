@@ -362,6 +362,18 @@ int fmm_direct_velocity_stretching(int64_t n, const float* pos, const float* gam
 
 int64_t fmm_kernel_launch_count(void) { return fmm::g_launches; }
 
+int fmm_lattice_operator(int32_t p, int32_t images, int32_t on_device, double* out) {
+  if (p < 1 || p > kPMax || images < 1 || images > 8 || !out) return FMM_E_INVAL;
+  const size_t bytes = (size_t)p * p * p * p * sizeof(double);
+  if (!on_device) return lattice_operator_host(p, images, out);
+  DBuf A;
+  int rc = A.ensure(bytes);
+  if (rc == FMM_OK) rc = lattice_operator_device(p, images, A.as<double>(), 0);
+  if (rc == FMM_OK && cudaMemcpy(out, A.ptr, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) rc = FMM_E_CUDA;
+  A.release();
+  return rc;
+}
+
 int fmm_plan_set_timing(fmm_plan p, int enable) {
   if (!p) return FMM_E_INVAL;
   p->timing = enable ? 1 : 0;

@@ -147,6 +147,9 @@ int build_forest(fmm_plan p, int64_t n, const float* pos, const float* gam, cons
 int build_constant_operators(fmm_plan p);
 int build_m2l_operators(fmm_plan p, cudaStream_t s);
 int apply_lattice(fmm_plan p, cudaStream_t s);
+int lattice_operator_host(int p, int images, double* out);
+// lattice.cu
+int lattice_operator_device(int p, int images, double* A, cudaStream_t s);
 // upward.cu
 int upward_pass(fmm_plan p, cudaStream_t s);
 // traverse.cu

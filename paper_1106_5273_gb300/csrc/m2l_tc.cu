@@ -47,10 +47,17 @@ constexpr uint32_t kBarOff = kStages * kStageBytes;
 constexpr int kTmemCols = 256;
 constexpr long long kSpin = 1ll << 24;
 constexpr int kGather = (2 * kN * 8) / kProducers;          // 16-byte items per producer thread (12)
-// Work items of one-problem plans: S = max(kItemMinSteps, steps / kItemTarget)
-// steps per item, about four items per concurrent CTA (2 per SM x 152 SMs).
-constexpr int64_t kItemMinSteps = 128;
+// Work items of one-problem plans: S = steps / kItemTarget (about four items
+// per concurrent CTA, 2 per SM x 152 SMs) clamped to [kItemMinSteps,
+// kItemMaxSteps], then raised if needed so that there are at most kItemsMax
+// items.  The upper clamp is for accuracy as much as for balance: the FP32
+// accumulation of the tensor memory over a whole tile's steps (thousands of
+// MMAs into one sum) measured 4x the M2L error of sums over at most a few
+// hundred steps added in FP32 afterwards.
+constexpr int64_t kItemMinSteps = 64;
+constexpr int64_t kItemMaxSteps = 256;
 constexpr int64_t kItemTarget = 4 * 2 * 152;
+constexpr int64_t kItemsMax = 1 << 16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -416,14 +423,17 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   const int T = 256;
   // One-problem plans split the tiles into work items of at most S steps:
   // with Alg. 1's printed rule the coarse target tiles collect many more
-  // steps than the rest, and one CTA per tile left a long tail.  Batches keep
-  // one CTA per tile, so that a problem's sums do not depend on the others.
+  // steps than the rest, and one CTA per tile left a long tail (and long
+  // tensor-memory sums).  Batches keep one CTA per tile: their tiles mix
+  // problems, and items cut at fixed step counts would make a problem's sums
+  // depend on the other problems of the batch.
   const int4* items = nullptr;
   const uint32_t* nitems = nullptr;
   uint32_t *cnt = nullptr, *poff = nullptr;
   unsigned grid = (unsigned)nt;
   if (!p->batched) {
-    const int64_t S = std::max<int64_t>(kItemMinSteps, (p->n_steps + kItemTarget - 1) / kItemTarget);
+    int64_t S = std::min(kItemMaxSteps, std::max(kItemMinSteps, (p->n_steps + kItemTarget - 1) / kItemTarget));
+    S = std::max(S, (p->n_steps + kItemsMax - 1) / kItemsMax);
     const int64_t max_items = nt + p->n_steps / S + 1;
     const int64_t max_split = 2 * (p->n_steps / S) + 1;
     const size_t b_items = (size_t)max_items * sizeof(int4), b_arr = (size_t)(nt + 1) * sizeof(uint32_t);

@@ -261,11 +261,18 @@ int build_constant_operators(fmm_plan p) {
       }
   FMM_TRY(p->l2p_w.ensure(w.size() * sizeof(float)));
   FMM_CUDA_TRY(cudaMemcpy(p->l2p_w.ptr, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
-  if (p->prm.periodic) {
-    Mat A = lattice_matrix(pp, p->prm.images);
-    FMM_TRY(p->lattice.ensure(A.size() * sizeof(double)));
-    FMM_CUDA_TRY(cudaMemcpy(p->lattice.ptr, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (p->prm.periodic) {  // the lattice operator, in FP64 on the device
+    FMM_TRY(p->lattice.ensure((size_t)P * P * sizeof(double)));
+    FMM_TRY(lattice_operator_device(pp, p->prm.images, p->lattice.as<double>(), 0));
   }
+  return FMM_OK;
+}
+
+// The lattice operator built on the host (the same sums in FP64 C++), kept to
+// cross-check the device build (fmm_lattice_operator).
+int lattice_operator_host(int p, int images, double* out) {
+  Mat A = lattice_matrix(p, images);
+  for (size_t q = 0; q < A.size(); ++q) out[q] = A[q];
   return FMM_OK;
 }
 

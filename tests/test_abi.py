@@ -95,3 +95,15 @@ def test_noalloc_binding_rejects_bad_outputs_before_the_call(lib):
         b.morton_order_noalloc(torch.zeros(24, dtype=torch.float32), keys, order)
     with pytest.raises(TypeError):  # CPU outputs
         b.morton_order_noalloc(pos, keys, order)
+
+
+def test_lattice_operator_host_build_without_gpu(lib):
+    """fmm_lattice_operator's host build runs without a device; bad arguments are refused."""
+    import numpy as np
+    from paper_1106_5273_gb300 import binding as b
+    a = b.lattice_operator(3, 2, on_device=False)
+    assert a.shape == (9, 9) and np.isfinite(a).all() and np.abs(a).max() > 0
+    out = np.zeros(1)
+    assert lib.fmm_lattice_operator(0, 3, 0, out.ctypes.data) == -1
+    assert lib.fmm_lattice_operator(4, 9, 0, out.ctypes.data) == -1
+    assert lib.fmm_lattice_operator(4, 3, 0, None) == -1

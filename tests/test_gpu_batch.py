@@ -12,6 +12,14 @@ from gpu_common import rel_l2, to_dev
 
 pytestmark = pytest.mark.gpu
 
+# The one-problem entry point against the same problem in a batch on the tensor
+# cores: the same lists and products, but the one-problem M2L sums each tile in
+# work items of at most 256 steps (partial sums added in FP32 afterwards) and
+# the batch each tile in one FP32 tensor-memory accumulation; the long
+# accumulation carries an error of up to ~2e-5 (measured 1.4e-6 free space,
+# 1.1e-5 periodic, 2.0e-5 through the serving loop).
+PLAIN_VS_BATCH = 5e-5
+
 
 def _concat(probs, per_particle_sigma=False):
     off = np.zeros(len(probs) + 1, np.int64)
@@ -68,13 +76,16 @@ def test_batch_free_space_matches_direct_alone_and_plain(m2l_mode):
         # alone: the same problem as a batch of one gives the same bits
         ua, sa = _run_batch(plan, np.array([0, n]), w["pos"], w["gamma"], sig[k:k + 1])
         assert np.array_equal(ua, u[a:b]) and np.array_equal(sa, s[a:b]), k
-    # the one-problem entry point on the largest problem (21-bit keys there)
+    # the one-problem entry point on the largest problem (21-bit keys there;
+    # on the tensor cores its M2L sums each tile in runs of at most 256 steps,
+    # the batch each tile in one tensor-memory sum: FP32 accumulation order)
     k = int(np.argmax(np.diff(off)))
     w = probs[k]
     one = Plan(w["pos"].shape[0], prm)
     up, sp_ = one.eval(to_dev(w["pos"]), to_dev(w["gamma"]), sigma_uniform=float(w["sigma"]))
-    assert rel_l2(u[off[k]:off[k + 1]], up.cpu().numpy()) < 1e-6
-    assert rel_l2(s[off[k]:off[k + 1]], sp_.cpu().numpy()) < 1e-6
+    tol = 1e-6 if m2l_mode == 1 else PLAIN_VS_BATCH
+    assert rel_l2(u[off[k]:off[k + 1]], up.cpu().numpy()) < tol
+    assert rel_l2(s[off[k]:off[k + 1]], sp_.cpu().numpy()) < tol
 
 
 def test_batch_order_of_problems_does_not_matter():
@@ -126,7 +137,7 @@ def test_batch_periodic_cubes_match_fourier_and_plain():
     # against the one-problem entry point with the same cube
     one = Plan(600, Params.default(p=P_, theta=TH, ncrit=NC, periodic=1, box_min=np.ones(3), box_len=1.0, images=3))
     up, sp_ = one.eval(to_dev(cloud["pos"]), to_dev(g), sigma_uniform=0.07)
-    assert rel_l2(u[off[1]:off[2]], up.cpu().numpy()) < 1e-5
+    assert rel_l2(u[off[1]:off[2]], up.cpu().numpy()) < PLAIN_VS_BATCH
     # alone
     ua, sa = _run_batch(plan, np.array([0, 600]), cloud["pos"], g, sig[1:2], boxes=boxes[1:2])
     assert np.array_equal(ua, u[off[1]:off[2]]) and np.array_equal(sa, s[off[1]:off[2]])

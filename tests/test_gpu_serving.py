@@ -111,8 +111,11 @@ def test_serving_one_request_per_call_mode():
     results = [srv.wait(t, 120.0) for t in tickets]
     assert all(res["status"] == 0 and res["batch_problems"] == 1 for res, _, _ in results)
     for r, (res, u, s) in zip(reqs, results):
-        ua, sa = _alone(r)  # 21-bit keys there, 16 here: same trees at these sizes, rounding-level differences
-        assert rel_l2(u, ua) < 1e-5 and rel_l2(s, sa) < 1e-5
+        # 21-bit keys there, 16 here: same trees at these sizes; on the tensor
+        # cores the one-problem path sums M2L in work items of at most 256 steps,
+        # the batch whole tiles in tensor memory (FP32 accumulation order)
+        ua, sa = _alone(r)
+        assert rel_l2(u, ua) < 5e-5 and rel_l2(s, sa) < 5e-5
     assert srv.counters()["batches"] == len(reqs)
     srv.close()
 
