@@ -742,6 +742,16 @@ def main():
         except Exception:
             traffic = None
     roof = p2p_roofline(st, sum(p2p_ms) / len(p2p_ms), traffic)
+    if rank == 0:
+        from paper_1106_5273_gb300 import binding as _b
+        pclk = ClockSampler(local)
+        pclk.start()
+        probe_tf, probe_ms = _b.probe_fp32_rate(1000)
+        pc = pclk.stop()
+        roof["peak_probe"] = {"value": probe_tf, "unit": "TFLOP/s", "frac": roof["achieved"] / probe_tf,
+                              "ms_per_launch": probe_ms, "clocks": pc,
+                              "what": "fmm_probe_fp32_rate: independent FFMA2 chains, 8 CTAs x 256 threads per SM, "
+                                      "1000 launches timed with CUDA events"}
     roof_m2l = m2l_roofline(st, w["p"])
     reuse = None
     if rank == 0 and not args.no_reuse:

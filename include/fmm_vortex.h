@@ -437,6 +437,16 @@ void fmm_graph_destroy(fmm_graph graph);
 int fmm_lattice_operator(int32_t p, int32_t images, int32_t on_device, double* out);
 
 /*
+ * Measurement aid (no counterpart in the paper): the FP32 rate the device
+ * sustains on independent packed FMA chains (FFMA2), in TFLOP/s (FMA = 2
+ * flops), timed with CUDA events over `launches` launches (1..1000) of a
+ * kernel with 8 CTAs of 256 threads per SM.  Synchronous.  It is the
+ * practical ceiling beside the derived peak (FP32 lanes x clock) that the
+ * P2P roofline fraction is quoted against.
+ */
+int fmm_probe_fp32_rate(int32_t launches, double* tflops, double* ms_per_launch, void* cuda_stream);
+
+/*
  * All-pairs direct sum of Eqs. (1)-(3) on the device, free space, without
  * a tree: the same P2P pair kernel over every (target, source) pair of one
  * array (the self pair excluded).  Device arrays as above.  O(n^2).

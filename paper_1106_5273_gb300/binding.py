@@ -99,6 +99,8 @@ lib.fmm_graph_kernel_count.restype = _i64
 lib.fmm_graph_destroy.argtypes = [_vp]
 lib.fmm_graph_destroy.restype = None
 lib.fmm_lattice_operator.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
+lib.fmm_probe_fp32_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     _vp]
 lib.fmm_kernel_launch_count.argtypes = []
 lib.fmm_kernel_launch_count.restype = ctypes.c_int64
 lib.fmm_plan_get_stats.argtypes = [_vp, ctypes.POINTER(Stats)]
@@ -359,6 +361,15 @@ def lattice_operator(p, images, on_device=True):
     _check(lib.fmm_lattice_operator(int(p), int(images), 1 if on_device else 0, out.ctypes.data),
            "fmm_lattice_operator")
     return out
+
+
+def probe_fp32_rate(launches=20, stream=None):
+    """fmm_probe_fp32_rate: (TFLOP/s, ms per launch) of independent FFMA2 chains."""
+    t = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(lib.fmm_probe_fp32_rate(int(launches), ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)),
+           "fmm_probe_fp32_rate")
+    return float(t.value), float(ms.value)
 
 
 def selftest_bounded_wait(spins, arrive, stream=None):

@@ -57,7 +57,7 @@ constexpr int kGather = (2 * kN * 8) / kProducers;          // 16-byte items per
 constexpr int64_t kItemMinSteps = 64;
 constexpr int64_t kItemMaxSteps = 256;
 constexpr int64_t kItemTarget = 4 * 2 * 152;
-constexpr int64_t kItemsMax = 1 << 16;
+constexpr int64_t kItemsMax = 1 << 15;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

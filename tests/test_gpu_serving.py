@@ -163,16 +163,17 @@ def test_serving_memory_budget():
 
 def test_serving_budget_holds_when_the_footprint_model_underestimates():
     """The class footprint model starts at 1 byte per particle, so the first
-    batch (all twelve 200k-blob requests) is admitted far beyond what the 3 GiB
-    budget holds.  The budget refuses the plan's allocations, the batch goes
+    batch (all twelve 50k-blob Plummer requests, which need several GiB
+    together: a 200k-blob request alone measured 3.2 GB) is admitted far beyond
+    the 3 GiB budget.  The budget refuses the plan's allocations, the batch goes
     back to the queue with a larger per-particle need, and every request still
     completes, bit-identical to its evaluation alone, while the bytes the
     server allocated never exceed the budget."""
     from paper_1106_5273_gb300 import Server
     budget = 3 << 30
     srv = Server(workers=2, batching=1, theta=THETA, ncrit=NCRIT, hbm_budget_bytes=budget,
-                 max_batch_particles=4000000, model_bytes_per_particle=1)
-    reqs = [dict(w=workloads.plummer(200000, seed=300 + k, sigma_rule="halfmass"), p=4, periodic=False, box=None)
+                 max_batch_particles=600000, model_bytes_per_particle=1)
+    reqs = [dict(w=workloads.plummer(50000, seed=300 + k, sigma_rule="halfmass"), p=4, periodic=False, box=None)
             for k in range(12)]
     tickets = _submit_all(srv, reqs)
     results = [srv.wait(t, 600.0) for t in tickets]
