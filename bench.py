@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-config3", action="store_true", help="skip the 512^3 spectrum run of the default line")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched run of the default line")
     ap.add_argument("--no-reuse", action="store_true", help="skip the tree-reuse / graph-replay run")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FP32 throughput probe (profiling runs)")
     ap.add_argument("--serving-seconds", type=float, default=1.0, help="arrival horizon of the serving run")
     ap.add_argument("--serving-rate", type=float, default=200.0, help="mean arrivals per second")
     return ap.parse_args()
@@ -742,7 +743,7 @@ def main():
         except Exception:
             traffic = None
     roof = p2p_roofline(st, sum(p2p_ms) / len(p2p_ms), traffic)
-    if rank == 0:
+    if rank == 0 and not args.no_probe:
         from paper_1106_5273_gb300 import binding as _b
         pclk = ClockSampler(local)
         pclk.start()
