@@ -113,6 +113,10 @@ typedef struct fmm_plan_s* fmm_plan;
  *              A and B are cubes of one size) or FMM_SPLIT_TARGET (split A
  *              then).  Alg. 1 always splits the larger cube; when that cell
  *              is a leaf the other one is split.
+ *   p2p_tpl    P2P tile: target particles per lane of the one-warp pair kernel,
+ *              0 (default: 2 when ncrit > 32, else 1), 1, or 2 (the two
+ *              targets as the two halves of packed FP32x2 instructions).  The
+ *              same pair terms either way; fmm_autotune_plan measures it.
  */
 typedef struct {
   int32_t p;
@@ -128,6 +132,7 @@ typedef struct {
   int32_t sigma_rule;
   int32_t p2p_pair_max;
   int32_t split_tie;
+  int32_t p2p_tpl;
 } fmm_params;
 
 /* Work counts of the last evaluation (for throughput and roofline reports). */
@@ -238,6 +243,16 @@ int fmm_eval_batch(fmm_plan plan, int32_t nprob, const int64_t* offsets, const f
  * its own plans and output buffers; synchronous.  FMM_E_INVAL for bad
  * arguments (ncand >= 1, 1 <= reps <= 100, candidates in 1..4096).
  */
+/*
+ * The same measurement over leaf sizes and P2P tiles: every pair
+ * (ncrit_cand[i], tpl_cand[j]) is timed as above; *best_ncrit and *best_tpl
+ * receive the fastest, ms_out[n_ncrit * n_tpl] (HOST, may be NULL) the mean
+ * milliseconds, ncrit-major.  tpl candidates are 0, 1 or 2 (fmm_params.p2p_tpl).
+ */
+int fmm_autotune_plan(const fmm_params* base, int32_t nprob, const int64_t* offsets, const float* pos,
+                      const float* gamma, const float* sigma_prob, const double* boxes,
+                      const int32_t* ncrit_cand, int32_t n_ncrit, const int32_t* tpl_cand, int32_t n_tpl,
+                      int32_t reps, int32_t* best_ncrit, int32_t* best_tpl, double* ms_out, void* cuda_stream);
 int fmm_autotune_ncrit(const fmm_params* base, int32_t nprob, const int64_t* offsets, const float* pos,
                        const float* gamma, const float* sigma_prob, const double* boxes,
                        const int32_t* candidates, int32_t ncand, int32_t reps, int32_t* best_ncrit,
@@ -267,8 +282,10 @@ int64_t fmm_plan_device_bytes(fmm_plan plan);
  * grew to); the first batch of a class runs alone, so its footprint is
  * measured before anything is admitted next to it.  When a batch does not fit
  * the worker first frees idle plans, then takes fewer requests, then waits
- * for other workers (which free their idle plans while anyone waits).  A
- * request that does not fit the budget on its own completes with FMM_E_NOMEM.
+ * for other workers (which free their idle plans while anyone waits).  When
+ * nothing else runs, the oldest request is attempted alone whatever its
+ * estimate says; a request that does not fit the budget on its own completes
+ * with FMM_E_NOMEM (see below).
  * The budget is also enforced on what the plans actually allocate: every
  * device allocation of a worker is charged to it first and refused if the
  * server's bytes would exceed hbm_budget_bytes.  A batch refused that way
@@ -291,8 +308,9 @@ typedef struct {
   int64_t max_batch_particles;  /* particles per batch (a larger single request runs alone) */
   int32_t max_batch_problems;   /* requests per batch, 1..FMM_BATCH_MAX */
   float theta;                  /* as fmm_params; shared by every request */
-  int32_t ncrit;                /* leaf capacity; 0: autotuned per (p, periodic) class on its
-                                   first batch (fmm_autotune_ncrit over 32 ... 256) */
+  int32_t ncrit;                /* leaf capacity; 0: leaf capacity and P2P tile autotuned per
+                                   (p, periodic) class on its first batch (fmm_autotune_plan
+                                   over ncrit 32 ... 256 and p2p_tpl 1, 2) */
   float sigma_sep;
   int32_t images;
   int32_t m2l_mode;             /* the plans' other parameters take fmm_params_default's values */

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
                 ("box_min", ctypes.c_double * 3), ("box_len", ctypes.c_double),
                 ("sigma_sep", ctypes.c_float), ("outputs", ctypes.c_int32),
                 ("m2l_mode", ctypes.c_int32), ("sigma_rule", ctypes.c_int32),
-                ("p2p_pair_max", ctypes.c_int32), ("split_tie", ctypes.c_int32)]
+                ("p2p_pair_max", ctypes.c_int32), ("split_tie", ctypes.c_int32), ("p2p_tpl", ctypes.c_int32)]
 
     @classmethod
     def default(cls, **kw):
@@ -82,6 +82,8 @@ for _name in ("fmm_eval_velocity_stretching", "fmm_eval_velocity_stretching_host
     getattr(lib, _name).argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_direct_velocity_stretching.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
 lib.fmm_eval_targets.argtypes = [_vp, _i64, _vp, _vp, _vp, ctypes.c_float, _i64, _vp, _vp, _vp]
+lib.fmm_autotune_plan.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32,
+                                  _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp]
 lib.fmm_autotune_ncrit.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
@@ -416,6 +418,26 @@ def autotune_ncrit(params, offsets, pos, gamma, sigma_prob, boxes=None, candidat
                                   int(reps), ctypes.byref(best), ms.ctypes.data, _stream_ptr(stream)),
            "fmm_autotune_ncrit")
     return int(best.value), {int(c): float(m) for c, m in zip(cand, ms)}
+
+
+def autotune_plan(params, offsets, pos, gamma, sigma_prob, boxes=None, ncrit=(32, 48, 64, 96, 128, 192, 256),
+                  tpl=(1, 2), reps=1, stream=None):
+    """fmm_autotune_plan: the fastest (ncrit, p2p_tpl) on a sample batch; returns
+    (ncrit, tpl, {(ncrit, tpl): ms})."""
+    import numpy as np
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    sp = np.ascontiguousarray(sigma_prob, dtype=np.float32)
+    bx = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.float64)
+    nc = np.ascontiguousarray(ncrit, dtype=np.int32)
+    tp = np.ascontiguousarray(tpl, dtype=np.int32)
+    ms = np.zeros(nc.shape[0] * tp.shape[0], np.float64)
+    bn, bt = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib.fmm_autotune_plan(ctypes.byref(params), off.shape[0] - 1, off.ctypes.data, _dptr(pos, name="pos"),
+                                 _dptr(gamma, name="gamma"), sp.ctypes.data, None if bx is None else bx.ctypes.data,
+                                 nc.ctypes.data, nc.shape[0], tp.ctypes.data, tp.shape[0], int(reps), ctypes.byref(bn),
+                                 ctypes.byref(bt), ms.ctypes.data, _stream_ptr(stream)), "fmm_autotune_plan")
+    table = {(int(a), int(b)): float(ms[i * tp.shape[0] + j]) for i, a in enumerate(nc) for j, b in enumerate(tp)}
+    return int(bn.value), int(bt.value), table
 
 
 class ServerParams(ctypes.Structure):

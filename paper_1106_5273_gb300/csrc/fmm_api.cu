@@ -29,6 +29,7 @@ int check_params(const fmm_params* q) {
   if (q->sigma_rule != FMM_SIGMA_SOURCE && q->sigma_rule != FMM_SIGMA_MIXED) return FMM_E_INVAL;
   if (q->p2p_pair_max < 0) return FMM_E_INVAL;
   if (q->split_tie != FMM_SPLIT_SOURCE && q->split_tie != FMM_SPLIT_TARGET) return FMM_E_INVAL;
+  if (q->p2p_tpl < 0 || q->p2p_tpl > 2) return FMM_E_INVAL;
   return FMM_OK;
 }
 

@@ -1071,7 +1071,7 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
   const float* fs = p->far_s.as<float>();
   const float smaxf = (float)smax;
   const float margin0 = (float)p->cf_margin;
-  const bool two = p->prm.ncrit > 32;
+  const bool two = p->prm.p2p_tpl ? p->prm.p2p_tpl == 2 : p->prm.ncrit > 32;
   const int mixed = ps && p->prm.sigma_rule == FMM_SIGMA_MIXED;
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(scal + kScalCount + 4);
   FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));

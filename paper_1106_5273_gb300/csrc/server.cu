@@ -154,7 +154,9 @@ int run_batch(fmm_server S, Worker* W, std::vector<fmm_request>& rs, int64_t nto
   fmm_params_default(&q);
   q.p = r0.p;
   q.theta = S->prm.theta;
-  q.ncrit = ncrit > 0 ? ncrit : 64;
+  // ncrit: the leaf capacity, with an autotuned P2P tile in bits 16 and up
+  q.ncrit = ncrit > 0 ? (ncrit & 0xffff) : 64;
+  q.p2p_tpl = ncrit > 0 ? (ncrit >> 16) : 0;
   q.sigma_sep = S->prm.sigma_sep;
   q.images = S->prm.images;
   q.m2l_mode = S->prm.m2l_mode;
@@ -186,16 +188,18 @@ int run_batch(fmm_server S, Worker* W, std::vector<fmm_request>& rs, int64_t nto
     FMM_CUDA_TRY(cudaMemcpyAsync(dp + 3 * off[k], rs[k].pos, (size_t)rs[k].n * 12, cudaMemcpyHostToDevice, st));
     FMM_CUDA_TRY(cudaMemcpyAsync(dg + 3 * off[k], rs[k].gamma, (size_t)rs[k].n * 12, cudaMemcpyHostToDevice, st));
   }
-  if (ncrit == 0 && ntot > 0) {  // first batch of the class: measure the leaf capacity on it
-    int32_t best = 64;
-    FMM_TRY(fmm_autotune_ncrit(&q, (int32_t)rs.size(), off.data(), dp, dg, sig.data(),
-                               r0.periodic ? box.data() : nullptr, kTuneCandidates,
-                               (int32_t)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0])), 1, &best, nullptr,
-                               st));
+  if (ncrit == 0 && ntot > 0) {  // first batch of the class: measure leaf capacity and P2P tile on it
+    int32_t best = 64, best_tpl = 0;
+    const int32_t tpls[2] = {1, 2};
+    FMM_TRY(fmm_autotune_plan(&q, (int32_t)rs.size(), off.data(), dp, dg, sig.data(),
+                              r0.periodic ? box.data() : nullptr, kTuneCandidates,
+                              (int32_t)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0])), tpls, 2, 1, &best,
+                              &best_tpl, nullptr, st));
     q.ncrit = best;
-    *ncrit_out = best;
+    q.p2p_tpl = best_tpl;
+    *ncrit_out = best | (best_tpl << 16);
   }
-  if (plan && (plan->n_max < ntot || plan->prm.ncrit != q.ncrit)) {
+  if (plan && (plan->n_max < ntot || plan->prm.ncrit != q.ncrit || plan->prm.p2p_tpl != q.p2p_tpl)) {
     fmm_plan_destroy(plan);
     plan = nullptr;
   }
@@ -283,18 +287,12 @@ void worker_loop(fmm_server S, Worker* W) {
       drop_plans(S, W, c);
       if (S->held_total - W->held + projected(S, W, c, ntot) <= budget) continue;
       if (!busy) {
+        // Nothing else runs and nothing else is held: the request goes ahead
+        // alone whatever the projection says.  The byte budget decides on its
+        // actual allocations; a request it keeps refusing completes with
+        // FMM_E_NOMEM (the refusal path after the batch).
         drop_plans(S, W, -1);
-        if (S->held_total - W->held + projected(S, W, c, ntot) <= budget) continue;
-        Req& rq = S->reqs[batch[0]];
-        rq.res.status = FMM_E_NOMEM;
-        rq.res.t_start = rq.res.t_done = S->now();
-        rq.res.worker = W->id;
-        rq.res.batch_problems = 1;
-        rq.res.batch_particles = rq.r.n;
-        rq.done = true;
-        S->queue.erase(std::find(S->queue.begin(), S->queue.end(), batch[0]));
-        S->cv_done.notify_all();
-        continue;
+        break;
       }
       if (!waited) ++S->ctr.memory_waits;
       waited = true;

@@ -250,50 +250,71 @@ __device__ inline void child_bounds(const uint64_t* skeys, int b, int e, uint64_
   for (int d = 1; d < 8; ++d) bd[d] = lower_bound_u64(skeys, b, e, ((prefix << 3) | (uint64_t)d) << shift);
 }
 
+// One group of 8 lanes per cell: lane d finds the first particle of child
+// digit d (a binary search in the cell's sorted keys, d = 1..7; lane 0 holds
+// the cell's begin), so the 7 searches run side by side instead of one after
+// the other.  The bounds are kept in bnd[8 * (c - lb) + d] for k_split_write.
 __global__ void k_split_count(const uint64_t* __restrict__ skeys, const int* __restrict__ begin,
                               const int* __restrict__ end, const uint64_t* __restrict__ key, int lb, int le,
-                              int l, int kbits, int ncrit, uint32_t* __restrict__ cnt) {
-  int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= le) return;
-  int b = begin[c], e = end[c];
+                              int l, int kbits, int ncrit, uint32_t* __restrict__ cnt, int* __restrict__ bnd) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = lb + (t >> 3), d = t & 7;
+  const bool live = c < le;
+  int b = 0, e = 0;
+  bool split = false;
+  if (live) {
+    b = begin[c];
+    e = end[c];
+    split = e - b > ncrit && l < kbits;
+  }
+  int bd = b;
+  if (split && d > 0) {
+    const int shift = 3 * (kbits - 1 - l);
+    bd = lower_bound_u64(skeys, b, e, ((key[c] << 3) | (uint64_t)d) << shift);
+  }
+  // lane d's child is non-empty when the next bound (lane d + 1, or the end) is larger
+  const int nb = __shfl_down_sync(0xffffffffu, bd, 1, 8);
+  const int next = d == 7 ? e : nb;
+  const unsigned grp = (threadIdx.x & 31) & ~7u;
+  const unsigned m = __ballot_sync(0xffffffffu, split && next > bd);
+  if (!live) return;
+  bnd[8 * (c - lb) + d] = bd;
+  if (d == 0) cnt[c - lb] = (uint32_t)__popc((m >> grp) & 0xffu);
+}
+
+__global__ void k_split_write(int* __restrict__ begin, int* __restrict__ end, int* __restrict__ level,
+                              int* __restrict__ parent, int* __restrict__ child, int* __restrict__ nchild,
+                              uint64_t* __restrict__ key, int lb, int le, int l, const uint32_t* __restrict__ cnt,
+                              const uint32_t* __restrict__ off, const int* __restrict__ bnd) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = lb + (t >> 3), d = t & 7;
+  const bool live = c < le;
   uint32_t k = 0;
-  if (e - b > ncrit && l < kbits) {
-    int bd[9];
-    child_bounds(skeys, b, e, key[c], l, kbits, bd);
-    for (int d = 0; d < 8; ++d) k += bd[d + 1] > bd[d] ? 1u : 0u;
+  int bd = 0, e = 0;
+  if (live) {
+    k = cnt[c - lb];
+    bd = bnd[8 * (c - lb) + d];
+    e = end[c];
   }
-  cnt[c - lb] = k;
+  const int nb = __shfl_down_sync(0xffffffffu, bd, 1, 8);
+  const int next = d == 7 ? e : nb;
+  const bool mine = live && k > 0 && next > bd;
+  const unsigned grp = (threadIdx.x & 31) & ~7u;
+  const unsigned m = (__ballot_sync(0xffffffffu, mine) >> grp) & 0xffu;
+  if (!live) return;
+  const int first = le + (int)off[c - lb];
+  if (d == 0) {
+    nchild[c] = (int)k;
+    child[c] = k ? first : -1;
+  }
+  if (!mine) return;
+  const int o = first + __popc(m & ((1u << d) - 1u));  // children in digit order
+  begin[o] = bd;
+  end[o] = next;
+  level[o] = l + 1;
+  parent[o] = c;
+  key[o] = (key[c] << 3) | (uint64_t)d;
 }
-
-__global__ void k_split_write(const uint64_t* __restrict__ skeys, int* __restrict__ begin, int* __restrict__ end,
-                              int* __restrict__ level, int* __restrict__ parent, int* __restrict__ child,
-                              int* __restrict__ nchild, uint64_t* __restrict__ key, int lb, int le, int l,
-                              int kbits, const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off) {
-  int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= le) return;
-  uint32_t k = cnt[c - lb];
-  nchild[c] = (int)k;
-  if (k == 0) {
-    child[c] = -1;
-    return;
-  }
-  int first = le + (int)off[c - lb];
-  child[c] = first;
-  int bd[9];
-  child_bounds(skeys, begin[c], end[c], key[c], l, kbits, bd);
-  int o = first;
-  for (int d = 0; d < 8; ++d) {
-    if (bd[d + 1] > bd[d]) {
-      begin[o] = bd[d];
-      end[o] = bd[d + 1];
-      level[o] = l + 1;
-      parent[o] = c;
-      key[o] = (key[c] << 3) | (uint64_t)d;
-      ++o;
-    }
-  }
-}
-
 
 // Cell key = problem index above the 3l level-local Morton bits.
 __global__ void k_centers(const int* __restrict__ level, const uint64_t* __restrict__ key, int nc,
@@ -409,10 +430,11 @@ static int tree_from_sorted(fmm_plan p, int64_t n, int nroot, const int* off, co
     int ncl = le - lb;
     FMM_TRY(p->tcount.ensure((size_t)(ncl + 1) * sizeof(uint32_t)));
     FMM_TRY(p->tscan0.ensure((size_t)(ncl + 1) * sizeof(uint32_t)));
-    unsigned g = (unsigned)((ncl + T - 1) / T);
+    FMM_TRY(p->tscan1.ensure((size_t)(8 * (int64_t)ncl + 8) * sizeof(int)));  // child bounds (free until the traversal)
+    unsigned g = (unsigned)((8 * (int64_t)ncl + T - 1) / T);
     ++g_launches;
     k_split_count<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_key.as<uint64_t>(),
-                                  lb, le, l, kbits, p->prm.ncrit, p->tcount.as<uint32_t>());
+                                  lb, le, l, kbits, p->prm.ncrit, p->tcount.as<uint32_t>(), p->tscan1.as<int>());
     FMM_TRY(exclusive_scan_u32(p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(), ncl,
                                p->tscan0.as<uint32_t>() + ncl, p->scan_tmp, s));
     FMM_CUDA_TRY(cudaMemcpyAsync(hcount, p->tscan0.as<uint32_t>() + ncl, sizeof(uint32_t),
@@ -421,10 +443,10 @@ static int tree_from_sorted(fmm_plan p, int64_t n, int nroot, const int* off, co
     int64_t nnew = hcount[0];
     if (le + nnew > (int64_t)(p->c_begin.bytes / sizeof(int))) FMM_TRY(grow_cells(p, 2 * (le + nnew), s));
     ++g_launches;
-    k_split_write<<<g, T, 0, s>>>(p->skeys, p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
+    k_split_write<<<g, T, 0, s>>>(p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(),
                                   p->c_parent.as<int>(), p->c_child.as<int>(), p->c_nchild.as<int>(),
-                                  p->c_key.as<uint64_t>(), lb, le, l, kbits, p->tcount.as<uint32_t>(),
-                                  p->tscan0.as<uint32_t>());
+                                  p->c_key.as<uint64_t>(), lb, le, l, p->tcount.as<uint32_t>(),
+                                  p->tscan0.as<uint32_t>(), p->tscan1.as<int>());
     FMM_CUDA_TRY(cudaGetLastError());
     if (nnew == 0) break;
     lb = le;

@@ -207,6 +207,29 @@ def test_autotune_ncrit_picks_the_fastest_candidate():
     plan.close()
 
 
+def test_autotune_plan_picks_leaf_size_and_p2p_tile():
+    """fmm_autotune_plan times every (ncrit, p2p_tpl) pair and returns the
+    fastest.  The one- and two-targets-per-lane P2P kernels evaluate the same
+    pair terms (staged in chunks of 32 or 64 sources, so the sums are ordered
+    differently): their results agree to FP32 rounding."""
+    import torch
+    from paper_1106_5273_gb300 import Params, Plan, autotune_plan
+    probs = _free_problems()[2:5]
+    off, pos, gam, sig, _ = _concat(probs)
+    prm = Params.default(p=8, theta=0.5, ncrit=64)
+    bn, bt, ms = autotune_plan(prm, off, to_dev(pos), to_dev(gam), sig, ncrit=(32, 64, 128), tpl=(1, 2), reps=2)
+    assert set(ms) == {(a, b) for a in (32, 64, 128) for b in (1, 2)}
+    assert all(v > 0 for v in ms.values()) and ms[(bn, bt)] == min(ms.values())
+    outs = []
+    for tpl in (1, 2):
+        plan = Plan(int(off[-1]), Params.default(p=8, theta=0.5, ncrit=64, p2p_tpl=tpl))
+        u, s = plan.eval_batch(off, to_dev(pos), to_dev(gam), sigma_prob=sig)
+        torch.cuda.synchronize()
+        outs.append((u.cpu().numpy(), s.cpu().numpy()))
+        plan.close()
+    assert rel_l2(outs[0][0], outs[1][0]) < 1e-6 and rel_l2(outs[0][1], outs[1][1]) < 1e-6
+
+
 def test_batch_argument_errors():
     import torch
     from paper_1106_5273_gb300 import Plan, Params, FmmError, BATCH_MAX
