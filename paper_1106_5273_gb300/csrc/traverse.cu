@@ -7,8 +7,9 @@
 // on every child pair: M2L if the FMM MAC holds (R_A + R_B < theta |X_A-X_B|)
 // and the pair is at least k_sigma sigma_max apart (the far field uses the
 // singular kernel), else P2P if both are leaves, else push.  Here the stack
-// is a breadth-first frontier processed in two passes (classify, scan, emit),
-// so the emitted lists have a fixed order.  Periodic: the traversal starts
+// is a breadth-first frontier processed in two passes per level (classify,
+// then emit at scanned offsets) by one cooperative kernel for all levels, so
+// the emitted lists have a fixed order and the host reads their sizes once.  Periodic: the traversal starts
 // from (root, root + o L) for the 27 o in {-1,0,1}^3.  The MAC is evaluated
 // in FP64 with explicitly rounded operations in a fixed order.
 //
@@ -16,6 +17,7 @@
 // into steps = (tile of 64 consecutive target cells of one level, translation
 // key), each step carrying the source cell of every tile slot (or -1).
 #include <climits>
+#include <cstring>
 
 #include "fmm_internal.cuh"
 
@@ -144,48 +146,206 @@ __device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, 
   nc = t.nchild[s];
 }
 
-__global__ void k_trav_classify(TravArgs t, const int4* __restrict__ fr, int nfr, uint32_t* __restrict__ mask,
-                                uint32_t* __restrict__ cm, uint32_t* __restrict__ cp, uint32_t* __restrict__ cf) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nfr) return;
-  int4 pr = fr[i];
-  bool sa;
-  int c0, nc;
-  split_of(t, pr.x, pr.y, sa, c0, nc);
-  uint32_t msk = 0, nm = 0, np = 0, nf = 0;
-  for (int q = 0; q < nc; ++q) {
-    int c = c0 + q;
-    int ty = sa ? interact(t, c, pr.y, pr.z) : interact(t, pr.x, c, pr.z);
-    msk |= (uint32_t)ty << (2 * q);
-    nm += ty == 0;
-    np += ty == 1;
-    nf += ty == 2;
+// ---- The frontier loop as one cooperative kernel.
+//
+// All levels of the frontier in one launch: the blocks own contiguous ranges
+// of the frontier; per level they classify their pairs (phase A), meet at a
+// grid barrier, take their output offsets from the block totals and emit the
+// children in item order (phase B), and meet again.  The lists come out in
+// the same order as the level-by-level kernels above (item order, children in
+// digit order), with no host round trip per level.  Every block is resident
+// (cooperative launch); each barrier wait is bounded and gives up with
+// FMM_E_TIMEOUT.  When a list would outgrow its buffer the blocks stop
+// together and report what they needed (the host grows the buffers and runs
+// the traversal again).
+
+constexpr int kTravThreads = 256;
+constexpr int kTravMaxIter = 128;         // > 2 x the 22 levels a pair can descend
+constexpr long long kGridSpin = 1ll << 24;
+
+// state[]: 0 nm, 1 np, 2 nf, 3 overflow, 4 need_m, 5 need_p, 6 need_f, 7 iterations,
+// 8 barrier arrivals, 9 barrier generation, 10 abort
+struct TravState {
+  uint32_t nm, np, nf, overflow, need_m, need_p, need_f, iters, bar_count, bar_gen, abort;
+};
+
+__device__ bool grid_barrier(TravState* st, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = &st->bar_gen;
+    volatile uint32_t* ab = &st->abort;
+    const uint32_t g = *gen;
+    __threadfence();
+    if (atomicAdd(&st->bar_count, 1u) == nblocks - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      for (long long i = 0; *gen == g; ++i) {
+        if (*ab) break;
+        if (i > kGridSpin) {
+          atomicExch(&st->abort, 1u);
+          break;
+        }
+      }
+    }
+    __threadfence();
   }
-  mask[i] = msk;
-  cm[i] = nm;
-  cp[i] = np;
-  cf[i] = nf;
+  __syncthreads();
+  return ((volatile uint32_t*)&st->abort)[0] == 0u;
 }
 
-__global__ void k_trav_emit(TravArgs t, const int4* __restrict__ fr, int nfr, const uint32_t* __restrict__ mask,
-                            const uint32_t* __restrict__ om, const uint32_t* __restrict__ op,
-                            const uint32_t* __restrict__ of, uint32_t bm, uint32_t bp, int4* __restrict__ m2l,
-                            int4* __restrict__ p2p, int4* __restrict__ nfrontier) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nfr) return;
-  int4 pr = fr[i];
-  bool sa;
-  int c0, nc;
-  split_of(t, pr.x, pr.y, sa, c0, nc);
-  uint32_t msk = mask[i];
-  uint32_t im = bm + om[i], ip = bp + op[i], iff = of[i];
-  for (int q = 0; q < nc; ++q) {
-    int c = c0 + q;
-    int4 v = sa ? make_int4(c, pr.y, pr.z, 0) : make_int4(pr.x, c, pr.z, 0);
-    int ty = (msk >> (2 * q)) & 3;
-    if (ty == 0) m2l[im++] = v;
-    else if (ty == 1) p2p[ip++] = v;
-    else nfrontier[iff++] = v;
+// Exclusive block scan of three counts (thread order); returns the block totals.
+__device__ inline void block_scan3(uint32_t v[3], uint32_t tot[3]) {
+  __shared__ uint32_t ws[3][kTravThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    inc[k] = v[k];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc[k], o);
+      if (lane >= o) inc[k] += y;
+    }
+    if (lane == 31) ws[k][w] = inc[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint32_t before = 0, all = 0;
+    for (int i = 0; i < kTravThreads / 32; ++i) {
+      const uint32_t x = ws[k][i];
+      if (i < w) before += x;
+      all += x;
+    }
+    v[k] = before + inc[k] - v[k];
+    tot[k] = all;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __restrict__ frA, int4* __restrict__ frB,
+                                                            const uint32_t* __restrict__ cnt0, int4* __restrict__ m2l,
+                                                            int4* __restrict__ p2p, uint32_t* __restrict__ mask,
+                                                            uint32_t* __restrict__ blk, TravState* st, uint32_t cap_fr,
+                                                            uint32_t cap_m, uint32_t cap_p) {
+  __shared__ uint32_t red[3][kTravThreads / 32];
+  __shared__ uint32_t bases[6];
+  const unsigned G = gridDim.x, b = blockIdx.x;
+  uint32_t nm = cnt0[0], np = cnt0[1], nf = cnt0[2];
+  int4* cur = frA;
+  int4* nxt = frB;
+  int iter = 0;
+  for (; nf > 0 && iter < kTravMaxIter; ++iter) {
+    const uint32_t chunk = (nf + G - 1) / G;
+    const uint32_t i0 = min(nf, b * chunk), i1 = min(nf, i0 + chunk);
+    // phase A: classify the block's pairs, block totals
+    uint32_t c[3] = {0u, 0u, 0u};
+    for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int4 pr = cur[i];
+      bool sa;
+      int c0, ncc;
+      split_of(t, pr.x, pr.y, sa, c0, ncc);
+      uint32_t msk = 0;
+      for (int q = 0; q < ncc; ++q) {
+        const int ch = c0 + q;
+        const int ty = sa ? interact(t, ch, pr.y, pr.z) : interact(t, pr.x, ch, pr.z);
+        msk |= (uint32_t)ty << (2 * q);
+        c[ty] += 1u;
+      }
+      mask[i] = msk | ((uint32_t)ncc << 16);
+    }
+    {
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        uint32_t x = c[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][w] = x;
+      }
+      __syncthreads();
+      if (threadIdx.x < 3) {
+        uint32_t x = 0;
+        for (int i = 0; i < kTravThreads / 32; ++i) x += red[threadIdx.x][i];
+        blk[3 * b + threadIdx.x] = x;
+      }
+    }
+    if (!grid_barrier(st, G)) return;
+    // offsets of this block (sum of the earlier blocks) and the level totals
+    if (threadIdx.x < 6) bases[threadIdx.x] = 0u;
+    __syncthreads();
+    {
+      uint32_t pre[3] = {0u, 0u, 0u}, all[3] = {0u, 0u, 0u};
+      for (unsigned j = threadIdx.x; j < G; j += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t x = ((volatile uint32_t*)blk)[3 * j + k];
+          all[k] += x;
+          if (j < b) pre[k] += x;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        atomicAdd(&bases[k], pre[k]);
+        atomicAdd(&bases[3 + k], all[k]);
+      }
+    }
+    __syncthreads();
+    const uint32_t tm = bases[3], tp = bases[4], tf = bases[5];
+    if ((uint64_t)nm + tm > cap_m || (uint64_t)np + tp > cap_p || tf > cap_fr) {
+      // every block sees the same totals and stops here
+      if (b == 0 && threadIdx.x == 0) {
+        st->overflow = 1u;
+        st->need_m = nm + tm;
+        st->need_p = np + tp;
+        st->need_f = tf;
+      }
+      break;
+    }
+    // phase B: emit in item order
+    uint32_t run[3] = {nm + bases[0], np + bases[1], bases[2]};
+    for (uint32_t base = i0; base < i1; base += blockDim.x) {
+      const uint32_t i = base + threadIdx.x;
+      uint32_t msk = 0, ncc = 0;
+      uint32_t v[3] = {0u, 0u, 0u};
+      if (i < i1) {
+        msk = mask[i];
+        ncc = msk >> 16;
+        for (uint32_t q = 0; q < ncc; ++q) v[(msk >> (2 * q)) & 3u] += 1u;
+      }
+      uint32_t tot[3];
+      block_scan3(v, tot);
+      if (i < i1) {
+        const int4 pr = cur[i];
+        bool sa;
+        int c0, ncn;
+        split_of(t, pr.x, pr.y, sa, c0, ncn);
+        uint32_t im = run[0] + v[0], ip = run[1] + v[1], iff = run[2] + v[2];
+        for (uint32_t q = 0; q < ncc; ++q) {
+          const int ch = c0 + (int)q;
+          const int4 val = sa ? make_int4(ch, pr.y, pr.z, 0) : make_int4(pr.x, ch, pr.z, 0);
+          const uint32_t ty = (msk >> (2 * q)) & 3u;
+          if (ty == 0) m2l[im++] = val;
+          else if (ty == 1) p2p[ip++] = val;
+          else nxt[iff++] = val;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) run[k] += tot[k];
+    }
+    nm += tm;
+    np += tp;
+    nf = tf;
+    int4* sw = cur;
+    cur = nxt;
+    nxt = sw;
+    if (!grid_barrier(st, G)) return;
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    st->nm = nm;
+    st->np = np;
+    st->nf = nf;
+    st->iters = (uint32_t)iter;
   }
 }
 
@@ -573,53 +733,62 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   uint32_t* hc = reinterpret_cast<uint32_t*>(p->pinned);
   uint32_t* dcnt = reinterpret_cast<uint32_t*>(p->scal.as<double>() + kScalCount);
 
+  // Frontier loop: one cooperative launch for all levels; the host reads the
+  // list sizes once.  Buffers too small for the lists are grown to what the
+  // kernel reports and the traversal runs again.
   int64_t cap_fr = std::max<int64_t>(1024, 16 * (int64_t)nc);
   int64_t cap_m = std::max<int64_t>(1024, 64 * (int64_t)nc);
   int64_t cap_p = std::max<int64_t>(1024, 32 * (int64_t)nc);
-  FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
-  FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
-  FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int4), s));
-  FMM_TRY(p->p2p_raw.grow_copy(cap_p * sizeof(int4), s));
-  ++g_launches;
-  k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(),
-                                 p->p2p_raw.as<int4>(), dcnt);
-  FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  FMM_CUDA_TRY(cudaStreamSynchronize(s));
-  int64_t nm = hc[0], np = hc[1], nf = hc[2];
-  fmm::DBuf* cur = &p->fr0;
-  fmm::DBuf* nxt = &p->fr1;
-  while (nf > 0) {
-    FMM_TRY(p->tmask.ensure((nf + 1) * sizeof(uint32_t)));
-    FMM_TRY(p->tcount.ensure((nf + 1) * sizeof(uint32_t)));
-    FMM_TRY(p->tscan0.ensure((nf + 1) * sizeof(uint32_t)));
-    FMM_TRY(p->tscan1.ensure((nf + 1) * sizeof(uint32_t)));
-    FMM_TRY(p->tscan2.ensure((nf + 1) * sizeof(uint32_t)));
-    unsigned g = (unsigned)((nf + T - 1) / T);
-    uint32_t* cm = p->tscan0.as<uint32_t>();
-    uint32_t* cp = p->tscan1.as<uint32_t>();
-    uint32_t* cf = p->tscan2.as<uint32_t>();
+  static int grid_blocks[64] = {0};
+  const int dev = p->device >= 0 && p->device < 64 ? p->device : 0;
+  if (!grid_blocks[dev]) {
+    int sms = 0, per_sm = 0;
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trav_loop, kTravThreads, 0));
+    grid_blocks[dev] = std::max(1, sms * std::min(per_sm, 4));
+  }
+  const unsigned G = (unsigned)grid_blocks[dev];
+  int64_t nm = 0, np = 0;
+  TravState* dst = nullptr;
+  for (int attempt = 0;; ++attempt) {
+    if (attempt > 4 || cap_fr > 0x7fffffff || cap_m > 0x7fffffff || cap_p > 0x7fffffff) return FMM_E_CAPACITY;
+    FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
+    FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
+    FMM_TRY(p->m2l_raw.ensure(cap_m * sizeof(int4)));
+    FMM_TRY(p->p2p_raw.ensure(cap_p * sizeof(int4)));
+    FMM_TRY(p->tmask.ensure(cap_fr * sizeof(uint32_t)));
+    FMM_TRY(p->tscan0.ensure((size_t)(3 * G + 8) * sizeof(uint32_t)));
+    FMM_TRY(p->tscan1.ensure(sizeof(TravState) + 64));
+    dst = p->tscan1.as<TravState>();
+    FMM_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), s));
     ++g_launches;
-    k_trav_classify<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf);
-    {  // the three counts in shared passes (sort_hist is free during the traversal)
-      const uint32_t* const cin[3] = {cm, cp, cf};
-      uint32_t* const cout[3] = {cm, cp, cf};
-      FMM_TRY(exclusive_scan3_u32(cin, cout, nf, dcnt, p->scan_tmp, p->sort_hist, s));
-    }
-    FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(),
+                                   p->p2p_raw.as<int4>(), dcnt);
+    int4* a0 = p->fr0.as<int4>();
+    int4* a1 = p->fr1.as<int4>();
+    int4* am = p->m2l_raw.as<int4>();
+    int4* ap = p->p2p_raw.as<int4>();
+    uint32_t* msk = p->tmask.as<uint32_t>();
+    uint32_t* blk = p->tscan0.as<uint32_t>();
+    uint32_t cf = (uint32_t)cap_fr, cm = (uint32_t)cap_m, cp = (uint32_t)cap_p;
+    void* args[] = {&ta, &a0, &a1, &dcnt, &am, &ap, &msk, &blk, &dst, &cf, &cm, &cp};
+    ++g_launches;
+    FMM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_trav_loop, dim3(G), dim3(kTravThreads), args, 0, s));
+    TravState hs;
+    FMM_CUDA_TRY(cudaMemcpyAsync(hc, dst, sizeof(TravState), cudaMemcpyDeviceToHost, s));
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
-    int64_t am = hc[0], ap = hc[1], af = hc[2];
-    FMM_TRY(p->m2l_raw.grow_copy((nm + am) * sizeof(int4), s));
-    FMM_TRY(p->p2p_raw.grow_copy((np + ap) * sizeof(int4), s));
-    FMM_TRY(nxt->ensure((af + 1) * sizeof(int4)));
-    ++g_launches;
-    k_trav_emit<<<g, T, 0, s>>>(ta, cur->as<int4>(), (int)nf, p->tmask.as<uint32_t>(), cm, cp, cf, (uint32_t)nm,
-                                (uint32_t)np, p->m2l_raw.as<int4>(), p->p2p_raw.as<int4>(), nxt->as<int4>());
-    FMM_CUDA_TRY(cudaGetLastError());
-    nm += am;
-    np += ap;
-    nf = af;
-    std::swap(cur, nxt);
-    if (nm > 0x7fffffff || np > 0x7fffffff) return FMM_E_CAPACITY;
+    memcpy(&hs, hc, sizeof(TravState));
+    if (hs.abort) return FMM_E_TIMEOUT;
+    if (hs.overflow) {  // grow to what was needed (x1.25) and run the traversal again
+      cap_m = std::max<int64_t>(cap_m, (int64_t)hs.need_m + hs.need_m / 4 + 1024);
+      cap_p = std::max<int64_t>(cap_p, (int64_t)hs.need_p + hs.need_p / 4 + 1024);
+      cap_fr = std::max<int64_t>(cap_fr, (int64_t)hs.need_f + hs.need_f / 4 + 1024);
+      continue;
+    }
+    if (hs.nf != 0) return FMM_E_CAPACITY;  // deeper than kTravMaxIter levels of the frontier
+    nm = hs.nm;
+    np = hs.np;
+    break;
   }
   p->n_m2l = nm;
   p->n_p2p = np;
