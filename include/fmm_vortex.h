@@ -158,6 +158,7 @@ typedef struct {
   double ms_downward;
   double ms_p2p;
   double ms_total;
+  int64_t traversal_runs; /* traversal launches (> 1 when the lists outgrew their buffers) */
 } fmm_stats;
 
 /* Fill *prm with defaults: p=10, theta=0.4, ncrit=64, free space, images=3,
@@ -519,6 +520,17 @@ int fmm_selftest_bounded_wait(int64_t spins, int arrive, void* cuda_stream);
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all plans and entry points; for launch accounting in benchmarks). */
 int64_t fmm_kernel_launch_count(void);
+
+/*
+ * Starting capacities (entries) of the traversal's buffers for the plan's
+ * next evaluations: the frontier, the M2L pairs and the P2P pairs (0: sized
+ * from the cell count, the default).  The traversal runs all levels in one
+ * launch; when a list would outgrow its buffer the launch stops, the buffers
+ * grow to what it reported and the traversal runs again
+ * (fmm_stats.traversal_runs counts the launches).  Small values exercise
+ * that path.  FMM_E_INVAL for a negative value.
+ */
+int fmm_plan_set_list_capacity(fmm_plan plan, int64_t frontier, int64_t m2l, int64_t p2p);
 
 /* Enable (1) or disable (0) CUDA-event phase timing in fmm_stats. */
 int fmm_plan_set_timing(fmm_plan plan, int enable);

@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
                 ("p2p_pairs_far", ctypes.c_int64), ("ms_tree", ctypes.c_double),
                 ("ms_upward", ctypes.c_double), ("ms_traverse", ctypes.c_double),
                 ("ms_m2l", ctypes.c_double), ("ms_downward", ctypes.c_double),
-                ("ms_p2p", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("ms_p2p", ctypes.c_double), ("ms_total", ctypes.c_double), ("traversal_runs", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +87,7 @@ lib.fmm_autotune_plan.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, _vp, _
 lib.fmm_autotune_ncrit.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
 lib.fmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+lib.fmm_plan_set_list_capacity.argtypes = [_vp, _i64, _i64, _i64]
 lib.fmm_selftest_bounded_wait.argtypes = [_i64, ctypes.c_int, _vp]
 lib.fmm_eval_batch.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 lib.fmm_plan_device_bytes.argtypes = [_vp]
@@ -257,6 +258,11 @@ class Plan:
     def device_bytes(self):
         """Device memory the plan holds (fmm_plan_device_bytes)."""
         return int(lib.fmm_plan_device_bytes(self._h))
+
+    def set_list_capacity(self, frontier=0, m2l=0, p2p=0):
+        """fmm_plan_set_list_capacity: starting capacities of the traversal's buffers."""
+        _check(lib.fmm_plan_set_list_capacity(self._h, int(frontier), int(m2l), int(p2p)),
+               "fmm_plan_set_list_capacity")
 
     def set_timing(self, on=True):
         _check(lib.fmm_plan_set_timing(self._h, 1 if on else 0), "fmm_plan_set_timing")

@@ -167,6 +167,7 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   st.m2l_steps = p->n_steps;
   st.m2l_keys = p->n_keys;
   st.m2l_built = p->n_built;
+  st.traversal_runs = p->trav_runs;
   st.p2p_pairs_near = (int64_t)cls[0];
   st.p2p_pairs_mid = (int64_t)cls[1];
   st.p2p_pairs_far = (int64_t)cls[2];
@@ -373,6 +374,14 @@ int fmm_lattice_operator(int32_t p, int32_t images, int32_t on_device, double* o
   if (rc == FMM_OK && cudaMemcpy(out, A.ptr, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) rc = FMM_E_CUDA;
   A.release();
   return rc;
+}
+
+int fmm_plan_set_list_capacity(fmm_plan p, int64_t frontier, int64_t m2l, int64_t p2p) {
+  if (!p || frontier < 0 || m2l < 0 || p2p < 0) return FMM_E_INVAL;
+  p->cap_fr0 = frontier;
+  p->cap_m0 = m2l;
+  p->cap_p0 = p2p;
+  return FMM_OK;
 }
 
 int fmm_plan_set_timing(fmm_plan p, int enable) {

@@ -126,6 +126,10 @@ struct fmm_plan_s {
   float reuse_sig_u = 0.f;  // its uniform sigma
   double reuse_smax = 0.0;  // its largest sigma
   int64_t epoch = 0;
+  // list capacities the next traversal starts from (0: from the cell count);
+  // a traversal whose lists outgrow them grows them and runs again
+  int64_t cap_fr0 = 0, cap_m0 = 0, cap_p0 = 0;
+  int64_t trav_runs = 0;  // traversal launches of the last evaluation
   fmm_stats stats;
   cudaEvent_t ev[8];
   int have_events = 0;

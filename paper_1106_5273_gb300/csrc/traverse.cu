@@ -736,9 +736,14 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   // Frontier loop: one cooperative launch for all levels; the host reads the
   // list sizes once.  Buffers too small for the lists are grown to what the
   // kernel reports and the traversal runs again.
-  int64_t cap_fr = std::max<int64_t>(1024, 16 * (int64_t)nc);
-  int64_t cap_m = std::max<int64_t>(1024, 64 * (int64_t)nc);
-  int64_t cap_p = std::max<int64_t>(1024, 32 * (int64_t)nc);
+  int64_t cap_fr = p->cap_fr0 > 0 ? p->cap_fr0 : std::max<int64_t>(1024, 16 * (int64_t)nc);
+  int64_t cap_m = p->cap_m0 > 0 ? p->cap_m0 : std::max<int64_t>(1024, 64 * (int64_t)nc);
+  int64_t cap_p = p->cap_p0 > 0 ? p->cap_p0 : std::max<int64_t>(1024, 32 * (int64_t)nc);
+  // the initial pairs (one per root and image) always fit
+  const int64_t ninit = (int64_t)(p->batched ? p->nseg : 1) * nimg;
+  cap_fr = std::max(cap_fr, ninit);
+  cap_m = std::max(cap_m, ninit);
+  cap_p = std::max(cap_p, ninit);
   static int grid_blocks[64] = {0};
   const int dev = p->device >= 0 && p->device < 64 ? p->device : 0;
   if (!grid_blocks[dev]) {
@@ -751,6 +756,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   int64_t nm = 0, np = 0;
   TravState* dst = nullptr;
   for (int attempt = 0;; ++attempt) {
+    p->trav_runs = attempt + 1;
     if (attempt > 4 || cap_fr > 0x7fffffff || cap_m > 0x7fffffff || cap_p > 0x7fffffff) return FMM_E_CAPACITY;
     FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
     FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
