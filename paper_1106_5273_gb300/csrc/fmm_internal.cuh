@@ -130,6 +130,7 @@ struct fmm_plan_s {
   // a traversal whose lists outgrow them grows them and runs again
   int64_t cap_fr0 = 0, cap_m0 = 0, cap_p0 = 0;
   int64_t trav_runs = 0;  // traversal launches of the last evaluation
+  int64_t hw_fr = 0, hw_m = 0, hw_p = 0;  // list sizes the plan's evaluations needed (+1/8)
   fmm_stats stats;
   cudaEvent_t ev[8];
   int have_events = 0;

@@ -16,6 +16,7 @@
 // Outputs: P2P entries grouped by target leaf (CSR), and M2L entries grouped
 // into steps = (tile of 64 consecutive target cells of one level, translation
 // key), each step carrying the source cell of every tile slot (or -1).
+#include <algorithm>
 #include <climits>
 #include <cstring>
 
@@ -233,6 +234,8 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
   __shared__ uint32_t bases[6];
   const unsigned G = gridDim.x, b = blockIdx.x;
   uint32_t nm = cnt0[0], np = cnt0[1], nf = cnt0[2];
+  bool over_m = false, over_p = false, over_f = false;
+  uint32_t need_f = nf;
   int4* cur = frA;
   int4* nxt = frB;
   int iter = 0;
@@ -292,14 +295,16 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
     }
     __syncthreads();
     const uint32_t tm = bases[3], tp = bases[4], tf = bases[5];
-    if ((uint64_t)nm + tm > cap_m || (uint64_t)np + tp > cap_p || tf > cap_fr) {
-      // every block sees the same totals and stops here
-      if (b == 0 && threadIdx.x == 0) {
-        st->overflow = 1u;
-        st->need_m = nm + tm;
-        st->need_p = np + tp;
-        st->need_f = tf;
-      }
+    // every block sees the same totals, so they all take the same decisions:
+    // a full M2L or P2P list stops being written but is still counted to the
+    // end (the rerun then needs one growth); a full frontier stops the loop
+    if ((uint64_t)nm + tm > cap_m) over_m = true;
+    if ((uint64_t)np + tp > cap_p) over_p = true;
+    need_f = max(need_f, tf);
+    if (tf > cap_fr) {
+      over_f = true;
+      nm += tm;
+      np += tp;
       break;
     }
     // phase B: emit in item order
@@ -325,9 +330,15 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
           const int ch = c0 + (int)q;
           const int4 val = sa ? make_int4(ch, pr.y, pr.z, 0) : make_int4(pr.x, ch, pr.z, 0);
           const uint32_t ty = (msk >> (2 * q)) & 3u;
-          if (ty == 0) m2l[im++] = val;
-          else if (ty == 1) p2p[ip++] = val;
-          else nxt[iff++] = val;
+          if (ty == 0) {
+            if (!over_m) m2l[im] = val;
+            ++im;
+          } else if (ty == 1) {
+            if (!over_p) p2p[ip] = val;
+            ++ip;
+          } else {
+            nxt[iff++] = val;
+          }
         }
       }
 #pragma unroll
@@ -344,8 +355,12 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
   if (b == 0 && threadIdx.x == 0) {
     st->nm = nm;
     st->np = np;
-    st->nf = nf;
+    st->nf = over_f ? 0u : nf;
     st->iters = (uint32_t)iter;
+    st->overflow = (over_m || over_p || over_f) ? 1u : 0u;
+    st->need_m = nm;
+    st->need_p = np;
+    st->need_f = need_f;
   }
 }
 
@@ -736,9 +751,11 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   // Frontier loop: one cooperative launch for all levels; the host reads the
   // list sizes once.  Buffers too small for the lists are grown to what the
   // kernel reports and the traversal runs again.
-  int64_t cap_fr = p->cap_fr0 > 0 ? p->cap_fr0 : std::max<int64_t>(1024, 16 * (int64_t)nc);
-  int64_t cap_m = p->cap_m0 > 0 ? p->cap_m0 : std::max<int64_t>(1024, 64 * (int64_t)nc);
-  int64_t cap_p = p->cap_p0 > 0 ? p->cap_p0 : std::max<int64_t>(1024, 32 * (int64_t)nc);
+  // starting capacities: from the cell count, at least what the plan's earlier
+  // evaluations needed (so a plan that saw its problem once does not rerun)
+  int64_t cap_fr = p->cap_fr0 > 0 ? p->cap_fr0 : std::max<int64_t>({1024, 16 * (int64_t)nc, p->hw_fr});
+  int64_t cap_m = p->cap_m0 > 0 ? p->cap_m0 : std::max<int64_t>({1024, 64 * (int64_t)nc, p->hw_m});
+  int64_t cap_p = p->cap_p0 > 0 ? p->cap_p0 : std::max<int64_t>({1024, 32 * (int64_t)nc, p->hw_p});
   // the initial pairs (one per root and image) always fit
   const int64_t ninit = (int64_t)(p->batched ? p->nseg : 1) * nimg;
   cap_fr = std::max(cap_fr, ninit);
@@ -785,6 +802,9 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&hs, hc, sizeof(TravState));
     if (hs.abort) return FMM_E_TIMEOUT;
+    p->hw_m = std::max<int64_t>(p->hw_m, (int64_t)hs.need_m + hs.need_m / 8);
+    p->hw_p = std::max<int64_t>(p->hw_p, (int64_t)hs.need_p + hs.need_p / 8);
+    p->hw_fr = std::max<int64_t>(p->hw_fr, (int64_t)hs.need_f + hs.need_f / 8);
     if (hs.overflow) {  // grow to what was needed (x1.25) and run the traversal again
       cap_m = std::max<int64_t>(cap_m, (int64_t)hs.need_m + hs.need_m / 4 + 1024);
       cap_p = std::max<int64_t>(cap_p, (int64_t)hs.need_p + hs.need_p / 4 + 1024);
