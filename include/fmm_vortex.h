@@ -158,7 +158,7 @@ typedef struct {
   double ms_downward;
   double ms_p2p;
   double ms_total;
-  int64_t traversal_runs; /* traversal launches (> 1 when the lists outgrew their buffers) */
+  int64_t traversal_runs; /* traversal launches (> 1 when a level outgrew the buffers) */
 } fmm_stats;
 
 /* Fill *prm with defaults: p=10, theta=0.4, ncrit=64, free space, images=3,
@@ -524,9 +524,10 @@ int64_t fmm_kernel_launch_count(void);
 /*
  * Starting capacities (entries) of the traversal's buffers for the plan's
  * next evaluations: the frontier, the M2L pairs and the P2P pairs (0: sized
- * from the cell count, the default).  The traversal runs all levels in one
- * launch; when a list would outgrow its buffer the launch stops, the buffers
- * grow to what it reported and the traversal runs again
+ * from the cell count and what the plan's earlier evaluations needed, the
+ * default).  The traversal runs all levels in one launch; when a level's
+ * output would outgrow a buffer the launch stops before writing it, the
+ * buffers grow (contents kept) and a new launch resumes at that level
  * (fmm_stats.traversal_runs counts the launches).  Small values exercise
  * that path.  FMM_E_INVAL for a negative value.
  */

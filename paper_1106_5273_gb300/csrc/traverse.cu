@@ -156,9 +156,11 @@ __device__ inline void split_of(const TravArgs& t, int a, int b, bool& split_a, 
 // the same order as the level-by-level kernels above (item order, children in
 // digit order), with no host round trip per level.  Every block is resident
 // (cooperative launch); each barrier wait is bounded and gives up with
-// FMM_E_TIMEOUT.  When a list would outgrow its buffer the blocks stop
-// together and report what they needed (the host grows the buffers and runs
-// the traversal again).
+// FMM_E_TIMEOUT.  When a level's output would outgrow a buffer the blocks
+// stop together before writing it and save where they are (the lists so far
+// and that level's frontier stay in place); the host grows the buffers,
+// keeping their contents, and relaunches the kernel, which resumes at that
+// level.
 
 constexpr int kTravThreads = 256;
 constexpr int kTravMaxIter = 128;         // > 2 x the 22 levels a pair can descend
@@ -167,7 +169,7 @@ constexpr long long kGridSpin = 1ll << 24;
 // state[]: 0 nm, 1 np, 2 nf, 3 overflow, 4 need_m, 5 need_p, 6 need_f, 7 iterations,
 // 8 barrier arrivals, 9 barrier generation, 10 abort
 struct TravState {
-  uint32_t nm, np, nf, overflow, need_m, need_p, need_f, iters, bar_count, bar_gen, abort;
+  uint32_t nm, np, nf, cur_b, overflow, need_m, need_p, need_f, iters, bar_count, bar_gen, abort;
 };
 
 __device__ bool grid_barrier(TravState* st, unsigned nblocks) {
@@ -229,16 +231,17 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
                                                             const uint32_t* __restrict__ cnt0, int4* __restrict__ m2l,
                                                             int4* __restrict__ p2p, uint32_t* __restrict__ mask,
                                                             uint32_t* __restrict__ blk, TravState* st, uint32_t cap_fr,
-                                                            uint32_t cap_m, uint32_t cap_p) {
+                                                            uint32_t cap_m, uint32_t cap_p, int resume) {
   __shared__ uint32_t red[3][kTravThreads / 32];
   __shared__ uint32_t bases[6];
   const unsigned G = gridDim.x, b = blockIdx.x;
-  uint32_t nm = cnt0[0], np = cnt0[1], nf = cnt0[2];
-  bool over_m = false, over_p = false, over_f = false;
-  uint32_t need_f = nf;
-  int4* cur = frA;
-  int4* nxt = frB;
-  int iter = 0;
+  // first launch: the initial pairs of k_trav_init; a resumed launch: the saved state
+  uint32_t nm = resume ? st->nm : cnt0[0], np = resume ? st->np : cnt0[1], nf = resume ? st->nf : cnt0[2];
+  const bool start_b = resume && st->cur_b;
+  int iter = resume ? (int)st->iters : 0;
+  int4* cur = start_b ? frB : frA;
+  int4* nxt = start_b ? frA : frB;
+  bool stopped = false;
   for (; nf > 0 && iter < kTravMaxIter; ++iter) {
     const uint32_t chunk = (nf + G - 1) / G;
     const uint32_t i0 = min(nf, b * chunk), i1 = min(nf, i0 + chunk);
@@ -295,16 +298,16 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
     }
     __syncthreads();
     const uint32_t tm = bases[3], tp = bases[4], tf = bases[5];
-    // every block sees the same totals, so they all take the same decisions:
-    // a full M2L or P2P list stops being written but is still counted to the
-    // end (the rerun then needs one growth); a full frontier stops the loop
-    if ((uint64_t)nm + tm > cap_m) over_m = true;
-    if ((uint64_t)np + tp > cap_p) over_p = true;
-    need_f = max(need_f, tf);
-    if (tf > cap_fr) {
-      over_f = true;
-      nm += tm;
-      np += tp;
+    // every block sees the same totals, so they all stop here together when a
+    // buffer is too small for this level's output (nothing of it written yet)
+    if ((uint64_t)nm + tm > cap_m || (uint64_t)np + tp > cap_p || tf > cap_fr) {
+      if (b == 0 && threadIdx.x == 0) {
+        st->overflow = 1u;
+        st->need_m = nm + tm;
+        st->need_p = np + tp;
+        st->need_f = tf;
+      }
+      stopped = true;
       break;
     }
     // phase B: emit in item order
@@ -330,15 +333,9 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
           const int ch = c0 + (int)q;
           const int4 val = sa ? make_int4(ch, pr.y, pr.z, 0) : make_int4(pr.x, ch, pr.z, 0);
           const uint32_t ty = (msk >> (2 * q)) & 3u;
-          if (ty == 0) {
-            if (!over_m) m2l[im] = val;
-            ++im;
-          } else if (ty == 1) {
-            if (!over_p) p2p[ip] = val;
-            ++ip;
-          } else {
-            nxt[iff++] = val;
-          }
+          if (ty == 0) m2l[im++] = val;
+          else if (ty == 1) p2p[ip++] = val;
+          else nxt[iff++] = val;
         }
       }
 #pragma unroll
@@ -352,15 +349,13 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
     nxt = sw;
     if (!grid_barrier(st, G)) return;
   }
-  if (b == 0 && threadIdx.x == 0) {
+  if (b == 0 && threadIdx.x == 0) {  // where the lists stand (and, if stopped, where to resume)
     st->nm = nm;
     st->np = np;
-    st->nf = over_f ? 0u : nf;
+    st->nf = nf;
+    st->cur_b = cur == frB ? 1u : 0u;
     st->iters = (uint32_t)iter;
-    st->overflow = (over_m || over_p || over_f) ? 1u : 0u;
-    st->need_m = nm;
-    st->need_p = np;
-    st->need_f = need_f;
+    if (!stopped) st->overflow = 0u;
   }
 }
 
@@ -749,10 +744,11 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   uint32_t* dcnt = reinterpret_cast<uint32_t*>(p->scal.as<double>() + kScalCount);
 
   // Frontier loop: one cooperative launch for all levels; the host reads the
-  // list sizes once.  Buffers too small for the lists are grown to what the
-  // kernel reports and the traversal runs again.
-  // starting capacities: from the cell count, at least what the plan's earlier
-  // evaluations needed (so a plan that saw its problem once does not rerun)
+  // list sizes once.  A launch that stops because a buffer is too small is
+  // resumed after the buffers grew (their contents kept).
+  // Starting capacities: from the cell count, at least what the plan's
+  // earlier evaluations needed (so a plan that saw its problem once runs one
+  // launch).
   int64_t cap_fr = p->cap_fr0 > 0 ? p->cap_fr0 : std::max<int64_t>({1024, 16 * (int64_t)nc, p->hw_fr});
   int64_t cap_m = p->cap_m0 > 0 ? p->cap_m0 : std::max<int64_t>({1024, 64 * (int64_t)nc, p->hw_m});
   int64_t cap_p = p->cap_p0 > 0 ? p->cap_p0 : std::max<int64_t>({1024, 32 * (int64_t)nc, p->hw_p});
@@ -770,23 +766,22 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     grid_blocks[dev] = std::max(1, sms * std::min(per_sm, 4));
   }
   const unsigned G = (unsigned)grid_blocks[dev];
+  FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
+  FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
+  FMM_TRY(p->m2l_raw.ensure(cap_m * sizeof(int4)));
+  FMM_TRY(p->p2p_raw.ensure(cap_p * sizeof(int4)));
+  FMM_TRY(p->tmask.ensure(cap_fr * sizeof(uint32_t)));
+  FMM_TRY(p->tscan0.ensure((size_t)(3 * G + 8) * sizeof(uint32_t)));
+  FMM_TRY(p->tscan1.ensure(sizeof(TravState) + 64));
+  TravState* dst = p->tscan1.as<TravState>();
+  FMM_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), s));
+  ++g_launches;
+  k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(),
+                                 p->p2p_raw.as<int4>(), dcnt);
   int64_t nm = 0, np = 0;
-  TravState* dst = nullptr;
-  for (int attempt = 0;; ++attempt) {
-    p->trav_runs = attempt + 1;
-    if (attempt > 4 || cap_fr > 0x7fffffff || cap_m > 0x7fffffff || cap_p > 0x7fffffff) return FMM_E_CAPACITY;
-    FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
-    FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
-    FMM_TRY(p->m2l_raw.ensure(cap_m * sizeof(int4)));
-    FMM_TRY(p->p2p_raw.ensure(cap_p * sizeof(int4)));
-    FMM_TRY(p->tmask.ensure(cap_fr * sizeof(uint32_t)));
-    FMM_TRY(p->tscan0.ensure((size_t)(3 * G + 8) * sizeof(uint32_t)));
-    FMM_TRY(p->tscan1.ensure(sizeof(TravState) + 64));
-    dst = p->tscan1.as<TravState>();
-    FMM_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), s));
-    ++g_launches;
-    k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(),
-                                   p->p2p_raw.as<int4>(), dcnt);
+  for (int launch = 0;; ++launch) {
+    p->trav_runs = launch + 1;
+    if (launch > 64) return FMM_E_CAPACITY;
     int4* a0 = p->fr0.as<int4>();
     int4* a1 = p->fr1.as<int4>();
     int4* am = p->m2l_raw.as<int4>();
@@ -794,7 +789,8 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     uint32_t* msk = p->tmask.as<uint32_t>();
     uint32_t* blk = p->tscan0.as<uint32_t>();
     uint32_t cf = (uint32_t)cap_fr, cm = (uint32_t)cap_m, cp = (uint32_t)cap_p;
-    void* args[] = {&ta, &a0, &a1, &dcnt, &am, &ap, &msk, &blk, &dst, &cf, &cm, &cp};
+    int resume = launch > 0 ? 1 : 0;
+    void* args[] = {&ta, &a0, &a1, &dcnt, &am, &ap, &msk, &blk, &dst, &cf, &cm, &cp, &resume};
     ++g_launches;
     FMM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_trav_loop, dim3(G), dim3(kTravThreads), args, 0, s));
     TravState hs;
@@ -802,13 +798,17 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     FMM_CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&hs, hc, sizeof(TravState));
     if (hs.abort) return FMM_E_TIMEOUT;
-    p->hw_m = std::max<int64_t>(p->hw_m, (int64_t)hs.need_m + hs.need_m / 8);
-    p->hw_p = std::max<int64_t>(p->hw_p, (int64_t)hs.need_p + hs.need_p / 8);
-    p->hw_fr = std::max<int64_t>(p->hw_fr, (int64_t)hs.need_f + hs.need_f / 8);
-    if (hs.overflow) {  // grow to what was needed (x1.25) and run the traversal again
-      cap_m = std::max<int64_t>(cap_m, (int64_t)hs.need_m + hs.need_m / 4 + 1024);
-      cap_p = std::max<int64_t>(cap_p, (int64_t)hs.need_p + hs.need_p / 4 + 1024);
-      cap_fr = std::max<int64_t>(cap_fr, (int64_t)hs.need_f + hs.need_f / 4 + 1024);
+    if (hs.overflow) {  // grow what was too small (x1.25, contents kept) and resume
+      if ((int64_t)hs.need_m > cap_m) cap_m = (int64_t)hs.need_m + hs.need_m / 4 + 1024;
+      if ((int64_t)hs.need_p > cap_p) cap_p = (int64_t)hs.need_p + hs.need_p / 4 + 1024;
+      if ((int64_t)hs.need_f > cap_fr) cap_fr = (int64_t)hs.need_f + hs.need_f / 4 + 1024;
+      if (cap_fr > 0x7fffffff || cap_m > 0x7fffffff || cap_p > 0x7fffffff) return FMM_E_CAPACITY;
+      FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int4), s));
+      FMM_TRY(p->p2p_raw.grow_copy(cap_p * sizeof(int4), s));
+      FMM_TRY(p->fr0.grow_copy(cap_fr * sizeof(int4), s));
+      FMM_TRY(p->fr1.grow_copy(cap_fr * sizeof(int4), s));
+      FMM_TRY(p->tmask.ensure(cap_fr * sizeof(uint32_t)));
+      FMM_CUDA_TRY(cudaMemsetAsync(&dst->overflow, 0, sizeof(uint32_t), s));
       continue;
     }
     if (hs.nf != 0) return FMM_E_CAPACITY;  // deeper than kTravMaxIter levels of the frontier
@@ -816,6 +816,9 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     np = hs.np;
     break;
   }
+  p->hw_m = std::max<int64_t>(p->hw_m, nm + nm / 8);
+  p->hw_p = std::max<int64_t>(p->hw_p, np + np / 8);
+  p->hw_fr = std::max<int64_t>(p->hw_fr, cap_fr);
   p->n_m2l = nm;
   p->n_p2p = np;
 
