@@ -167,16 +167,18 @@ def p2p_roofline(st, p2p_ms, traffic=None):
 
 
 def m2l_roofline(st, p):
-    """Tensor roofline of the M2L phase: useful flops = 3 BF16 products x 2 P^2 x 3 components
-    per M2L pair; peak = the dense BF16 rate."""
+    """Tensor roofline of the M2L phase: the products issued per M2L pair are
+    2 P x 3 components x (3 K3 + (P - K3)), K3 = the source coefficients that take
+    all three split products (the rest take hi x hi only); peak = the dense BF16 rate."""
     P = int(p) ** 2
     if not (st.ms_m2l > 0 and st.m2l_tensor):
         return None
     peak, src = bf16_peak()
-    ach = 3 * 2.0 * P * P * 3 * st.m2l_pairs / (st.ms_m2l * 1e-3) / 1e12
+    k3 = int(st.m2l_split_coefs) or P
+    ach = 2.0 * P * 3 * (3 * k3 + (P - k3)) * st.m2l_pairs / (st.ms_m2l * 1e-3) / 1e12
     return {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "peak_source": src, "ms": st.ms_m2l,
-            "flops": "3 BF16 products x 2 P^2 x 3 components per M2L pair (useful rows only)"}
+            "frac": ach / peak, "peak_source": src, "ms": st.ms_m2l, "split_coefs": k3,
+            "flops": "2 P x 3 components x (3 K3 + (P - K3)) per M2L pair (useful rows only)"}
 
 
 PHASES = ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l", "ms_downward", "ms_p2p", "ms_total")

@@ -61,7 +61,13 @@ enum {
    * the translations and (tile, translation) bins whenever those tables are
    * small (compact keys of <= 22 bits, <= 2^28 bins), else from the sort.
    * Both give the same steps in the same order. */
-  FMM_M2L_SORT_STEPS = 8
+  FMM_M2L_SORT_STEPS = 8,
+  /* Flag, OR'ed with FMM_M2L_AUTO / _TENSOR: every K chunk of the BF16 M2L
+   * takes the three split products.  Without it, for theta <= 0.42, source
+   * degrees >= 8 take the hi x hi product only: under the MAC their terms
+   * are at most theta^8 / (1 - theta) of the leading one, so that adds at
+   * most 7e-6 of it (fmm_stats.m2l_split_coefs reports which). */
+  FMM_M2L_FULL_SPLIT = 16
 };
 
 /* fmm_params.split_tie: the cell Algorithm 1 splits when the pair's cells are
@@ -99,7 +105,7 @@ typedef struct fmm_plan_s* fmm_plan;
  *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
  *              output pointer skips that output.
  *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR / _TENSOR_TF32, optionally
- *              | FMM_M2L_SORT_STEPS.
+ *              | FMM_M2L_SORT_STEPS and | FMM_M2L_FULL_SPLIT.
  *   p2p_pair_max  two leaves whose particle counts multiply to at most this
  *              do P2P even when the MAC would accept M2L (the cost rule for
  *              cells of "very few particles", Alg. 2); 0 (default): the MAC
@@ -159,6 +165,8 @@ typedef struct {
   double ms_p2p;
   double ms_total;
   int64_t traversal_runs; /* traversal launches (> 1 when a level outgrew the buffers) */
+  int64_t m2l_split_coefs; /* tensor-core M2L: source coefficients (of P) that take all
+                              three split products; the rest take hi x hi only */
 } fmm_stats;
 
 /* Fill *prm with defaults: p=10, theta=0.4, ncrit=64, free space, images=3,

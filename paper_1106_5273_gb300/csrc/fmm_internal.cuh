@@ -213,6 +213,19 @@ __host__ __device__ inline int m2l_kstep(int kind) { return kind ? 8 : 16; }
 __host__ __device__ inline int m2l_kchunks(int P, int kind = 0) {
   return ((P + m2l_kstep(kind) - 1) / m2l_kstep(kind) + 3) / 4;
 }
+// K chunks of the BF16 tensor-core M2L that take all three split products.
+// Under the MAC (R_A + R_B < theta |X_A - X_B|) the M2L terms of source
+// degree j sum to at most theta^j / (1 - theta) of the leading 1/|X_A - X_B|
+// term.  BF16 chunks from the second on hold degrees >= 8 (64 coefficients
+// per chunk), so one hi x hi product there (relative error <= 2^-8) adds at
+// most 2^-8 theta^8 / (1 - theta) of the leading term: <= 7e-6 for
+// theta <= 0.42, whose theta^8 <= 2^-10.  Otherwise, and for TF32, every
+// chunk takes three products.
+__host__ __device__ inline int m2l_split_chunks(int P, int kind, float theta, bool full) {
+  const int nkc = m2l_kchunks(P, kind);
+  const float t2 = theta * theta, t8 = t2 * t2 * t2 * t2;
+  return (kind == 0 && !full && t8 <= 1.0f / 1024.0f) ? 1 : nkc;
+}
 // Blocks of 128 output rows (one MMA M) covering P outputs.
 __host__ __device__ inline int m2l_rowblocks(int P) { return (P + 127) / 128; }
 

@@ -8,7 +8,10 @@
 // the slot's source for that potential component (zero if the slot has no
 // source under this translation).  T = T_hi + T_lo and B = B_hi + B_lo in
 // BF16; D accumulates T_hi B_hi + T_hi B_lo + T_lo B_hi (the lo.lo term is
-// below FP32 resolution of the sum).  D lives in TMEM for all steps of the
+// below FP32 resolution of the sum).  The K chunks from m2l_split_chunks on
+// (source degrees 8 and up) take T_hi B_hi only: under the MAC their terms
+// are at most theta^8 / (1 - theta) of the leading one, which keeps the
+// 2^-8 error of one BF16 product there under 7e-6 for theta <= 0.42.  D lives in TMEM for all steps of the
 // tile; each target local expansion is written once.  P > 128 output rows
 // take a second CTA per tile (blockIdx.y = block of 128 rows), which gathers
 // the same B and its own rows of T.
@@ -159,7 +162,8 @@ template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2)
     k_m2l_tc(const int2* __restrict__ tile_range, const int4* __restrict__ items, const uint32_t* __restrict__ nitems,
              const int* __restrict__ tfirst, const int* __restrict__ st_slot, const int* __restrict__ st_src,
-             const uint8_t* __restrict__ Tb, const uint8_t* __restrict__ Mb, int P, int nkc, int ksteps_last, int nrh,
+             const uint8_t* __restrict__ Tb, const uint8_t* __restrict__ Mb, int P, int nkc, int nkc3, int ksteps_last,
+             int nrh,
              const int* __restrict__ tcell, float* __restrict__ L, float* __restrict__ partial,
              int* __restrict__ flag) {
   extern __shared__ uint8_t smem_raw[];
@@ -220,6 +224,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int stage = it % kStages;
       const uint32_t ph = (uint32_t)(it / kStages) & 1u;
       const int st = rg.x + it / nkc, kc = it % nkc;
+      const bool lo = kc < nkc3;  // chunks from nkc3 on take the hi.hi product only
       const int srcA = __ldg(st_src + (size_t)st * kTile + r0), srcB = __ldg(st_src + (size_t)st * kTile + r0 + 32);
       uint4 v[kGather];
 #pragma unroll
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int h = q / 6, k = q % 6;
         const int src = (k & 1) ? srcB : srcA;
         v[q] = make_uint4(0u, 0u, 0u, 0u);
-        if (src >= 0)
+        if (src >= 0 && (h == 0 || lo))
           v[q] = __ldg(reinterpret_cast<const uint4*>(Mb + ((((size_t)src * 2 + h) * 3 + (k >> 1)) * nkc + kc) * 128) +
                        j);
       }
@@ -235,8 +240,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int q = 0; q < kGather; ++q) {
         const int h = q / 6, n = r0 + 32 * (q % 6);
-        *reinterpret_cast<uint4*>(smem + stage * kStageBytes + 2 * kABytes + h * kBBytes + n * 128 +
-                                  ((j ^ (n & 7)) << 4)) = v[q];
+        if (h == 0 || lo)
+          *reinterpret_cast<uint4*>(smem + stage * kStageBytes + 2 * kABytes + h * kBBytes + n * 128 +
+                                    ((j ^ (n & 7)) << 4)) = v[q];
       }
       fence_proxy_async();
       mbar_arrive(fullB(stage));
@@ -258,9 +264,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       const uint8_t* hi = Tb + ((key * 2 + 0) * nkc + kc) * chunk + row0;
       const uint8_t* lo = Tb + ((key * 2 + 1) * nkc + kc) * chunk + row0;
       const uint32_t a0 = sbase + stage * kStageBytes;
-      mbar_arrive_tx(fullA(stage), 2 * abytes);
+      const bool with_lo = kc < nkc3;
+      mbar_arrive_tx(fullA(stage), with_lo ? 2 * abytes : abytes);
       bulk_g2s(a0, hi, abytes, fullA(stage));
-      bulk_g2s(a0 + kABytes, lo, abytes, fullA(stage));
+      if (with_lo) bulk_g2s(a0 + kABytes, lo, abytes, fullA(stage));
       issued = it + 1;
       return true;
     };
@@ -290,11 +297,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int ks = (kc == nkc - 1) ? ksteps_last : 4;
       const uint32_t a_hi = sbase + stage * kStageBytes, a_lo = a_hi + kABytes;
       const uint32_t b_hi = a_hi + 2 * kABytes, b_lo = b_hi + kBBytes;
+      const bool three = kc < nkc3;
       for (int kk = 0; kk < ks; ++kk) {
         const uint32_t off = (uint32_t)kk * 32u;
         umma<KIND>(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (it > 0 || kk > 0) ? 1u : 0u);
-        umma<KIND>(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
-        umma<KIND>(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+        if (three) {
+          umma<KIND>(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+          umma<KIND>(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+        }
       }
       umma_commit(empty(stage));
     }
@@ -411,6 +421,7 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   const int ksteps = (p->P + m2l_kstep(kind) - 1) / m2l_kstep(kind);
   const int nkc = m2l_kchunks(p->P, kind);
   const int last = ksteps - 4 * (nkc - 1);
+  const int nkc3 = m2l_split_chunks(p->P, kind, p->prm.theta, p->prm.m2l_mode & FMM_M2L_FULL_SPLIT);
   const size_t sh = (size_t)kBarOff + 128 + 1024;
   static bool attr_set[2] = {false, false};
   if (!attr_set[kind]) {
@@ -463,12 +474,12 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   if (kind)
     k_m2l_tc<1><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
                                          p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
-                                         p->Mbf.as<uint8_t>(), p->P, nkc, last, nrh, p->tile_cells.as<int>(),
+                                         p->Mbf.as<uint8_t>(), p->P, nkc, nkc3, last, nrh, p->tile_cells.as<int>(),
                                          p->L.as<float>(), p->m2l_partial.as<float>(), p->flags.as<int>());
   else
     k_m2l_tc<0><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
                                          p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
-                                         p->Mbf.as<uint8_t>(), p->P, nkc, last, nrh, p->tile_cells.as<int>(),
+                                         p->Mbf.as<uint8_t>(), p->P, nkc, nkc3, last, nrh, p->tile_cells.as<int>(),
                                          p->L.as<float>(), p->m2l_partial.as<float>(), p->flags.as<int>());
   FMM_CUDA_TRY(cudaGetLastError());
   if (items) {

@@ -8,6 +8,8 @@
   FP32x2 for ncrit > 32, one target per lane otherwise) against the FP64
   oracle FMM on identical lists: rel-L2 within TOL_U / TOL_S, and every
   target within PT_U / PT_S of its own magnitude (per_target_error).
+* The single-product K chunks (theta <= 0.42, source degrees >= 8) against
+  three products in every chunk: within their stated bound.
 * The per-p accuracy gates against the FP64 direct sum (Eqs. 1-3) on the
   4096-blob jittered lattice (theta = 0.5, ncrit = 32, free space), p = 4 ..
   12: GATES[p] = 1.5 x the FP64 oracle FMM's own error at that p (the method
@@ -156,6 +158,30 @@ def test_tensor_m2l_plummer_vs_oracle_fmm(p):
     print("Plummer p%d: rel-L2 u %.2e s %.2e, per-target u %.2e s %.2e" % (p, eu, es, pu, ps))
     assert eu < TOL_U and es < TOL_S
     assert pu < PT_U and ps < PT_S
+
+
+@pytest.mark.parametrize("name,p", [("taylor-green-16", 10), ("plummer-free", 12)])
+def test_single_product_chunks_within_their_bound(name, p):
+    """At theta <= 0.42 the BF16 M2L takes one product (hi x hi) for source
+    degrees >= 8; under the MAC those terms are at most theta^8 / (1 - theta)
+    of the leading one, so the change is at most 2^-8 x that (7e-6 at theta
+    0.4) of the far field.  Against the same lists with three products in every
+    chunk (FMM_M2L_FULL_SPLIT): the difference stays under that bound, and both
+    stay within TOL_U / TOL_S of the FP64 oracle FMM."""
+    from paper_1106_5273_gb300 import FMM_M2L_FULL_SPLIT
+    w, (_, _, ncrit) = _case(name)
+    theta = 0.4
+    pa, ua, sa = run_fmm(w, p, theta, ncrit, m2l_mode=2)
+    pb, ub, sb = run_fmm(w, p, theta, ncrit, m2l_mode=2 | FMM_M2L_FULL_SPLIT)
+    assert pa.stats().m2l_split_coefs == 64 and pb.stats().m2l_split_coefs == p * p
+    bound = 2.0 ** -8 * theta ** 8 / (1 - theta)
+    du, ds = rel_l2(ua, ub), rel_l2(sa, sb)
+    ref = _oracle_fmm(w, p, theta, ncrit)
+    print("%s p%d: single vs split products u %.2e s %.2e (bound %.1e); vs oracle u %.2e / %.2e" % (
+        name, p, du, ds, bound, rel_l2(ua, ref.u), rel_l2(ub, ref.u)))
+    assert du <= bound and ds <= bound
+    for u, s in ((ua, sa), (ub, sb)):
+        assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
 
 
 @pytest.fixture(scope="module")
