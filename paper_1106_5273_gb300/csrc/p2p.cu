@@ -654,59 +654,68 @@ struct TgtT2 {
   float2 mx, my, mz, ngx, ngy, ngz;
 };
 
+// One staged source (v0..v4) against the two targets of one FP32x2 chain.
+// self_lo / self_hi: the staged index of each target itself (self pair
+// skipped), or -1.
+template <int MODE, bool SELF, int ST>
+__device__ __forceinline__ void pair_x2(const float4& v0, const float4& v1, const float4& v2, const float4& v3,
+                                        const float2& v4, int j, float2 tx, float2 ty, float2 tz, float2 gix,
+                                        float2 giy, float2 giz, const TgtT2& tt, int self_lo, int self_hi,
+                                        const SigK2& K, AccR2& a) {
+  const float2 dx = add2(tx, make_float2(v0.x, v0.y));
+  const float2 dy = add2(ty, make_float2(v0.z, v0.w));
+  const float2 dz = add2(tz, make_float2(v1.x, v1.y));
+  const float2 gjx = make_float2(v1.z, v1.w), gjy = make_float2(v2.x, v2.y), gjz = make_float2(v2.z, v2.w);
+  const float2 kjx = make_float2(v3.x, v3.y), kjy = make_float2(v3.z, v3.w), kjz = v4;
+  const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  float2 S, T;
+  pair_ST2<MODE, ST>(r2, K, S, T);
+  float2 td = dup2(0.f);
+  if (ST == 1) td = mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz))));
+  if (ST == 2)
+    td = mul2(T, fma2(tt.ngz, kjz, fma2(tt.ngy, kjy, fma2(tt.ngx, kjx, fma2(gjx, tt.mx, fma2(gjy, tt.my,
+                                                                                          mul2(gjz, tt.mz)))))));
+  if (SELF) {
+    if (j == self_lo) {
+      S.x = 0.f;
+      td.x = 0.f;
+    }
+    if (j == self_hi) {
+      S.y = 0.f;
+      td.y = 0.f;
+    }
+  }
+  a.ax = fma2(S, gjx, a.ax);
+  a.ay = fma2(S, gjy, a.ay);
+  a.az = fma2(S, gjz, a.az);
+  a.bx = fma2(S, kjx, a.bx);
+  a.by = fma2(S, kjy, a.by);
+  a.bz = fma2(S, kjz, a.bz);
+  if (ST == 0) return;
+  if (ST == 2) {  // td holds w
+    a.cx = add2(a.cx, td);
+    a.dx = fma2(td, make_float2(v0.x, v0.y), a.dx);
+    a.dy = fma2(td, make_float2(v0.z, v0.w), a.dy);
+    a.dz = fma2(td, make_float2(v1.x, v1.y), a.dz);
+    return;
+  }
+  a.cx = fma2(td, gjx, a.cx);
+  a.cy = fma2(td, gjy, a.cy);
+  a.cz = fma2(td, gjz, a.cz);
+  a.dx = fma2(td, kjx, a.dx);
+  a.dy = fma2(td, kjy, a.dy);
+  a.dz = fma2(td, kjz, a.dz);
+}
+
 template <int MODE, bool SELF, int ST>
 __device__ __forceinline__ void run_chunk_x2(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
                                              const float2* s4, int jb, int je, float2 tx, float2 ty, float2 tz,
                                              float2 gix, float2 giy, float2 giz, const TgtT2& tt, int self_lo,
                                              int self_hi, const SigK2& K, AccR2& a) {
 #pragma unroll 4
-  for (int j = jb; j < je; ++j) {
-    const float4 v0 = s0[j], v1 = s1[j], v2 = s2[j], v3 = s3[j];
-    const float2 v4 = s4[j];
-    const float2 dx = add2(tx, make_float2(v0.x, v0.y));
-    const float2 dy = add2(ty, make_float2(v0.z, v0.w));
-    const float2 dz = add2(tz, make_float2(v1.x, v1.y));
-    const float2 gjx = make_float2(v1.z, v1.w), gjy = make_float2(v2.x, v2.y), gjz = make_float2(v2.z, v2.w);
-    const float2 kjx = make_float2(v3.x, v3.y), kjy = make_float2(v3.z, v3.w), kjz = v4;
-    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-    float2 S, T;
-    pair_ST2<MODE, ST>(r2, K, S, T);
-    float2 td = dup2(0.f);
-    if (ST == 1) td = mul2(T, fma2(gix, dx, fma2(giy, dy, mul2(giz, dz))));
-    if (ST == 2)
-      td = mul2(T, fma2(tt.ngz, kjz, fma2(tt.ngy, kjy, fma2(tt.ngx, kjx, fma2(gjx, tt.mx, fma2(gjy, tt.my,
-                                                                                            mul2(gjz, tt.mz)))))));
-    if (SELF) {
-      if (j == self_lo) {
-        S.x = 0.f;
-        td.x = 0.f;
-      }
-      if (j == self_hi) {
-        S.y = 0.f;
-        td.y = 0.f;
-      }
-    }
-    a.ax = fma2(S, gjx, a.ax);
-    a.ay = fma2(S, gjy, a.ay);
-    a.az = fma2(S, gjz, a.az);
-    a.bx = fma2(S, kjx, a.bx);
-    a.by = fma2(S, kjy, a.by);
-    a.bz = fma2(S, kjz, a.bz);
-    if (ST == 0) continue;
-    if (ST == 2) {  // td holds w
-      a.cx = add2(a.cx, td);
-      a.dx = fma2(td, make_float2(v0.x, v0.y), a.dx);
-      a.dy = fma2(td, make_float2(v0.z, v0.w), a.dy);
-      a.dz = fma2(td, make_float2(v1.x, v1.y), a.dz);
-      continue;
-    }
-    a.cx = fma2(td, gjx, a.cx);
-    a.cy = fma2(td, gjy, a.cy);
-    a.cz = fma2(td, gjz, a.cz);
-    a.dx = fma2(td, kjx, a.dx);
-    a.dy = fma2(td, kjy, a.dy);
-    a.dz = fma2(td, kjz, a.dz);
-  }
+  for (int j = jb; j < je; ++j)
+    pair_x2<MODE, SELF, ST>(s0[j], s1[j], s2[j], s3[j], s4[j], j, tx, ty, tz, gix, giy, giz, tt, self_lo, self_hi,
+                            K, a);
 }
 
 // k_p2p for a uniform core width and two targets per lane, in the packed

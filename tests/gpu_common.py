@@ -14,7 +14,7 @@ def to_dev(a):
 
 
 def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=None, images=None, outputs=None,
-            sigma_rule=None, p2p_pair_max=None, split_tie=None):
+            sigma_rule=None, p2p_pair_max=None, split_tie=None, p2p_tpl=None, stretching=True):
     import torch
     from paper_1106_5273_gb300 import Plan, Params
     pos, gam = w["pos"], w["gamma"]
@@ -31,12 +31,15 @@ def run_fmm(w, p=None, theta=None, ncrit=None, m2l_mode=0, ksig=5.0, sigma_arr=N
         kw.update(p2p_pair_max=p2p_pair_max)
     if split_tie is not None:
         kw.update(split_tie=split_tie)
+    if p2p_tpl is not None:
+        kw.update(p2p_tpl=p2p_tpl)
     plan = Plan(max(n, 1), Params.default(**kw))
     dp, dg = to_dev(pos), to_dev(gam)
     ds = to_dev(sigma_arr) if sigma_arr is not None else None
-    u, s = plan.eval(dp, dg, sigma=ds, sigma_uniform=float(w["sigma"]))
+    u, s = plan.eval(dp, dg, sigma=ds, sigma_uniform=float(w["sigma"]), stretching=stretching)
     torch.cuda.synchronize()
-    return plan, u.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+    s = s.cpu().numpy().astype(np.float64) if s is not None else None
+    return plan, u.cpu().numpy().astype(np.float64), s
 
 
 def per_target_error(a, ref, floor=0.1):
