@@ -183,6 +183,7 @@ def m2l_roofline(st, p):
 
 PHASES = ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l", "ms_downward", "ms_p2p", "ms_total")
 WORK = ("ncells", "nleaves", "nlevels", "p2p_cell_pairs", "p2p_pairs", "m2l_pairs", "m2l_steps", "m2l_keys",
+        "m2l_split_coefs", "m2l_stage_chunks",
         "m2l_built", "m2l_tensor")
 
 

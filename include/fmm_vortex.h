@@ -67,7 +67,12 @@ enum {
    * degrees >= 8 take the hi x hi product only: under the MAC their terms
    * are at most theta^8 / (1 - theta) of the leading one, so that adds at
    * most 7e-6 of it (fmm_stats.m2l_split_coefs reports which). */
-  FMM_M2L_FULL_SPLIT = 16
+  FMM_M2L_FULL_SPLIT = 16,
+  /* Flag: one K chunk per pipeline stage of the BF16 M2L.  Without it a step
+   * of two K chunks whose second takes one product (p = 9, 10 at theta <=
+   * 0.42) runs as one stage; the MMAs are the same, in the same order, so
+   * the results are the same bit for bit. */
+  FMM_M2L_CHUNK_STAGES = 32
 };
 
 /* fmm_params.split_tie: the cell Algorithm 1 splits when the pair's cells are
@@ -105,7 +110,7 @@ typedef struct fmm_plan_s* fmm_plan;
  *              | FMM_OUT_STRETCHING_TRANSPOSE (the stretching scheme); a NULL
  *              output pointer skips that output.
  *   m2l_mode   FMM_M2L_AUTO / _SIMT / _TENSOR / _TENSOR_TF32, optionally
- *              | FMM_M2L_SORT_STEPS and | FMM_M2L_FULL_SPLIT.
+ *              | FMM_M2L_SORT_STEPS, | FMM_M2L_FULL_SPLIT, | FMM_M2L_CHUNK_STAGES.
  *   p2p_pair_max  two leaves whose particle counts multiply to at most this
  *              do P2P even when the MAC would accept M2L (the cost rule for
  *              cells of "very few particles", Alg. 2); 0 (default): the MAC
@@ -167,6 +172,8 @@ typedef struct {
   int64_t traversal_runs; /* traversal launches (> 1 when a level outgrew the buffers) */
   int64_t m2l_split_coefs; /* tensor-core M2L: source coefficients (of P) that take all
                               three split products; the rest take hi x hi only */
+  int64_t m2l_stage_chunks; /* tensor-core M2L: K chunks per pipeline stage (1, or 2
+                               when a whole step runs as one stage) */
 } fmm_stats;
 
 /* Fill *prm with defaults: p=10, theta=0.4, ncrit=64, free space, images=3,

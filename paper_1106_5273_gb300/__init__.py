@@ -12,7 +12,7 @@ works before the library exists; using the binding without the library
 raises ImportError (there is no fallback).
 """
 __all__ = ["Params", "Plan", "Stats", "FmmError", "direct", "lib", "library_path", "kernel_launch_count", "morton_order_noalloc", "NOALLOC_MAX_N", "BATCH_MAX", "BATCH_DEPTH", "Server", "ServerParams",
-           "FMM_M2L_AUTO", "FMM_M2L_SIMT", "FMM_M2L_TENSOR", "FMM_M2L_SORT_STEPS", "FMM_M2L_FULL_SPLIT", "FMM_SIGMA_SOURCE", "FMM_SIGMA_MIXED",
+           "FMM_M2L_AUTO", "FMM_M2L_SIMT", "FMM_M2L_TENSOR", "FMM_M2L_SORT_STEPS", "FMM_M2L_FULL_SPLIT", "FMM_M2L_CHUNK_STAGES", "FMM_SIGMA_SOURCE", "FMM_SIGMA_MIXED",
            "FMM_OUT_VELOCITY", "FMM_OUT_STRETCHING", "FMM_OUT_STRETCHING_TRANSPOSE", "autotune_ncrit",
            "FMM_SPLIT_SOURCE", "FMM_SPLIT_TARGET", "Graph", "autotune_plan"]
 

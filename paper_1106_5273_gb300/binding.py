@@ -16,6 +16,7 @@ FMM_OK = 0
 FMM_M2L_AUTO, FMM_M2L_SIMT, FMM_M2L_TENSOR = 0, 1, 2
 FMM_M2L_SORT_STEPS = 8
 FMM_M2L_FULL_SPLIT = 16
+FMM_M2L_CHUNK_STAGES = 32
 FMM_SIGMA_SOURCE, FMM_SIGMA_MIXED = 0, 1
 FMM_SPLIT_SOURCE, FMM_SPLIT_TARGET = 0, 1
 FMM_OUT_VELOCITY, FMM_OUT_STRETCHING, FMM_OUT_STRETCHING_TRANSPOSE = 1, 2, 4
@@ -65,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("ms_upward", ctypes.c_double), ("ms_traverse", ctypes.c_double),
                 ("ms_m2l", ctypes.c_double), ("ms_downward", ctypes.c_double),
                 ("ms_p2p", ctypes.c_double), ("ms_total", ctypes.c_double), ("traversal_runs", ctypes.c_int64),
-                ("m2l_split_coefs", ctypes.c_int64)]
+                ("m2l_split_coefs", ctypes.c_int64), ("m2l_stage_chunks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -24,7 +24,7 @@ int check_params(const fmm_params* q) {
   if (q->periodic != 0 && q->periodic != 1) return FMM_E_INVAL;
   if (q->periodic && (q->images < 1 || q->images > 8 || !(q->box_len > 0.0))) return FMM_E_INVAL;
   if (!(q->sigma_sep >= 0.f)) return FMM_E_INVAL;
-  if (q->m2l_mode & ~(3 | FMM_M2L_SORT_STEPS | FMM_M2L_FULL_SPLIT)) return FMM_E_INVAL;
+  if (q->m2l_mode & ~(3 | FMM_M2L_SORT_STEPS | FMM_M2L_FULL_SPLIT | FMM_M2L_CHUNK_STAGES)) return FMM_E_INVAL;
   if (q->outputs & ~(FMM_OUT_VELOCITY | FMM_OUT_STRETCHING | FMM_OUT_STRETCHING_TRANSPOSE)) return FMM_E_INVAL;
   if (q->sigma_rule != FMM_SIGMA_SOURCE && q->sigma_rule != FMM_SIGMA_MIXED) return FMM_E_INVAL;
   if (q->p2p_pair_max < 0) return FMM_E_INVAL;
@@ -173,6 +173,7 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
                                                 m2l_split_chunks(p->P, p->tc_kind, p->prm.theta,
                                                                  p->prm.m2l_mode & FMM_M2L_FULL_SPLIT))
                   : 0;
+  st.m2l_stage_chunks = p->last_tc ? p->m2l_stage_chunks : 0;
   st.p2p_pairs_near = (int64_t)cls[0];
   st.p2p_pairs_mid = (int64_t)cls[1];
   st.p2p_pairs_far = (int64_t)cls[2];

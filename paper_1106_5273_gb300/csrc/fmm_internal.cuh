@@ -118,6 +118,7 @@ struct fmm_plan_s {
   int64_t n_p2p = 0, n_m2l = 0, n_keys = 0, n_steps = 0, p2p_pairs = 0;
   int64_t last_n = 0;
   int last_tc = 0;
+  int m2l_stage_chunks = 0;  // K chunks per stage of the last tensor-core M2L
   // tree reuse (fmm_eval_strengths): set by a successful full evaluation of
   // the plan's own particles; epoch counts full evaluations (a captured graph
   // is valid only within the epoch it was captured in)

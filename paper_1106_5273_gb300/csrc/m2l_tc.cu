@@ -25,7 +25,11 @@
 // CTA waits on its gathers and barriers the other's MMAs keep the tensor pipe
 // busy.  The producers load a stage's rows into registers before they wait
 // for its buffer.  Measured at 2M blobs: 5.6 ms, against 6.6 ms without the
-// early loads and 7.8 ms for two stages in one CTA per SM.  Every wait is
+// early loads and 7.8 ms for two stages in one CTA per SM.  When a step has
+// two K chunks and the second takes one product (p = 9, 10 at theta <= 0.42)
+// the stage holds the whole step instead (three operator blocks of the rows
+// below P and three B blocks, 111 KB at p = 10, still two CTAs per SM), so
+// the operator-copy latency is paid once per step.  Every wait is
 // bounded; on expiry the kernel records FMM_E_TIMEOUT, waits (bounded) for
 // its own bulk copies, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -158,7 +162,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // partial slot) of *nitems: a tile's steps in runs of at most S; a tile split
 // into several items writes each item's D to its partial slot, summed later
 // by k_m2l_combine.
-template <int KIND>
+template <int KIND, bool M2>
 __global__ void __launch_bounds__(kThreads, 2)
     k_m2l_tc(const int2* __restrict__ tile_range, const int4* __restrict__ items, const uint32_t* __restrict__ nitems,
              const int* __restrict__ tfirst, const int* __restrict__ st_slot, const int* __restrict__ st_src,
@@ -181,7 +185,17 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   const int rh = blockIdx.y;  // block of 128 output rows
   if (rg.y <= rg.x) return;  // no M2L for this tile: the whole CTA leaves before any barrier
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  // Only the operator rows below P are copied (whole 8-row swizzle groups):
+  // the rows above feed only output rows that the epilogue never stores.
+  const uint32_t arows = (uint32_t)min(128, ((P - rh * 128) + 7) & ~7);
+  const uint32_t abytes = arows * 128u;
+  // M2 (two K chunks, the second with one product, P <= 128): the stage holds
+  // a whole step, A buffers of abytes (chunk 0 hi, chunk 0 lo, chunk 1 hi;
+  // the MMA's rows past arows read the next buffer and feed discarded output
+  // rows) followed by the B buffers (chunk 0 hi, chunk 0 lo, chunk 1 hi).
+  const uint32_t abuf = M2 ? abytes : kABytes;
+  const uint32_t stage_bytes = M2 ? 3u * abuf + 3u * kBBytes : kStageBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + stage_bytes);
   // bars: fullA[2], fullB[2], empty[2], done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
   volatile int* abort = reinterpret_cast<volatile int*>(bars + 9);
@@ -212,9 +226,93 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int niter = (rg.y - rg.x) * nkc;
+  const int niter = M2 ? (rg.y - rg.x) : (rg.y - rg.x) * nkc;
 
-  if (warp < kProducerWarps) {
+  if (M2 && warp < kProducerWarps) {
+    // ---- producers, whole step per stage: 16-byte chunk j = t % 8 of rows
+    // n = t/8 + 32k (k = 0..5) of the three B buffers
+    const int j = threadIdx.x & 7, r0 = threadIdx.x >> 3;
+    constexpr int G = 18;
+    for (int it = 0; it < niter; ++it) {
+      const uint32_t ph = (uint32_t)it & 1u;
+      const int st = rg.x + it;
+      const int srcA = __ldg(st_src + (size_t)st * kTile + r0), srcB = __ldg(st_src + (size_t)st * kTile + r0 + 32);
+      uint4 v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int bsel = q / 6, k = q % 6;  // buffer: chunk 0 hi, chunk 0 lo, chunk 1 hi
+        const int h = bsel == 1 ? 1 : 0, kc = bsel == 2 ? 1 : 0;
+        const int src = (k & 1) ? srcB : srcA;
+        v[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (src >= 0)
+          v[q] = __ldg(reinterpret_cast<const uint4*>(Mb + ((((size_t)src * 2 + h) * 3 + (k >> 1)) * nkc + kc) * 128) +
+                       j);
+      }
+      if (!mbar_wait(empty(0), ph ^ 1u, abort)) break;
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int bsel = q / 6, n = r0 + 32 * (q % 6);
+        *reinterpret_cast<uint4*>(smem + 3 * abuf + bsel * kBBytes + n * 128 + ((j ^ (n & 7)) << 4)) = v[q];
+      }
+      fence_proxy_async();
+      mbar_arrive(fullB(0));
+    }
+  } else if (M2 && lane == 0 && warp == kProducerWarps) {
+    // ---- control thread, whole step per stage: three operator copies, then
+    // 12 MMAs for chunk 0 (three products) and ksteps_last for chunk 1 (hi x hi)
+    int issued = 0, consumed = 0;
+    bool ok = true;
+    const size_t chunk = (size_t)128 * 128;  // bytes of one (operator, hi/lo, K chunk) block (nrh == 1)
+    for (int it = 0; it < niter; ++it) {
+      const uint32_t ph = (uint32_t)it & 1u;
+      if (!mbar_wait(empty(0), ph ^ 1u, abort)) {
+        ok = false;
+        break;
+      }
+      const size_t key = (size_t)st_slot[rg.x + it];
+      const uint32_t a0 = sbase;
+      mbar_arrive_tx(fullA(0), 3u * abytes);
+      bulk_g2s(a0, Tb + ((key * 2 + 0) * nkc + 0) * chunk, abytes, fullA(0));
+      bulk_g2s(a0 + abuf, Tb + ((key * 2 + 1) * nkc + 0) * chunk, abytes, fullA(0));
+      bulk_g2s(a0 + 2 * abuf, Tb + ((key * 2 + 0) * nkc + 1) * chunk, abytes, fullA(0));
+      issued = it + 1;
+      if (!mbar_wait(fullA(0), ph, abort)) {
+        ok = false;
+        break;
+      }
+      consumed = it + 1;
+      if (!mbar_wait(fullB(0), ph, abort)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t b0 = a0 + 3 * abuf;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t off = (uint32_t)kk * 32u;
+        umma<KIND>(tmem, sw128_desc(a0 + off), sw128_desc(b0 + off), (it > 0 || kk > 0) ? 1u : 0u);
+        umma<KIND>(tmem, sw128_desc(a0 + off), sw128_desc(b0 + kBBytes + off), 1u);
+        umma<KIND>(tmem, sw128_desc(a0 + abuf + off), sw128_desc(b0 + off), 1u);
+      }
+      for (int kk = 0; kk < ksteps_last; ++kk) {
+        const uint32_t off = (uint32_t)kk * 32u;
+        umma<KIND>(tmem, sw128_desc(a0 + 2 * abuf + off), sw128_desc(b0 + 2 * kBBytes + off), 1u);
+      }
+      umma_commit(empty(0));
+    }
+    if (ok) {
+      umma_commit(done);
+    } else {
+      *abort = 1;
+      volatile int never = 0;
+      for (int it = consumed; it < issued; ++it) mbar_wait(fullA(0), (uint32_t)it & 1u, &never);
+      umma_commit(done);
+      mbar_wait(done, 0u, &never);
+      atomicExch(flag, FMM_E_TIMEOUT);
+    }
+  } else if (M2) {
+    // the other lanes of the control warp go straight to the teardown
+  } else if (warp < kProducerWarps) {
     // ---- producers: thread t stores 16-byte chunk j = t % 8 of rows n = t/8 + 32k
     // (k = 0..5) of both halves, i.e. of the sources in slots t/8 and t/8 + 32;
     // the rows are loaded before the stage's buffer is waited for.
@@ -248,11 +346,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       mbar_arrive(fullB(stage));
     }
   } else if (lane == 0) {
-    // ---- control thread: operator copies and MMAs.  Only the operator rows
-    // below P are copied (whole 8-row swizzle groups): the rows above feed only
-    // output rows that the epilogue never stores.
-    const uint32_t arows = (uint32_t)min(128, ((P - rh * 128) + 7) & ~7);
-    const uint32_t abytes = arows * 128u;
+    // ---- control thread: operator copies and MMAs
     int issued = 0;  // A copies issued for iterations [0, issued)
     auto issue_A = [&](int it) -> bool {
       const int stage = it % kStages;
@@ -425,11 +519,50 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   const size_t sh = (size_t)kBarOff + 128 + 1024;
   static bool attr_set[2] = {false, false};
   if (!attr_set[kind]) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(kind ? k_m2l_tc<1> : k_m2l_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sh));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(kind ? k_m2l_tc<1, false> : k_m2l_tc<0, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     attr_set[kind] = true;
   }
   const int nrh = m2l_rowblocks(p->P);
+  // A whole step per stage when it has two BF16 K chunks, the second with one
+  // product, in one block of output rows, and two such CTAs still fit an SM
+  // (p = 9 and 10 at theta <= 0.42): one operator-copy latency per step
+  // instead of one per chunk.
+  bool m2 = false;
+  size_t sh2 = 0;
+  if (kind == 0 && nkc == 2 && nkc3 == 1 && nrh == 1 && !(p->prm.m2l_mode & FMM_M2L_CHUNK_STAGES)) {
+    const size_t arows = (size_t)std::min(128, (p->P + 7) & ~7);
+    sh2 = 3 * arows * 128 + 3 * (size_t)kBBytes + 128 + 1024;
+    static int m2_ok = -1;  // 1: two CTAs per SM at the largest stage (P = 128 rows would not fit)
+    static size_t m2_sh = 0;
+    if (m2_ok < 0 || m2_sh != sh2) {
+      // Two CTAs per SM by shared memory (each with the per-block reserve) and
+      // registers, from the device and kernel attributes; the occupancy query
+      // reports one CTA per SM for both forms of this kernel, although two
+      // run (ncu: 17.5 of 18 warps active per SM).  Two such CTAs need the
+      // largest shared-memory carveout.
+      int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
+      cudaFuncAttributes fa{};
+      m2_ok = cudaGetDevice(&dev) == cudaSuccess &&
+                      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ==
+                          cudaSuccess &&
+                      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+                      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+                      cudaFuncGetAttributes(&fa, k_m2l_tc<0, true>) == cudaSuccess &&
+                      cudaFuncSetAttribute(k_m2l_tc<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh2) ==
+                          cudaSuccess &&
+                      cudaFuncSetAttribute(k_m2l_tc<0, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+                          cudaSuccess &&
+                      2 * (sh2 + (size_t)resv + fa.sharedSizeBytes) <= (size_t)smem_sm &&
+                      2 * (size_t)fa.numRegs * kThreads <= (size_t)regs_sm
+                  ? 1
+                  : 0;
+      cudaGetLastError();
+      m2_sh = sh2;
+    }
+    m2 = m2_ok == 1;
+  }
+  p->m2l_stage_chunks = m2 ? 2 : 1;
   const int nt = (int)p->ntiles;
   const int T = 256;
   // One-problem plans split the tiles into work items of at most S steps:
@@ -471,13 +604,19 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   }
   ++g_launches;
   const dim3 g3(grid, (unsigned)nrh);
-  if (kind)
-    k_m2l_tc<1><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
+  if (m2)
+    k_m2l_tc<0, true><<<g3, kThreads, sh2, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
+                                                p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
+                                                p->Mbf.as<uint8_t>(), p->P, nkc, nkc3, last, nrh,
+                                                p->tile_cells.as<int>(), p->L.as<float>(), p->m2l_partial.as<float>(),
+                                                p->flags.as<int>());
+  else if (kind)
+    k_m2l_tc<1, false><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
                                          p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
                                          p->Mbf.as<uint8_t>(), p->P, nkc, nkc3, last, nrh, p->tile_cells.as<int>(),
                                          p->L.as<float>(), p->m2l_partial.as<float>(), p->flags.as<int>());
   else
-    k_m2l_tc<0><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
+    k_m2l_tc<0, false><<<g3, kThreads, sh, s>>>(p->tile_range.as<int2>(), items, nitems, p->tile_first.as<int>(),
                                          p->st_slot.as<int>(), p->st_src.as<int>(), p->Tbf.as<uint8_t>(),
                                          p->Mbf.as<uint8_t>(), p->P, nkc, nkc3, last, nrh, p->tile_cells.as<int>(),
                                          p->L.as<float>(), p->m2l_partial.as<float>(), p->flags.as<int>());

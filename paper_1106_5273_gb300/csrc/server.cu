@@ -449,7 +449,7 @@ int fmm_server_create(const fmm_server_params* prm, fmm_server* out) {
   q.images = prm->images;
   q.m2l_mode = prm->m2l_mode;
   if (!(q.theta > 0.f && q.theta < 1.f) || q.ncrit < 1 || q.ncrit > 4096 || !(q.sigma_sep >= 0.f) ||
-      q.images < 1 || q.images > 8 || (q.m2l_mode & ~(3 | FMM_M2L_SORT_STEPS | FMM_M2L_FULL_SPLIT)))
+      q.images < 1 || q.images > 8 || (q.m2l_mode & ~(3 | FMM_M2L_SORT_STEPS | FMM_M2L_FULL_SPLIT | FMM_M2L_CHUNK_STAGES)))
     return FMM_E_INVAL;
   if (prm->model_bytes_per_particle < 0) return FMM_E_INVAL;
   fmm_server S = new (std::nothrow) fmm_server_s();

@@ -43,7 +43,7 @@ def test_params_and_errors_without_gpu(lib):
     # parameter validation happens before any CUDA call
     h = ctypes.c_void_p()
     for bad in (dict(p=0), dict(p=17), dict(theta=1.5), dict(ncrit=0), dict(periodic=1, box_len=0.0),
-                dict(periodic=1, images=0), dict(m2l_mode=7), dict(m2l_mode=32), dict(sigma_rule=2),
+                dict(periodic=1, images=0), dict(m2l_mode=7), dict(m2l_mode=64), dict(sigma_rule=2),
                 dict(p2p_pair_max=-1),
                 dict(split_tie=2), dict(p2p_tpl=3)):
         qq = binding.Params.default(**bad)

@@ -184,6 +184,22 @@ def test_single_product_chunks_within_their_bound(name, p):
         assert rel_l2(u, ref.u) < TOL_U and rel_l2(s, ref.s) < TOL_S
 
 
+@pytest.mark.parametrize("name,p", [("taylor-green-16", 10), ("taylor-green-16", 9), ("plummer-free", 10)])
+def test_whole_step_stage_bit_identical_to_chunk_stages(name, p):
+    """A step of two K chunks, the second with one product, runs as one
+    pipeline stage (three operator copies, 12 + ksteps_last MMAs); with
+    FMM_M2L_CHUNK_STAGES it runs as one stage per chunk.  The MMAs are the same
+    and go to the tensor memory in the same order, so both outputs must agree
+    bit for bit."""
+    from paper_1106_5273_gb300 import FMM_M2L_CHUNK_STAGES
+    w, (_, _, ncrit) = _case(name)
+    pa, ua, sa = run_fmm(w, p, 0.4, ncrit, m2l_mode=2)
+    pb, ub, sb = run_fmm(w, p, 0.4, ncrit, m2l_mode=2 | FMM_M2L_CHUNK_STAGES)
+    assert pa.stats().m2l_pairs > 0 and pa.stats().m2l_split_coefs == 64
+    assert pa.stats().m2l_stage_chunks == 2 and pb.stats().m2l_stage_chunks == 1
+    assert np.array_equal(ua, ub) and np.array_equal(sa, sb)
+
+
 @pytest.fixture(scope="module")
 def _lattice_direct():
     from oracle import direct as od
