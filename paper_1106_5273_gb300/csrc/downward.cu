@@ -35,57 +35,32 @@ __global__ void __launch_bounds__(128) k_l2l(int lb, const int* __restrict__ par
   }
 }
 
-// L~_N^M for any M (|M| <= N), from real-packed storage.
-__device__ inline float2 lget(const float* Lp, int N, int M) {
-  int am = M < 0 ? -M : M;
-  float re = Lp[N * N + (am == 0 ? 0 : 2 * am - 1)];
-  float im = am == 0 ? 0.f : Lp[N * N + 2 * am];
-  if (M < 0) {
-    im = -im;
-    if (am & 1) {
-      re = -re;
-      im = -im;
-    }
-  }
-  return make_float2(re, im);
-}
-
 // One CTA per leaf, one thread per particle.
 __global__ void __launch_bounds__(64) k_l2p(const int* __restrict__ leaves, const int* __restrict__ begin,
                                             const int* __restrict__ end, const int* __restrict__ level,
                                             const double* __restrict__ center, const double* __restrict__ box,
                                             const int* __restrict__ cseg,
                                             const float4* __restrict__ A, const float4* __restrict__ B,
-                                            const float* __restrict__ L, const float* __restrict__ Wg, int p,
+                                            const float* __restrict__ L, const int4* __restrict__ tab, int p,
                                             int transpose, float* __restrict__ far_u, float* __restrict__ far_s) {
   extern __shared__ float sm[];
   const int P = p * p;
   float2* sD = reinterpret_cast<float2*>(sm);  // [3][5][P] complex, see below
   float* sL = sm + 2 * 15 * P;                 // [3][P]
-  float* sW = sL + 3 * P;                      // [5][P]
   const int leaf = leaves[blockIdx.x];
   for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) sL[i] = L[(size_t)leaf * 3 * P + i];
-  for (int i = threadIdx.x; i < 5 * P; i += blockDim.x) sW[i] = Wg[i];
   __syncthreads();
-  const int on[5] = {1, 1, 2, 2, 2}, om[5] = {0, 1, 0, 1, 2};
+  const int on[5] = {1, 1, 2, 2, 2};
   // The leaf's coefficients of the derivative expansions, once per leaf:
   // D[q][o][k^2+k+mm] = W_o(k, mm) L~_q(on_o + k, om_o + mm) for mm >= 0 and
   // (-1)^m W_o(k, -m) L~_q(on_o + k, om_o - m) for mm = -m < 0, so that the
   // derivative o of potential q is sum_k,m D(+m) R~_k^m + D(-m) conj(R~_k^m).
-  for (int i = threadIdx.x; i < 15 * P; i += blockDim.x) {
-    const int qo = i / P, kk = i % P, q = qo / 5, o = qo % 5;
-    int k = 0;
-    while ((k + 1) * (k + 1) <= kk) ++k;
-    const int mm = kk - k * k - k, m = mm < 0 ? -mm : mm;
-    const int N = on[o] + k;
-    float2 d = make_float2(0.f, 0.f);
-    if (N <= p - 1) {
-      const float w = sW[o * P + kk];
-      const float2 lt = lget(sL + q * P, N, om[o] + mm);
-      const float sg = (mm < 0 && (m & 1)) ? -w : w;
-      d = make_float2(sg * lt.x, sg * lt.y);
-    }
-    sD[i] = d;
+  // The table holds, per (o, k, mm), where L~ is read and the signed weights.
+  for (int e = threadIdx.x; e < 5 * P; e += blockDim.x) {
+    const int4 t = __ldg(tab + e);
+    const float cre = __int_as_float(t.z), cim = __int_as_float(t.w);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sD[q * 5 * P + e] = make_float2(cre * sL[q * P + t.x], cim * sL[q * P + t.y]);
   }
   __syncthreads();
   const int b = begin[leaf], e = end[leaf];
@@ -210,10 +185,10 @@ int downward_pass(fmm_plan p, int64_t n, cudaStream_t s) {
   FMM_TRY(p->far_u.ensure((size_t)n * 3 * sizeof(float)));
   FMM_TRY(p->far_s.ensure((size_t)n * 3 * sizeof(float)));
   ++g_launches;
-  k_l2p<<<(unsigned)p->nleaves, 64, (2 * 15 + 8) * P * sizeof(float), s>>>(
+  k_l2p<<<(unsigned)p->nleaves, 64, (2 * 15 + 3) * P * sizeof(float), s>>>(
       p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(), p->c_level.as<int>(), p->c_center.as<double>(),
       p->batched ? p->seg_box.as<double>() : p->scal.as<double>(), p->batched ? p->c_seg.as<int>() : nullptr,
-      p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_w.as<float>(),
+      p->sortA.as<float4>(), p->sortB.as<float4>(), p->L.as<float>(), p->l2p_tab.as<int4>(),
       p->prm.p, (p->prm.outputs & FMM_OUT_STRETCHING_TRANSPOSE) ? 1 : 0, p->far_u.as<float>(), p->far_s.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
   return FMM_OK;

@@ -34,7 +34,7 @@ int check_params(const fmm_params* q) {
 }
 
 std::vector<DBuf*> plan_buffers(fmm_plan p) {
-  return {&p->m2m_T, &p->l2l_T, &p->l2p_w, &p->lattice, &p->keys0, &p->keys1, &p->vals0, &p->vals1,
+  return {&p->m2m_T, &p->l2l_T, &p->l2p_tab, &p->lattice, &p->keys0, &p->keys1, &p->vals0, &p->vals1,
           &p->sortA, &p->sortB, &p->far_u, &p->far_s, &p->leaf_of, &p->in_pos, &p->in_gam, &p->in_sig,
           &p->out_vel, &p->out_dg, &p->c_begin, &p->c_end, &p->c_level, &p->c_parent, &p->c_child,
           &p->c_nchild, &p->c_key, &p->c_center, &p->c_radius2, &p->c_radius, &p->c_cf, &p->c_tile,

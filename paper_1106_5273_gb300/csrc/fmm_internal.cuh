@@ -63,7 +63,7 @@ struct fmm_plan_s {
   // constant operator tables (device)
   fmm::DBuf m2m_T;    // [8][P(k)][P(r)] FP32 transposed M2M matrices by child octant
   fmm::DBuf l2l_T;    // [8][P(k)][P(r)] FP32 transposed L2L matrices by child octant
-  fmm::DBuf l2p_w;    // [5][P] FP32 L2P weights
+  fmm::DBuf l2p_tab;  // [5][P] int4 L2P gather table (indices into L~, signed weights)
   fmm::DBuf lattice;  // [P][P] FP64 periodic lattice operator (row = output)
   // particles
   fmm::DBuf keys0, keys1, vals0, vals1;  // radix sort ping-pong

@@ -10,6 +10,7 @@
 // rings of 702 super-cells, each ring the M2L sum from offsets
 // {-4..4}^3 \ {-1..1}^3, the next super-cell the M2M sum of 27 copies.
 #include <complex>
+#include <cstring>
 
 #include "fmm_internal.cuh"
 #include <cuda_bf16.h>
@@ -259,8 +260,41 @@ int build_constant_operators(fmm_plan p) {
         if (n2 + k > pp - 1 || std::abs(m2 + l) > n2 + k) continue;
         w[(size_t)o * P + k * k + k + l] = (float)(nu_d(n2 + k, m2 + l) / nu_d(k, l));
       }
-  FMM_TRY(p->l2p_w.ensure(w.size() * sizeof(float)));
-  FMM_CUDA_TRY(cudaMemcpy(p->l2p_w.ptr, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // The L2P gather table: entry o P + (k^2 + k + mm) of the leaf's derivative
+  // coefficients D_o(k, mm) = c_re L~(i_re) + i c_im L~(i_im) (per potential),
+  // with L~_N^M, N = n'_o + k, M = m'_o + mm read from the real-packed
+  // storage (re at N^2 + (|M| ? 2|M| - 1 : 0), im at N^2 + 2|M|), the signs
+  // of M < 0, the weight, and (-1)^m for mm = -m < 0 folded into
+  // c_re, c_im (zero where N > p - 1 or the term has no imaginary part).
+  std::vector<int4> tab((size_t)5 * P);
+  for (int o = 0; o < 5; ++o)
+    for (int k = 0; k < pp; ++k)
+      for (int mm = -k; mm <= k; ++mm) {
+        const int kk = k * k + k + mm, m = std::abs(mm);
+        const int N = outs[o][0] + k, M = outs[o][1] + mm;
+        int4 t = make_int4(0, 0, 0, 0);
+        if (N <= pp - 1) {
+          const float wv = w[(size_t)o * P + kk];
+          const float sg = (mm < 0 && (m & 1)) ? -wv : wv;
+          const int am = std::abs(M);
+          float sre = 1.f, sim = am == 0 ? 0.f : 1.f;
+          if (M < 0) {  // L~_N^{-|M|} = (-1)^|M| conj(L~_N^{|M|})
+            sim = -sim;
+            if (am & 1) {
+              sre = -sre;
+              sim = -sim;
+            }
+          }
+          const float cre = sg * sre, cim = sg * sim;
+          t.x = N * N + (am == 0 ? 0 : 2 * am - 1);
+          t.y = am == 0 ? 0 : N * N + 2 * am;
+          std::memcpy(&t.z, &cre, sizeof(float));
+          std::memcpy(&t.w, &cim, sizeof(float));
+        }
+        tab[(size_t)o * P + kk] = t;
+      }
+  FMM_TRY(p->l2p_tab.ensure(tab.size() * sizeof(int4)));
+  FMM_CUDA_TRY(cudaMemcpy(p->l2p_tab.ptr, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (p->prm.periodic) {  // the lattice operator, in FP64 on the device
     FMM_TRY(p->lattice.ensure((size_t)P * P * sizeof(double)));
     FMM_TRY(lattice_operator_device(pp, p->prm.images, p->lattice.as<double>(), 0));
