@@ -4,8 +4,11 @@ Sec. 3.2 (Morton keys: interleaved coordinate bits, 63-bit keys, at most 21
 levels) and Sec. 3.3 (Algorithm 1 Evaluate, Algorithm 2 Interact, the FMM MAC).
 
 Readings taken where the paper is silent or ambiguous:
-  * Keys: FP64 normalisation into the cube, 21 bits per axis, bit b of x, y, z
-    at positions 3b+2, 3b+1, 3b (x most significant).  Child digit = 4x+2y+z.
+  * Keys: FP64 normalisation into the cube, 21 bits per axis: cell coordinate
+    floor((x - x_min) f) with f = 2^21 / L rounded once (Sec. 3.2 fixes the
+    interleaved bits of the normalised coordinates, not the rounding of the
+    normalisation), clamped to [0, 2^21 - 1]; bit b of x, y, z at positions
+    3b+2, 3b+1, 3b (x most significant).  Child digit = 4x+2y+z.
   * Free-space cube: centre of the bounding box, side = longest extent times
     (1 + 2^-10) (half-side 0.5 if all points coincide).  Periodic: given cube.
   * A cell splits while it holds more than ncrit particles and its level < 21.
@@ -55,8 +58,8 @@ def free_space_box(pos):
 def quantize(pos, box_min, box_len):
     """Integer cell coordinates at level 21, [n,3] int64."""
     x = np.asarray(pos, np.float32).astype(np.float64)
-    u = (x - np.asarray(box_min, np.float64)) / float(box_len)
-    k = np.floor(u * KEY_SCALE)
+    f = KEY_SCALE / float(box_len)
+    k = np.floor((x - np.asarray(box_min, np.float64)) * f)
     k = np.clip(k, 0.0, KEY_SCALE - 1.0)
     return k.astype(np.int64)
 

@@ -161,9 +161,10 @@ __device__ inline uint32_t compact3(uint64_t x) {
   return (uint32_t)x;
 }
 
-__device__ inline uint64_t quantize_axis(float x, double bmin, double blen, double scale) {
-  double u = __ddiv_rn(__dsub_rn((double)x, bmin), blen);
-  double k = floor(__dmul_rn(u, scale));
+// Cell coordinate floor((x - bmin) f) with f = 2^kbits / L rounded once (one
+// FP64 division per particle rather than one per coordinate), clamped.
+__device__ inline uint64_t quantize_axis(float x, double bmin, double f, double scale) {
+  double k = floor(__dmul_rn(__dsub_rn((double)x, bmin), f));
   if (!(k >= 0.0)) k = 0.0;
   if (k > scale - 1.0) k = scale - 1.0;
   return (uint64_t)k;
@@ -180,10 +181,10 @@ __global__ void k_keys(const float* __restrict__ pos, int64_t n, const double* _
   if (i < n) {
     const int sg = off ? seg_of(off, nseg, i) : 0;
     const double* b = box + 4 * sg;
-    const double blen = b[3], scale = ldexp(1.0, kbits);
-    uint64_t kx = quantize_axis(pos[3 * i + 0], b[0], blen, scale);
-    uint64_t ky = quantize_axis(pos[3 * i + 1], b[1], blen, scale);
-    uint64_t kz = quantize_axis(pos[3 * i + 2], b[2], blen, scale);
+    const double scale = ldexp(1.0, kbits), f = __ddiv_rn(scale, b[3]);
+    uint64_t kx = quantize_axis(pos[3 * i + 0], b[0], f, scale);
+    uint64_t ky = quantize_axis(pos[3 * i + 1], b[1], f, scale);
+    uint64_t kz = quantize_axis(pos[3 * i + 2], b[2], f, scale);
     const uint64_t k = ((uint64_t)sg << (3 * kbits)) | (spread3(kx) << 2) | (spread3(ky) << 1) | spread3(kz);
     keys[i] = k;
     idx[i] = (uint32_t)i;
