@@ -426,43 +426,37 @@ __global__ void k_cell_ijk(const int* __restrict__ level, const uint64_t* __rest
   ijk[c] = (uint64_t)r[0] | ((uint64_t)r[1] << 21) | ((uint64_t)r[2] << 42);
 }
 
+// Translation key of every M2L pair, and the field ranges of the keys
+// (delta, tx, ty, tz; min and max in rng[2q], rng[2q + 1]) for their compact
+// encoding.
 __global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __restrict__ level,
-                           const uint64_t* __restrict__ cijk, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                           const uint64_t* __restrict__ cijk, uint64_t* __restrict__ keys, int* __restrict__ rng,
                            int* __restrict__ flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int4 v = raw[i];
-  int la = level[v.x], lb = level[v.y];
-  int lf = la > lb ? la : lb;
-  const uint64_t pa = cijk[v.x], pb = cijk[v.y];
-  const long long ia[3] = {(long long)(pa & 0x1FFFFFull), (long long)((pa >> 21) & 0x1FFFFFull),
-                           (long long)(pa >> 42)};
-  const long long ib[3] = {(long long)(pb & 0x1FFFFFull), (long long)((pb >> 21) & 0x1FFFFFull),
-                           (long long)(pb >> 42)};
-  int o[3] = {v.z / 9 - 1, (v.z / 3) % 3 - 1, v.z % 3 - 1};
-  long long t[3];
-  bool ok = true;
-  for (int q = 0; q < 3; ++q) {
-    t[q] = (2 * ia[q] + 1) * (1ll << (lf - la)) - (2 * ib[q] + 1) * (1ll << (lf - lb)) - (long long)o[q] * (1ll << (lf + 1));
-    if (t[q] > kKeyLim || t[q] < -kKeyLim) ok = false;
-  }
-  if (!ok) atomicExch(flag, FMM_E_DEPTH);
-  keys[i] = m2l_key_encode(la - lb, t[0], t[1], t[2]);
-  vals[i] = (uint32_t)i;
-}
-
-// Field ranges of the translation keys (delta, tx, ty, tz) for the compact
-// encoding of the step sort.
-__global__ void k_key_ranges(const uint64_t* __restrict__ keys, int n, int* __restrict__ rng) {
   int lo[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX}, hi[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint64_t k = keys[i];
+  if (i < n) {
+    int4 v = raw[i];
+    int la = level[v.x], lb = level[v.y];
+    int lf = la > lb ? la : lb;
+    const uint64_t pa = cijk[v.x], pb = cijk[v.y];
+    const long long ia[3] = {(long long)(pa & 0x1FFFFFull), (long long)((pa >> 21) & 0x1FFFFFull),
+                             (long long)(pa >> 42)};
+    const long long ib[3] = {(long long)(pb & 0x1FFFFFull), (long long)((pb >> 21) & 0x1FFFFFull),
+                             (long long)(pb >> 42)};
+    int o[3] = {v.z / 9 - 1, (v.z / 3) % 3 - 1, v.z % 3 - 1};
+    long long t[3];
+    bool ok = true;
+    for (int q = 0; q < 3; ++q) {
+      t[q] = (2 * ia[q] + 1) * (1ll << (lf - la)) - (2 * ib[q] + 1) * (1ll << (lf - lb)) -
+             (long long)o[q] * (1ll << (lf + 1));
+      if (t[q] > kKeyLim || t[q] < -kKeyLim) ok = false;
+    }
+    if (!ok) atomicExch(flag, FMM_E_DEPTH);
+    const uint64_t k = m2l_key_encode(la - lb, t[0], t[1], t[2]);
+    keys[i] = k;
     const int f[4] = {(int)(k >> 57) - 32, (int)key_field(k, 38), (int)key_field(k, 19), (int)key_field(k, 0)};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      lo[q] = min(lo[q], f[q]);
-      hi[q] = max(hi[q], f[q]);
-    }
+    for (int q = 0; q < 4; ++q) lo[q] = hi[q] = f[q];
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -470,9 +464,25 @@ __global__ void k_key_ranges(const uint64_t* __restrict__ keys, int n, int* __re
       lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
       hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
     }
-    if ((threadIdx.x & 31) == 0) {
-      atomicMin(&rng[2 * q], lo[q]);
-      atomicMax(&rng[2 * q + 1], hi[q]);
+  }
+  __shared__ int slo[4][32], shi[4][32];
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 4; ++q) {
+      slo[q][w] = lo[q];
+      shi[q][w] = hi[q];
+    }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x;
+    int l = INT_MAX, h = INT_MIN;
+    for (int k = 0; k < nw; ++k) {
+      l = min(l, slo[q][k]);
+      h = max(h, shi[q][k]);
+    }
+    if (l <= h) {
+      atomicMin(&rng[2 * q], l);
+      atomicMax(&rng[2 * q + 1], h);
     }
   }
 }
@@ -915,15 +925,13 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       ++g_launches;
       k_cell_ijk<<<(unsigned)((nc + T - 1) / T), T, 0, s>>>(p->c_level.as<int>(), p->c_key.as<uint64_t>(), nc,
                                                            p->c_ijk.as<uint64_t>());
-      k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_ijk.as<uint64_t>(),
-                                 p->m2l_key.as<uint64_t>(), p->lv0.as<uint32_t>(), flag);
       int* drng = reinterpret_cast<int*>(p->scal.as<double>() + kScalCount + 8);
       const int init[8] = {INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN};
       int* hr = reinterpret_cast<int*>(reinterpret_cast<char*>(p->pinned) + 256);
       memcpy(hr, init, sizeof(init));
       FMM_CUDA_TRY(cudaMemcpyAsync(drng, hr, sizeof(init), cudaMemcpyHostToDevice, s));
-      ++g_launches;
-      k_key_ranges<<<std::min<unsigned>(g, 1024u), T, 0, s>>>(p->m2l_key.as<uint64_t>(), n, drng);
+      k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_ijk.as<uint64_t>(),
+                                 p->m2l_key.as<uint64_t>(), drng, flag);
       FMM_CUDA_TRY(cudaMemcpyAsync(hr, drng, sizeof(init), cudaMemcpyDeviceToHost, s));
       FMM_CUDA_TRY(cudaStreamSynchronize(s));
       KeyPack kp;
