@@ -432,9 +432,9 @@ __global__ void k_cell_ijk(const int* __restrict__ level, const uint64_t* __rest
 __global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __restrict__ level,
                            const uint64_t* __restrict__ cijk, uint64_t* __restrict__ keys, int* __restrict__ rng,
                            int* __restrict__ flag) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
   int lo[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX}, hi[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
-  if (i < n) {
+  // grid-stride over the pairs: few blocks, so few atomics on the 8 range words
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int4 v = raw[i];
     int la = level[v.x], lb = level[v.y];
     int lf = la > lb ? la : lb;
@@ -456,7 +456,10 @@ __global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __res
     keys[i] = k;
     const int f[4] = {(int)(k >> 57) - 32, (int)key_field(k, 38), (int)key_field(k, 19), (int)key_field(k, 0)};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) lo[q] = hi[q] = f[q];
+    for (int q = 0; q < 4; ++q) {
+      lo[q] = min(lo[q], f[q]);
+      hi[q] = max(hi[q], f[q]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -930,8 +933,9 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       int* hr = reinterpret_cast<int*>(reinterpret_cast<char*>(p->pinned) + 256);
       memcpy(hr, init, sizeof(init));
       FMM_CUDA_TRY(cudaMemcpyAsync(drng, hr, sizeof(init), cudaMemcpyHostToDevice, s));
-      k_m2l_keys<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(), p->c_ijk.as<uint64_t>(),
-                                 p->m2l_key.as<uint64_t>(), drng, flag);
+      k_m2l_keys<<<std::min<unsigned>(g, 2048u), T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(),
+                                                            p->c_ijk.as<uint64_t>(), p->m2l_key.as<uint64_t>(), drng,
+                                                            flag);
       FMM_CUDA_TRY(cudaMemcpyAsync(hr, drng, sizeof(init), cudaMemcpyDeviceToHost, s));
       FMM_CUDA_TRY(cudaStreamSynchronize(s));
       KeyPack kp;
