@@ -388,6 +388,35 @@ def test_morton_keys_by_hand():
     assert np.array_equal(tr.deinterleave(key), k)
 
 
+def test_key_quantization_matches_exact_cell_of_each_point():
+    """The cell coordinate of a point is the integer part of its normalised
+    coordinate u = (x - x_min) 2^21 / L (Sec. 3.2), clamped to [0, 2^21 - 1].
+    Against exact rational arithmetic: the oracle's floor((x - x_min) f), with
+    f = 2^21 / L rounded once in FP64, gives exactly that cell unless u lies
+    within the FP64 rounding (2^-28 here) of an integer, and then a neighbour."""
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    box_min = np.array([-0.3, 0.1, 2.0])
+    box_len = 1.6180339887498949  # no small-integer ratio to the FP32 spacing of the points
+    pos = (box_min + rng.random((2000, 3)) * box_len).astype(np.float32)
+    pos[:4] = np.array([[-5.0, 0.0, 2.5], [9.0, 9.0, 9.0], box_min, box_min + box_len], np.float32)
+    k = tr.quantize(pos, box_min, box_len)
+    top = (1 << 21) - 1
+    close = 0
+    for i in range(pos.shape[0]):
+        for a in range(3):
+            u = (Fraction(float(pos[i, a])) - Fraction(float(box_min[a]))) * (1 << 21) / Fraction(box_len)
+            want = 0 if u < 0 else min(int(u), top)
+            dist = abs(u - round(u))
+            if 0 <= u <= top + 1 and dist < Fraction(1, 1 << 28):
+                close += 1
+                assert abs(int(k[i, a]) - want) <= 1
+            else:
+                assert int(k[i, a]) == want, (i, a, float(u))
+    assert close <= 8  # the exact corners of the cube and little else
+    assert tuple(k[1]) == (top, top, top) and k[0, 0] == 0 and k[0, 1] == 0
+
+
 def test_tree_invariants():
     for w in (workloads.jittered_lattice(8), workloads.plummer(3000)):
         pos = w["pos"]
