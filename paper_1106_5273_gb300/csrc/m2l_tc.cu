@@ -482,7 +482,7 @@ __global__ void k_m2l_combine(const uint32_t* __restrict__ cnt, const uint32_t* 
   if (k <= 1) return;
   const int first = tfirst[t], ncell = tfirst[t + 1] - first;
   const size_t per = (size_t)nrh * kN * 128;  // floats per partial slot
-  for (int e = threadIdx.x; e < nrh * kN * 128; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < nrh * kN * 128; e += gridDim.y * blockDim.x) {
     const int r = e & 127, n = (e >> 7) % kN, rh = e / (kN * 128);
     const int row = rh * 128 + r, slot = n % kTile, comp = n / kTile;
     if (row >= P || slot >= ncell) continue;
@@ -623,8 +623,9 @@ int m2l_tensor(fmm_plan p, cudaStream_t s) {
   FMM_CUDA_TRY(cudaGetLastError());
   if (items) {
     ++g_launches;
-    k_m2l_combine<<<(unsigned)nt, T, 0, s>>>(cnt, poff, p->tile_first.as<int>(), p->tile_cells.as<int>(), p->P, nrh,
-                                             p->m2l_partial.as<float>(), p->L.as<float>());
+    // a tile's D block over 8 CTAs (the split tiles are a few hundred)
+    k_m2l_combine<<<dim3((unsigned)nt, 8), T, 0, s>>>(cnt, poff, p->tile_first.as<int>(), p->tile_cells.as<int>(),
+                                                      p->P, nrh, p->m2l_partial.as<float>(), p->L.as<float>());
     FMM_CUDA_TRY(cudaGetLastError());
   }
   return FMM_OK;
