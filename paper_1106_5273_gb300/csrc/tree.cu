@@ -243,14 +243,6 @@ __device__ inline int lower_bound_u64(const uint64_t* a, int lo, int hi, uint64_
   return lo;
 }
 
-// Child boundaries of cell c at level l (8 digits -> 9 bounds).
-__device__ inline void child_bounds(const uint64_t* skeys, int b, int e, uint64_t prefix, int l, int kbits, int* bd) {
-  const int shift = 3 * (kbits - 1 - l);
-  bd[0] = b;
-  bd[8] = e;
-  for (int d = 1; d < 8; ++d) bd[d] = lower_bound_u64(skeys, b, e, ((prefix << 3) | (uint64_t)d) << shift);
-}
-
 // One group of 8 lanes per cell: lane d finds the first particle of child
 // digit d (a binary search in the cell's sorted keys, d = 1..7; lane 0 holds
 // the cell's begin), so the 7 searches run side by side instead of one after

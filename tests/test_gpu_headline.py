@@ -124,6 +124,24 @@ def test_lists_bit_exact_under_both_split_rules(name, split_tie):
         assert dl == ({0, -1} if split_tie == "source" else {0, 1})
 
 
+@pytest.mark.parametrize("shift,ncrit", [((100.0, -50.0, 30.0), 8), ((0.0, 0.0, 0.0), 4)])
+def test_cells_and_radii_bit_exact_far_from_origin(shift, ncrit):
+    """Cell centres and tight radii (FP64 distances from the cube centres) of a
+    Plummer cloud moved far from the origin (cells thousands of times smaller
+    than the coordinates) and of a deep tree of the unmoved cloud: bit-exact
+    against the oracle."""
+    from oracle import tree as tr
+    w = workloads.plummer(3000, seed=21)
+    w["pos"] = (w["pos"].astype(np.float64) + np.array(shift)).astype(np.float32)
+    plan, u, s = run_fmm(w, 6, 0.5, ncrit, m2l_mode=2)
+    order, keys, t, bmin, blen = tr.build(w["pos"], ncrit)
+    c = plan.cells()
+    assert np.array_equal(c["level"].astype(np.int64), t.level) and t.level.max() >= 6
+    assert np.array_equal(c["center"], t.center)
+    assert np.array_equal(c["radius"], t.radius)
+    assert np.isfinite(u).all() and np.isfinite(s).all()
+
+
 def test_headline_path_p10_taylor_green_16_vs_oracle_fmm():
     """Periodic Taylor-Green 16^3, p=10, theta=0.4, ncrit=64 (the benchmark's
     parameters), tensor-core M2L (two K chunks), packed P2P, 27 images and
