@@ -10,73 +10,100 @@ namespace fmm {
 
 namespace {
 
-constexpr int kP2MChunk = 32;
+constexpr int kP2MThreads = 64;  // particles per pass of k_p2m (one per thread)
+constexpr int kP2MRows = 4;      // output rows per thread: P <= 256 (p <= 16)
 
 // One CTA per leaf; threads own coefficients r = tid, tid + 128.
-__global__ void __launch_bounds__(128) k_p2m(const int* __restrict__ leaves, const int* __restrict__ begin,
-                                             const int* __restrict__ end, const int* __restrict__ level,
-                                             const double* __restrict__ center, const double* __restrict__ box,
-                                             const int* __restrict__ cseg,
-                                             const float4* __restrict__ A, const float4* __restrict__ B, int p,
-                                             float* __restrict__ M) {
+__global__ void __launch_bounds__(kP2MThreads) k_p2m(const int* __restrict__ leaves, const int* __restrict__ begin,
+                                                     const int* __restrict__ end, const int* __restrict__ level,
+                                                     const double* __restrict__ center,
+                                                     const double* __restrict__ box, const int* __restrict__ cseg,
+                                                     const float4* __restrict__ A, const float4* __restrict__ B,
+                                                     int p, float* __restrict__ M) {
   extern __shared__ float sm[];
   const int P = p * p;
-  const int NC = p * (p + 1) / 2;
-  float* sR = sm;                       // [32][P] conj(R~) real-packed
-  float* sG = sR + kP2MChunk * P;       // [32][3]
-  float* sRe = sG + kP2MChunk * 3;      // [32][NC] scratch
-  float* sIm = sRe + kP2MChunk * NC;    // [32][NC]
+  const int PS = P | 1;                          // odd row stride: the per-thread row stores hit distinct banks
+  float* sR = sm;                                // [kP2MThreads][PS] conj(R~) real-packed
+  float4* sG = reinterpret_cast<float4*>(sm + ((kP2MThreads * PS + 3) & ~3));  // [kP2MThreads]
   const int leaf = leaves[blockIdx.x];
   const int b = begin[leaf], e = end[leaf];
   const double a = box[4 * (cseg ? cseg[leaf] : 0) + 3] * ldexp(1.0, -level[leaf]);
   const float inv_a = (float)(1.0 / a);
   const double cx = center[3 * leaf], cy = center[3 * leaf + 1], cz = center[3 * leaf + 2];
-  float acc[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  for (int c0 = b; c0 < e; c0 += kP2MChunk) {
-    const int t = threadIdx.x;
-    if (t < kP2MChunk) {
-      int j = c0 + t;
-      float* re = sRe + t * NC;
-      float* im = sIm + t * NC;
-      float* row = sR + t * P;
-      if (j < e) {
-        float4 x = A[j];
-        float4 g = B[j];
-        float yx = (float)((double)x.x - cx) * inv_a;
-        float yy = (float)((double)x.y - cy) * inv_a;
-        float yz = (float)((double)x.z - cz) * inv_a;
-        regular_table_f(yx, yy, yz, p, re, im);
-        for (int n = 0; n < p; ++n) {
-          row[n * n] = re[n * (n + 1) / 2];
-          for (int m = 1; m <= n; ++m) {
-            row[n * n + 2 * m - 1] = re[n * (n + 1) / 2 + m];
-            row[n * n + 2 * m] = -im[n * (n + 1) / 2 + m];
+  const int t = threadIdx.x;
+  float acc[3][kP2MRows];
+#pragma unroll
+  for (int q = 0; q < kP2MRows; ++q) acc[0][q] = acc[1][q] = acc[2][q] = 0.f;
+  for (int c0 = b; c0 < e; c0 += kP2MThreads) {
+    // one particle per thread: the regular solid harmonics R~_n^m by the
+    // recurrences in registers (the diagonal m = n, then up each column m),
+    // stored conjugated in real-packed order
+    const int j = c0 + t;
+    float* row = sR + t * PS;
+    if (j < e) {
+      const float4 x = A[j];
+      const float4 g = B[j];
+      const float X = (float)((double)x.x - cx) * inv_a;
+      const float Y = (float)((double)x.y - cy) * inv_a;
+      const float Z = (float)((double)x.z - cz) * inv_a;
+      const float r2 = X * X + Y * Y + Z * Z;
+      float dre = 1.f, dim = 0.f;  // R~_m^m
+      for (int m = 0; m < p; ++m) {
+        if (m > 0) {
+          const float f = sqrtf((2.f * m - 1.f) / (2.f * m));
+          const float nr = f * (dre * X - dim * Y), ni = f * (dre * Y + dim * X);
+          dre = nr;
+          dim = ni;
+        }
+        float r1r = 0.f, r1i = 0.f, r0r = dre, r0i = dim;  // R~_{n-1}^m, R~_n^m
+        for (int n = m; n < p; ++n) {
+          if (n > m) {
+            const float inv = rsqrtf((float)((n + m) * (n - m)));
+            const float aa = (2.f * n - 1.f) * Z;
+            float vr = aa * r0r, vi = aa * r0i;
+            if (n - 2 >= m) {
+              const float bb = r2 * sqrtf((float)((n + m - 1) * (n - m - 1)));
+              vr -= bb * r1r;
+              vi -= bb * r1i;
+            }
+            r1r = r0r;
+            r1i = r0i;
+            r0r = vr * inv;
+            r0i = vi * inv;
+          }
+          if (m == 0) {
+            row[n * n] = r0r;
+          } else {
+            row[n * n + 2 * m - 1] = r0r;
+            row[n * n + 2 * m] = -r0i;
           }
         }
-        sG[3 * t] = g.x;
-        sG[3 * t + 1] = g.y;
-        sG[3 * t + 2] = g.z;
-      } else {
-        for (int r = 0; r < P; ++r) row[r] = 0.f;
-        sG[3 * t] = sG[3 * t + 1] = sG[3 * t + 2] = 0.f;
       }
+      sG[t] = make_float4(g.x, g.y, g.z, 0.f);
+    } else {
+      for (int r = 0; r < P; ++r) row[r] = 0.f;
+      sG[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    const int cnt = min(kP2MChunk, e - c0);
-    for (int q = 0; q < 2; ++q) {
-      int r = threadIdx.x + 128 * q;
+    // M_c[r] += sum over the chunk's particles of gamma_c R~*[r]
+    const int cnt = min(kP2MThreads, e - c0);
+#pragma unroll
+    for (int q = 0; q < kP2MRows; ++q) {
+      const int r = t + kP2MThreads * q;
       if (r >= P) break;
       for (int jj = 0; jj < cnt; ++jj) {
-        float v = sR[jj * P + r];
-        acc[0][q] = fmaf(sG[3 * jj], v, acc[0][q]);
-        acc[1][q] = fmaf(sG[3 * jj + 1], v, acc[1][q]);
-        acc[2][q] = fmaf(sG[3 * jj + 2], v, acc[2][q]);
+        const float v = sR[jj * PS + r];
+        const float4 gg = sG[jj];
+        acc[0][q] = fmaf(gg.x, v, acc[0][q]);
+        acc[1][q] = fmaf(gg.y, v, acc[1][q]);
+        acc[2][q] = fmaf(gg.z, v, acc[2][q]);
       }
     }
     __syncthreads();
   }
-  for (int q = 0; q < 2; ++q) {
-    int r = threadIdx.x + 128 * q;
+#pragma unroll
+  for (int q = 0; q < kP2MRows; ++q) {
+    const int r = t + kP2MThreads * q;
     if (r >= P) break;
     for (int c = 0; c < 3; ++c) M[((size_t)leaf * 3 + c) * P + r] = acc[c][q];
   }
@@ -164,11 +191,10 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
   const int P = p->P, pp = p->prm.p;
   const int nc = (int)p->ncells;
   FMM_TRY(p->M.ensure((size_t)nc * 3 * P * sizeof(float)));
-  const int NC = pp * (pp + 1) / 2;
-  size_t sh = (size_t)(kP2MChunk * P + kP2MChunk * 3 + 2 * kP2MChunk * NC) * sizeof(float);
+  const size_t sh = ((size_t)((kP2MThreads * (P | 1) + 3) & ~3) + 4 * kP2MThreads) * sizeof(float);
   if (sh > 48 * 1024) FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   ++g_launches;
-  k_p2m<<<(unsigned)p->nleaves, 128, sh, s>>>(p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(),
+  k_p2m<<<(unsigned)p->nleaves, kP2MThreads, sh, s>>>(p->leaves.as<int>(), p->c_begin.as<int>(), p->c_end.as<int>(),
                                               p->c_level.as<int>(), p->c_center.as<double>(),
                                               p->batched ? p->seg_box.as<double>() : p->scal.as<double>(),
                                               p->batched ? p->c_seg.as<int>() : nullptr,
