@@ -169,16 +169,26 @@ def p2p_roofline(st, p2p_ms, traffic=None):
 def m2l_roofline(st, p):
     """Tensor roofline of the M2L phase: the products issued per M2L pair are
     2 P x 3 components x (3 K3 + (P - K3)), K3 = the source coefficients that take
-    all three split products (the rest take hi x hi only); peak = the dense BF16 rate."""
+    all three split products (the rest take hi x hi only); peak = the dense BF16 rate.
+    `issued` counts what the tensor pipe executes instead: every MMA of 128 rows x 192
+    columns x 16 (BF16 path), padding rows above P and empty tile slots included."""
     P = int(p) ** 2
     if not (st.ms_m2l > 0 and st.m2l_tensor):
         return None
     peak, src = bf16_peak()
     k3 = int(st.m2l_split_coefs) or P
     ach = 2.0 * P * 3 * (3 * k3 + (P - k3)) * st.m2l_pairs / (st.ms_m2l * 1e-3) / 1e12
-    return {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "peak_source": src, "ms": st.ms_m2l, "split_coefs": k3,
-            "flops": "2 P x 3 components x (3 K3 + (P - K3)) per M2L pair (useful rows only)"}
+    out = {"bound": "tensor", "kernel": "k_m2l_tc", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+           "frac": ach / peak, "peak_source": src, "ms": st.ms_m2l, "split_coefs": k3,
+           "flops": "2 P x 3 components x (3 K3 + (P - K3)) per M2L pair (useful rows only)"}
+    if k3 % 16 == 0 or k3 == P:  # BF16 path: K steps of 16
+        ks = (P + 15) // 16
+        k3s = min(ks, (k3 + 15) // 16)
+        mmas = (3 * k3s + (ks - k3s)) * ((P + 127) // 128)
+        iss = 2.0 * 128 * 192 * 16 * mmas * st.m2l_steps / (st.ms_m2l * 1e-3) / 1e12
+        out["issued"] = {"achieved": iss, "frac": iss / peak, "mmas_per_step": mmas,
+                         "what": "2 x 128 x 192 x 16 per MMA x MMAs per step x steps"}
+    return out
 
 
 PHASES = ("ms_tree", "ms_upward", "ms_traverse", "ms_m2l", "ms_downward", "ms_p2p", "ms_total")
