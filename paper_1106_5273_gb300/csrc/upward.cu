@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const int* __restrict__ lea
   }
 }
 
-// One CTA per cell of the level; leaves keep their P2M result.
+// One CTA per cell of the level; leaves keep their P2M result.  The cell's
+// expansion is the sum, in child order, of each child's term.
 __global__ void __launch_bounds__(128) k_m2m(int lb, const int* __restrict__ child, const int* __restrict__ nchild,
                                              const uint64_t* __restrict__ ckey, const float* __restrict__ opT, int P,
                                              float* __restrict__ M) {
@@ -127,12 +128,24 @@ __global__ void __launch_bounds__(128) k_m2m(int lb, const int* __restrict__ chi
     for (int h = 0; h < 2; ++h) {
       int r = threadIdx.x + 128 * h;
       if (r >= P) break;
+      // the child's term, then added to the sum of the earlier children's
+      // (the order and rounding of k_m2m8)
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll 8
       for (int k = 0; k < P; ++k) {
         float w = W[(size_t)k * P + r];
-        acc[0][h] = fmaf(w, sMc[k], acc[0][h]);
-        acc[1][h] = fmaf(w, sMc[P + k], acc[1][h]);
-        acc[2][h] = fmaf(w, sMc[2 * P + k], acc[2][h]);
+        a0 = fmaf(w, sMc[k], a0);
+        a1 = fmaf(w, sMc[P + k], a1);
+        a2 = fmaf(w, sMc[2 * P + k], a2);
+      }
+      if (q == 0) {
+        acc[0][h] = a0;
+        acc[1][h] = a1;
+        acc[2][h] = a2;
+      } else {
+        acc[0][h] += a0;
+        acc[1][h] += a1;
+        acc[2][h] += a2;
       }
     }
     __syncthreads();
@@ -141,6 +154,56 @@ __global__ void __launch_bounds__(128) k_m2m(int lb, const int* __restrict__ chi
     int r = threadIdx.x + 128 * h;
     if (r >= P) break;
     for (int cc = 0; cc < 3; ++cc) M[((size_t)c * 3 + cc) * P + r] = acc[cc][h];
+  }
+}
+
+// The same for levels of few cells (the upper levels, where one CTA per cell
+// walking its children one after the other is a latency chain).  Each of the
+// cell's children has its own group of 128 threads (thread = output row):
+// the group applies the child's octant operator to the child's expansion,
+// and the cell's expansion is the sum of the children's terms in child
+// order (a fixed order, so the result is deterministic).
+constexpr int kM2MGroup = 128;
+constexpr int kM2MWide = 1024;  // levels of at least this many cells use k_m2m (one 128-thread CTA per cell)
+__global__ void __launch_bounds__(8 * kM2MGroup) k_m2m8(int lb, const int* __restrict__ child,
+                                                       const int* __restrict__ nchild,
+                                                       const uint64_t* __restrict__ ckey,
+                                                       const float* __restrict__ opT, int P, float* __restrict__ M) {
+  extern __shared__ float sm[];
+  float* sMc = sm;               // [8][3][P] the children's expansions
+  float* sPart = sm + 8 * 3 * P;  // [8][3][P] each child's term
+  const int c = lb + blockIdx.x;
+  const int nch = nchild[c];
+  if (nch == 0) return;
+  const int g = threadIdx.x / kM2MGroup, t = threadIdx.x % kM2MGroup;
+  const int cb = child[c];
+  for (int i = threadIdx.x; i < nch * 3 * P; i += blockDim.x) sMc[i] = M[(size_t)cb * 3 * P + i];
+  __syncthreads();
+  if (g < nch) {
+    const int oct = (int)(ckey[cb + g] & 7ull);
+    const float* W = opT + (size_t)oct * P * P;
+    const float* x = sMc + g * 3 * P;
+    for (int h = 0; h < 2; ++h) {
+      const int r = t + kM2MGroup * h;
+      if (r >= P) break;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < P; ++k) {
+        const float w = W[(size_t)k * P + r];
+        a0 = fmaf(w, x[k], a0);
+        a1 = fmaf(w, x[P + k], a1);
+        a2 = fmaf(w, x[2 * P + k], a2);
+      }
+      sPart[(g * 3 + 0) * P + r] = a0;
+      sPart[(g * 3 + 1) * P + r] = a1;
+      sPart[(g * 3 + 2) * P + r] = a2;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * P; e += blockDim.x) {
+    float acc = sPart[e];
+    for (int q = 1; q < nch; ++q) acc += sPart[q * 3 * P + e];
+    M[(size_t)c * 3 * P + e] = acc;
   }
 }
 
@@ -200,12 +263,20 @@ int upward_pass(fmm_plan p, cudaStream_t s) {
                                               p->batched ? p->c_seg.as<int>() : nullptr,
                                               p->sortA.as<float4>(), p->sortB.as<float4>(), pp, p->M.as<float>());
   FMM_CUDA_TRY(cudaGetLastError());
+  const size_t sh_m2m = (size_t)2 * 8 * 3 * P * sizeof(float);  // 48 KB at P = 256
+  if (sh_m2m > 48 * 1024)
+    FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2m8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_m2m));
   for (int l = p->nlevels - 2; l >= 0; --l) {
     int lb = p->level_begin[l], le = p->level_begin[l + 1];
     ++g_launches;
-    k_m2m<<<le - lb, 128, 3 * P * sizeof(float), s>>>(lb, p->c_child.as<int>(), p->c_nchild.as<int>(),
-                                                      p->c_key.as<uint64_t>(), p->m2m_T.as<float>(), P,
-                                                      p->M.as<float>());
+    if (le - lb >= kM2MWide)
+      k_m2m<<<le - lb, 128, 3 * P * sizeof(float), s>>>(lb, p->c_child.as<int>(), p->c_nchild.as<int>(),
+                                                        p->c_key.as<uint64_t>(), p->m2m_T.as<float>(), P,
+                                                        p->M.as<float>());
+    else
+      k_m2m8<<<le - lb, 8 * kM2MGroup, 2 * 8 * 3 * P * sizeof(float), s>>>(
+          lb, p->c_child.as<int>(), p->c_nchild.as<int>(), p->c_key.as<uint64_t>(), p->m2m_T.as<float>(), P,
+          p->M.as<float>());
   }
   FMM_CUDA_TRY(cudaGetLastError());
   if (p->last_tc) {
