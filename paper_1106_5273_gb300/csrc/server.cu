@@ -320,7 +320,6 @@ void worker_loop(fmm_server S, Worker* W) {
     PlanRec rec = W->plans.count(c) ? W->plans[c] : PlanRec();
     const int ncrit = S->prm.ncrit > 0 ? S->prm.ncrit : (S->tuned.count(c) ? S->tuned[c] : 0);
     int ncrit_used = ncrit;
-    const int64_t others_at_start = S->held_total - W->held;
     lk.unlock();
     int rc = run_batch(S, W, rs, ntot, &rec, ncrit, &ncrit_used);
     lk.lock();
