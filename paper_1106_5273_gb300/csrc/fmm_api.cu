@@ -37,7 +37,7 @@ std::vector<DBuf*> plan_buffers(fmm_plan p) {
   return {&p->m2m_T, &p->l2l_T, &p->l2p_tab, &p->lattice, &p->keys0, &p->keys1, &p->vals0, &p->vals1,
           &p->sortA, &p->sortB, &p->far_u, &p->far_s, &p->leaf_of, &p->in_pos, &p->in_gam, &p->in_sig,
           &p->out_vel, &p->out_dg, &p->c_begin, &p->c_end, &p->c_level, &p->c_parent, &p->c_child,
-          &p->c_nchild, &p->c_key, &p->c_center, &p->c_radius2, &p->c_radius, &p->c_cf, &p->c_tile,
+          &p->c_nchild, &p->c_key, &p->c_center, &p->c_radius2, &p->c_radius, &p->dip_part, &p->c_cf, &p->c_tile,
           &p->tile_cells, &p->tile_first, &p->tile_groups, &p->c_ijk, &p->t_pos, &p->t_gam, &p->t_sig, &p->t_vel, &p->leaves, &p->M, &p->L, &p->Mbf, &p->fr0, &p->fr1, &p->tcount, &p->tmask,
           &p->tscan0, &p->tscan1, &p->tscan2, &p->p2p_raw, &p->m2l_raw, &p->lk0, &p->lk1, &p->lv0, &p->lv1,
           &p->p2p_sorted, &p->p2p_off, &p->m2l_key, &p->m2l_slot, &p->ukeys, &p->T32, &p->Tbf,
@@ -96,7 +96,8 @@ int eval_device(fmm_plan p, int64_t n, const float* pos, const float* gam, const
   FMM_CUDA_TRY(cudaEventRecord(p->ev_fork, s));
   FMM_CUDA_TRY(cudaStreamWaitEvent(p->s_up, p->ev_fork, 0));
   {
-    const int urc = upward_pass(p, p->s_up);
+    int urc = upward_pass(p, p->s_up);
+    if (urc == FMM_OK) urc = dipole_pass(p, n, p->s_up);
     if (urc != FMM_OK) {
       cudaStreamSynchronize(p->s_up);
       return urc;

@@ -119,6 +119,7 @@ struct fmm_plan_s {
   int64_t last_n = 0;
   int last_tc = 0;
   int m2l_stage_chunks = 0;  // K chunks per stage of the last tensor-core M2L
+  fmm::DBuf dip_part;        // partial sums of the dipole term (written beside the traversal)
   // tree reuse (fmm_eval_strengths): set by a successful full evaluation of
   // the plan's own particles; epoch counts full evaluations (a captured graph
   // is valid only within the epoch it was captured in)
@@ -158,6 +159,7 @@ int lattice_operator_host(int p, int images, double* out);
 int lattice_operator_device(int p, int images, double* A, cudaStream_t s);
 // upward.cu
 int upward_pass(fmm_plan p, cudaStream_t s);
+int dipole_pass(fmm_plan p, int64_t n, cudaStream_t s);
 // traverse.cu
 int traverse(fmm_plan p, double sigma_max_host, cudaStream_t s);
 // per-problem MAC and near-field tables of a batch (after the forest is built)

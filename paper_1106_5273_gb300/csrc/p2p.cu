@@ -1046,6 +1046,24 @@ __global__ void __launch_bounds__(256) k_dipole_seg(const float4* __restrict__ A
 
 }  // namespace
 
+// The uniform dipole velocity of a periodic one-problem evaluation (the
+// zero-mean convention, subtracted in the P2P epilogue).  It needs only the
+// sorted particles, so it runs on the upward pass's stream beside the
+// traversal, into its own partial-sum buffer.
+int dipole_pass(fmm_plan p, int64_t n, cudaStream_t s) {
+  if (!p->prm.periodic || p->batched || n == 0) return FMM_OK;
+  const int parts = 256;
+  double* scal = p->scal.as<double>();
+  FMM_TRY(p->dip_part.ensure((size_t)parts * 3 * sizeof(double)));
+  ++g_launches;
+  k_dipole_partial<<<parts, 256, 0, s>>>(p->sortA.as<float4>(), p->sortB.as<float4>(), n, scal,
+                                         p->dip_part.as<double>());
+  ++g_launches;
+  k_dipole_final<<<1, 32, 0, s>>>(p->dip_part.as<double>(), parts, scal, scal + kScalDipole);
+  FMM_CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
 int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel, float* dg, cudaStream_t s) {
   const double* dip = nullptr;
   double* scal = p->scal.as<double>();
@@ -1056,14 +1074,7 @@ int p2p_near(fmm_plan p, int64_t n, float sig_u, int ps, double smax, float* vel
     k_dipole_seg<<<p->nseg, 256, 0, s>>>(p->sortA.as<float4>(), p->sortB.as<float4>(), p->seg_off.as<int>(),
                                          p->seg_box.as<double>(), sp);
   } else if (p->prm.periodic) {
-    const int parts = 256;
-    FMM_TRY(p->scan_tmp.ensure((size_t)parts * 3 * sizeof(double)));
-    ++g_launches;
-    k_dipole_partial<<<parts, 256, 0, s>>>(p->sortA.as<float4>(), p->sortB.as<float4>(), n, scal,
-                                           p->scan_tmp.as<double>());
-    ++g_launches;
-    k_dipole_final<<<1, 32, 0, s>>>(p->scan_tmp.as<double>(), parts, scal, scal + kScalDipole);
-    dip = scal + kScalDipole;
+    dip = scal + kScalDipole;  // dipole_pass ran beside the traversal
   }
   const float blen = p->prm.periodic ? (float)p->prm.box_len : 0.f;
   SigK K0 = make_sigk(ps ? 1.f : sig_u);

@@ -52,6 +52,7 @@ int eval_strengths(fmm_plan p, const float* gam, float* vel, float* dg, cudaStre
   k_gather_gamma<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gam, p->sidx, n, p->sortB.as<float4>());
   FMM_CUDA_TRY(cudaGetLastError());
   FMM_TRY(upward_pass(p, s));
+  FMM_TRY(dipole_pass(p, n, s));
   const size_t lbytes = (size_t)p->ncells * 3 * p->P * sizeof(float);
   FMM_CUDA_TRY(cudaMemsetAsync(p->L.ptr, 0, lbytes, s));
   if (p->last_tc) FMM_TRY(m2l_tensor(p, s));
