@@ -442,13 +442,13 @@ int fmm_plan_get_lists(fmm_plan p, int32_t* p2p, int32_t* m2l) {
       p2p[3 * i + 2] = h[i].z;
     }
   }
-  if (m2l && p->n_m2l) {
-    std::vector<int4> h(p->n_m2l);
-    FMM_CUDA_TRY(cudaMemcpy(h.data(), p->m2l_raw.ptr, p->n_m2l * sizeof(int4), cudaMemcpyDeviceToHost));
+  if (m2l && p->n_m2l) {  // 8-byte records: (target, source | image << 27)
+    std::vector<int2> h(p->n_m2l);
+    FMM_CUDA_TRY(cudaMemcpy(h.data(), p->m2l_raw.ptr, p->n_m2l * sizeof(int2), cudaMemcpyDeviceToHost));
     for (int64_t i = 0; i < p->n_m2l; ++i) {
       m2l[3 * i] = h[i].x;
-      m2l[3 * i + 1] = h[i].y;
-      m2l[3 * i + 2] = h[i].z;
+      m2l[3 * i + 1] = h[i].y & ((1 << 27) - 1);
+      m2l[3 * i + 2] = (int32_t)((uint32_t)h[i].y >> 27);
     }
   }
   return FMM_OK;

@@ -92,9 +92,16 @@ __device__ inline int interact(const TravArgs& t, int a, int b, int o) {
   return 2;                                                   // push
 }
 
+// An M2L pair record in 8 bytes: (target, source | image << 27).  Cells are
+// fewer than 2^27 (checked before the traversal) and images fewer than 32.
+constexpr int kPairSrcBits = 27;
+__device__ __forceinline__ int2 pack_m2l(int a, int b, int img) { return make_int2(a, b | (img << kPairSrcBits)); }
+__device__ __forceinline__ int m2l_src(int2 v) { return v.y & ((1 << kPairSrcBits) - 1); }
+__device__ __forceinline__ int m2l_img(int2 v) { return (int)((unsigned)v.y >> kPairSrcBits); }
+
 // Initial pairs (root r, root r + o L) for every root (one per problem) and
 // image, in (root, image) order; one CTA, order-preserving compaction.
-__global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int nimg, int img0, int4* fr, int4* m2l,
+__global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int nimg, int img0, int4* fr, int2* m2l,
                                                     int4* p2p, uint32_t* cnt) {
   __shared__ uint32_t wsum[3][32];
   __shared__ uint32_t base[3];
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(1024) k_trav_init(TravArgs t, int nroot, int n
       base[tid] = acc;
     }
     __syncthreads();
-    if (ty == 0) m2l[wsum[0][w] + rank[0]] = v;
+    if (ty == 0) m2l[wsum[0][w] + rank[0]] = pack_m2l(v.x, v.y, v.z);
     else if (ty == 1) p2p[wsum[1][w] + rank[1]] = v;
     else if (ty == 2) fr[wsum[2][w] + rank[2]] = v;
     __syncthreads();
@@ -228,7 +235,7 @@ __device__ inline void block_scan3(uint32_t v[3], uint32_t tot[3]) {
 }
 
 __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __restrict__ frA, int4* __restrict__ frB,
-                                                            const uint32_t* __restrict__ cnt0, int4* __restrict__ m2l,
+                                                            const uint32_t* __restrict__ cnt0, int2* __restrict__ m2l,
                                                             int4* __restrict__ p2p, uint32_t* __restrict__ mask,
                                                             uint32_t* __restrict__ blk, TravState* st, uint32_t cap_fr,
                                                             uint32_t cap_m, uint32_t cap_p, int resume) {
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(kTravThreads) k_trav_loop(TravArgs t, int4* __
           const int ch = c0 + (int)q;
           const int4 val = sa ? make_int4(ch, pr.y, pr.z, 0) : make_int4(pr.x, ch, pr.z, 0);
           const uint32_t ty = (msk >> (2 * q)) & 3u;
-          if (ty == 0) m2l[im++] = val;
+          if (ty == 0) m2l[im++] = pack_m2l(val.x, val.y, val.z);
           else if (ty == 1) p2p[ip++] = val;
           else nxt[iff++] = val;
         }
@@ -429,21 +436,22 @@ __global__ void k_cell_ijk(const int* __restrict__ level, const uint64_t* __rest
 // Translation key of every M2L pair, and the field ranges of the keys
 // (delta, tx, ty, tz; min and max in rng[2q], rng[2q + 1]) for their compact
 // encoding.
-__global__ void k_m2l_keys(const int4* __restrict__ raw, int n, const int* __restrict__ level,
+__global__ void k_m2l_keys(const int2* __restrict__ raw, int n, const int* __restrict__ level,
                            const uint64_t* __restrict__ cijk, uint64_t* __restrict__ keys, int* __restrict__ rng,
                            int* __restrict__ flag) {
   int lo[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX}, hi[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
   // grid-stride over the pairs: few blocks, so few atomics on the 8 range words
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int4 v = raw[i];
-    int la = level[v.x], lb = level[v.y];
+    const int2 pr = raw[i];
+    const int va = pr.x, vb = m2l_src(pr), vz = m2l_img(pr);
+    int la = level[va], lb = level[vb];
     int lf = la > lb ? la : lb;
-    const uint64_t pa = cijk[v.x], pb = cijk[v.y];
+    const uint64_t pa = cijk[va], pb = cijk[vb];
     const long long ia[3] = {(long long)(pa & 0x1FFFFFull), (long long)((pa >> 21) & 0x1FFFFFull),
                              (long long)(pa >> 42)};
     const long long ib[3] = {(long long)(pb & 0x1FFFFFull), (long long)((pb >> 21) & 0x1FFFFFull),
                              (long long)(pb >> 42)};
-    int o[3] = {v.z / 9 - 1, (v.z / 3) % 3 - 1, v.z % 3 - 1};
+    int o[3] = {vz / 9 - 1, (vz / 3) % 3 - 1, vz % 3 - 1};
     long long t[3];
     bool ok = true;
     for (int q = 0; q < 3; ++q) {
@@ -514,7 +522,7 @@ __device__ inline uint64_t compact_key(uint64_t k, const KeyPack& kp) {
 // (tile, compact key) sort keys of the M2L pairs: a run of equal keys is one
 // step.  A target has at most one source per translation, so the pairs of a
 // step have distinct slots and their order within the run does not matter.
-__global__ void k_step_keys2(const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
+__global__ void k_step_keys2(const int2* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
                              const int* __restrict__ ctile, KeyPack kp, uint64_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -546,7 +554,7 @@ __global__ void k_key_unpack(const uint32_t* __restrict__ kflag, const uint32_t*
 }
 
 // bin of pair i = tile * nkeys + slot; flags the bin and keeps it per pair.
-__global__ void k_bin_mark(const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
+__global__ void k_bin_mark(const int2* __restrict__ raw, const uint64_t* __restrict__ fkeys, int n,
                            const int* __restrict__ ctile, KeyPack kp, const uint32_t* __restrict__ kslot, int nkeys,
                            uint32_t* __restrict__ bflag, uint32_t* __restrict__ pbin) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -564,18 +572,18 @@ __global__ void k_bin_steps(const uint32_t* __restrict__ bflag, const uint32_t* 
   st_slot[bstep[b]] = (int)(b % nkeys);
 }
 
-__global__ void k_bin_fill(const int4* __restrict__ raw, const uint32_t* __restrict__ pbin, int n,
+__global__ void k_bin_fill(const int2* __restrict__ raw, const uint32_t* __restrict__ pbin, int n,
                            const uint32_t* __restrict__ bstep, const int* __restrict__ ctile,
                            int* __restrict__ st_src) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int4 v = raw[i];
-  st_src[(size_t)bstep[pbin[i]] * kTile + (ctile[v.x] % kTile)] = v.y;
+  const int2 v = raw[i];
+  st_src[(size_t)bstep[pbin[i]] * kTile + (ctile[v.x] % kTile)] = m2l_src(v);
 }
 
 __global__ void k_step_write2(const uint64_t* __restrict__ k, const uint32_t* __restrict__ idx, int n,
                               const uint32_t* __restrict__ f, const uint32_t* __restrict__ e,
-                              const int4* __restrict__ raw, const uint64_t* __restrict__ fkeys,
+                              const int2* __restrict__ raw, const uint64_t* __restrict__ fkeys,
                               const int* __restrict__ ctile, int kbits, int* __restrict__ st_tile,
                               uint64_t* __restrict__ st_ckey, uint64_t* __restrict__ st_fkey,
                               int* __restrict__ st_src) {
@@ -588,8 +596,8 @@ __global__ void k_step_write2(const uint64_t* __restrict__ k, const uint32_t* __
     st_ckey[s] = key & ((1ull << kbits) - 1ull);
     st_fkey[s] = fkeys[idx[i]];
   }
-  const int4 v = raw[idx[i]];
-  st_src[(size_t)s * kTile + (ctile[v.x] % kTile)] = v.y;
+  const int2 v = raw[idx[i]];
+  st_src[(size_t)s * kTile + (ctile[v.x] % kTile)] = m2l_src(v);
 }
 
 __global__ void k_step_slots(const uint64_t* __restrict__ sk, const uint32_t* __restrict__ sidx, int ns,
@@ -718,6 +726,7 @@ int segment_tables(fmm_plan p, int per_particle_sigma, cudaStream_t s) {
 int traverse(fmm_plan p, double smax, cudaStream_t s) {
   const int T = 256;
   const int nc = (int)p->ncells;
+  if (p->ncells >= (1ll << kPairSrcBits)) return FMM_E_CAPACITY;  // the 8-byte M2L pair record
   TravArgs ta;
   ta.center = p->c_center.as<double>();
   ta.radius = p->c_radius.as<double>();
@@ -781,7 +790,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   const unsigned G = (unsigned)grid_blocks[dev];
   FMM_TRY(p->fr0.ensure(cap_fr * sizeof(int4)));
   FMM_TRY(p->fr1.ensure(cap_fr * sizeof(int4)));
-  FMM_TRY(p->m2l_raw.ensure(cap_m * sizeof(int4)));
+  FMM_TRY(p->m2l_raw.ensure(cap_m * sizeof(int2)));
   FMM_TRY(p->p2p_raw.ensure(cap_p * sizeof(int4)));
   FMM_TRY(p->tmask.ensure(cap_fr * sizeof(uint32_t)));
   FMM_TRY(p->tscan0.ensure((size_t)(3 * G + 8) * sizeof(uint32_t)));
@@ -789,7 +798,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
   TravState* dst = p->tscan1.as<TravState>();
   FMM_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(TravState), s));
   ++g_launches;
-  k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int4>(),
+  k_trav_init<<<1, 1024, 0, s>>>(ta, p->batched ? p->nseg : 1, nimg, img0, p->fr0.as<int4>(), p->m2l_raw.as<int2>(),
                                  p->p2p_raw.as<int4>(), dcnt);
   int64_t nm = 0, np = 0;
   for (int launch = 0;; ++launch) {
@@ -797,7 +806,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
     if (launch > 64) return FMM_E_CAPACITY;
     int4* a0 = p->fr0.as<int4>();
     int4* a1 = p->fr1.as<int4>();
-    int4* am = p->m2l_raw.as<int4>();
+    int2* am = p->m2l_raw.as<int2>();
     int4* ap = p->p2p_raw.as<int4>();
     uint32_t* msk = p->tmask.as<uint32_t>();
     uint32_t* blk = p->tscan0.as<uint32_t>();
@@ -816,7 +825,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       if ((int64_t)hs.need_p > cap_p) cap_p = (int64_t)hs.need_p + hs.need_p / 4 + 1024;
       if ((int64_t)hs.need_f > cap_fr) cap_fr = (int64_t)hs.need_f + hs.need_f / 4 + 1024;
       if (cap_fr > 0x7fffffff || cap_m > 0x7fffffff || cap_p > 0x7fffffff) return FMM_E_CAPACITY;
-      FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int4), s));
+      FMM_TRY(p->m2l_raw.grow_copy(cap_m * sizeof(int2), s));
       FMM_TRY(p->p2p_raw.grow_copy(cap_p * sizeof(int4), s));
       FMM_TRY(p->fr0.grow_copy(cap_fr * sizeof(int4), s));
       FMM_TRY(p->fr1.grow_copy(cap_fr * sizeof(int4), s));
@@ -933,7 +942,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       int* hr = reinterpret_cast<int*>(reinterpret_cast<char*>(p->pinned) + 256);
       memcpy(hr, init, sizeof(init));
       FMM_CUDA_TRY(cudaMemcpyAsync(drng, hr, sizeof(init), cudaMemcpyHostToDevice, s));
-      k_m2l_keys<<<std::min<unsigned>(g, 2048u), T, 0, s>>>(p->m2l_raw.as<int4>(), n, p->c_level.as<int>(),
+      k_m2l_keys<<<std::min<unsigned>(g, 2048u), T, 0, s>>>(p->m2l_raw.as<int2>(), n, p->c_level.as<int>(),
                                                             p->c_ijk.as<uint64_t>(), p->m2l_key.as<uint64_t>(), drng,
                                                             flag);
       FMM_CUDA_TRY(cudaMemcpyAsync(hr, drng, sizeof(init), cudaMemcpyDeviceToHost, s));
@@ -983,7 +992,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
           uint32_t* pbin = p->lv0.as<uint32_t>();
           FMM_CUDA_TRY(cudaMemsetAsync(bflag, 0, (size_t)nb * sizeof(uint32_t), s));
           ++g_launches;
-          k_bin_mark<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
+          k_bin_mark<<<g, T, 0, s>>>(p->m2l_raw.as<int2>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
                                      kslot, (int)nkeys, bflag, pbin);
           FMM_TRY(exclusive_scan_u32(bflag, bstep, nb, dcnt, p->scan_tmp, s));
           FMM_CUDA_TRY(cudaMemcpyAsync(hc, dcnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -998,7 +1007,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
           k_bin_steps<<<(unsigned)((nb + T - 1) / T), T, 0, s>>>(bflag, bstep, nb, (int)nkeys, p->st_tile.as<int>(),
                                                                  p->st_slot.as<int>());
           ++g_launches;
-          k_bin_fill<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), pbin, n, bstep, p->c_tile.as<int>(),
+          k_bin_fill<<<g, T, 0, s>>>(p->m2l_raw.as<int2>(), pbin, n, bstep, p->c_tile.as<int>(),
                                      p->st_src.as<int>());
           ++g_launches;
           k_tile_ranges<<<(unsigned)((ns + T - 1) / T), T, 0, s>>>(p->st_tile.as<int>(), (int)ns,
@@ -1009,7 +1018,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
       if (!binned) {
         // 2. sort pairs by (tile, compact key): consecutive runs are the steps
         ++g_launches;
-        k_step_keys2<<<g, T, 0, s>>>(p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
+        k_step_keys2<<<g, T, 0, s>>>(p->m2l_raw.as<int2>(), p->m2l_key.as<uint64_t>(), n, p->c_tile.as<int>(), kp,
                                      p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>());
         int second = 0;
         FMM_TRY(radix_sort_u64(p->lk0.as<uint64_t>(), p->lv0.as<uint32_t>(), p->lk1.as<uint64_t>(),
@@ -1031,7 +1040,7 @@ int traverse(fmm_plan p, double smax, cudaStream_t s) {
         FMM_CUDA_TRY(cudaMemsetAsync(p->st_src.ptr, 0xff, (ns + 1) * kTile * sizeof(int), s));
         ++g_launches;
         k_step_write2<<<g, T, 0, s>>>(sk, sv, n, p->tcount.as<uint32_t>(), p->tscan0.as<uint32_t>(),
-                                      p->m2l_raw.as<int4>(), p->m2l_key.as<uint64_t>(), p->c_tile.as<int>(), kp.bits,
+                                      p->m2l_raw.as<int2>(), p->m2l_key.as<uint64_t>(), p->c_tile.as<int>(), kp.bits,
                                       p->st_tile.as<int>(),
                                       p->st_ckey.as<uint64_t>(), p->st_fkey.as<uint64_t>(), p->st_src.as<int>());
         ++g_launches;
