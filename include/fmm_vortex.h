@@ -288,7 +288,9 @@ int64_t fmm_plan_device_bytes(fmm_plan plan);
  * arrival order, up to max_batch_particles / max_batch_problems, and only as
  * far as the device-memory budget admits (see below).  Batches of different
  * workers run concurrently on the device.  Requests that arrive while batches
- * run wait in the queue and join the next batch of their class.
+ * run wait in the queue and join the next batch of their class; a batch
+ * leaves to idle workers the requests they can start at once (it takes at
+ * most the queued requests minus the idle other workers).
  *
  * Memory admission: the server accounts every device byte it holds (plans and
  * staging buffers).  A batch is admitted when the bytes held by all workers,

@@ -239,8 +239,15 @@ void worker_loop(fmm_server S, Worker* W) {
       if (S->stop) break;
       continue;
     }
-    // ---- form a batch: the oldest request, then later ones of its class
-    const int max_prob = S->prm.batching ? S->prm.max_batch_problems : 1;
+    // ---- form a batch: the oldest request, then later ones of its class.
+    // Requests that an idle worker can start right away are left to it: a
+    // batch takes at most (queued requests - idle other workers), so batches
+    // form only from requests that would otherwise wait (below saturation a
+    // small request does not wait behind a large one in the same batch).
+    int idle_others = 0;
+    for (Worker* o : S->workers) idle_others += (o != W && !o->busy) ? 1 : 0;
+    const int max_prob =
+        S->prm.batching ? std::max(1, std::min(S->prm.max_batch_problems, (int)S->queue.size() - idle_others)) : 1;
     const int64_t budget = S->prm.hbm_budget_bytes;
     std::vector<int64_t> batch;
     int64_t ntot = 0;
